@@ -1,0 +1,165 @@
+/*
+ * grlb.h -- C ABI of the B300 (sm_103a) gradient-reconstruction lattice Boltzmann sweep for
+ * the compressible Navier-Stokes-Fourier equations (arxiv 2609.16361).
+ *
+ * One domain = five conserved-field D3Q7 lattices (rho, m_x, m_y, m_z, E), 35 populations per
+ * cell (Sec. 2.2), advanced by the fused stream-and-collide sweep of Algorithm 1.
+ *
+ * Conventions shared by every entry point:
+ *  - Ownership: the library allocates and owns all device memory of a domain or batch; the
+ *    caller owns every host array it passes and keeps it alive for the duration of the call.
+ *  - Fields on the host are FP64, physical units, structure of arrays, x fastest:
+ *    a[x + nx*(y + ny*z)], N = nx*ny*nz entries per field plane.
+ *  - Streams: work is enqueued on the stream given at creation (a cudaStream_t passed as
+ *    void*, e.g. a torch stream handle; NULL = legacy default stream).  grlb_step,
+ *    grlb_step_diag and grlb_batch_step only enqueue.  Calls that return host data
+ *    (grlb_read_*, grlb_diag_read, grlb_save) synchronize that stream first.
+ *  - Errors: every call returns a grlb_status; on failure grlb_last_error() returns a
+ *    thread-local message.  No call aborts the process.  A numeric blow-up is reported by
+ *    the diagnostics (n_nan, n_floor), not by the plain sweep.
+ *  - Lattice units: dx = dt = 1 inside the kernels.  With s = dt/dx: rho unchanged,
+ *    u_L = s u, (p, E, T)_L = s^2 (p, E, T), (mu, kappa)_L = (mu, kappa) dt/dx^2.
+ */
+#ifndef GRLB_H
+#define GRLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRLB_OK = 0,
+    GRLB_EINVAL = -1,   /* bad argument (null pointer, size, enum, parameter range)      */
+    GRLB_ENOMEM = -2,   /* device or host allocation failed                              */
+    GRLB_ECUDA = -3,    /* a CUDA runtime call failed; message carries cudaGetErrorString */
+    GRLB_ENUMERIC = -4, /* non-finite or non-positive state detected                     */
+    GRLB_ETIMEOUT = -5, /* a bounded device wait ran out                                 */
+    GRLB_ESTATE = -6    /* call not valid in the object's current state                  */
+} grlb_status;
+
+typedef enum { GRLB_BC_PERIODIC = 0, GRLB_BC_X_DIRICHLET_EQ = 1 } grlb_bc;
+typedef enum { GRLB_COLL_BGK = 0, GRLB_COLL_RLB_SENSOR = 1 } grlb_collision;
+typedef enum { GRLB_STORE_F32 = 0, GRLB_STORE_F16 = 1, GRLB_STORE_BF16 = 2 } grlb_storage;
+
+/* Physical description of one domain (Sec. 2.1 system, Listing 1 closures, Listing 2
+ * sensor, Tab. run_params numerical parameters). */
+typedef struct {
+    int32_t nx, ny, nz;         /* cells; N = nx*ny*nz must be < 2^31                       */
+    int32_t bc;                 /* grlb_bc.  X_DIRICHLET_EQ: ghost cells at x=-1 and x=nx
+                                   hold the equilibrium of left_prim / right_prim; y, z
+                                   periodic.  PERIODIC: every axis periodic.                 */
+    int32_t collision;          /* grlb_collision (Sec. 2.2 BGK, Sec. 2.5 regularized)      */
+    int32_t storage;            /* grlb_storage: population storage type                   */
+    double dx, dt;              /* physical cell size and time step (> 0)                  */
+    double gamma;               /* ratio of specific heats (> 1)                            */
+    double mu_ref;              /* dynamic viscosity at T_ref (>= 0)                        */
+    double prandtl;             /* kappa = mu c_p / Pr, c_p = gamma/(gamma-1)  (> 0)        */
+    double T_ref;               /* Sutherland reference temperature (T = p/rho, > 0)        */
+    int32_t sutherland;         /* 1: mu(T) by the Sutherland law of Listing 1; 0: constant */
+    int32_t pad0;
+    double T_S;                 /* Sutherland constant relative to T_ref (0.4042)           */
+    double omega_rho, omega_mom, omega_E; /* per-field relaxation 1/tau_LB, in (0, 2]       */
+    double omega_min;           /* sensor floor rate (Listing 2)                            */
+    double sensor_gain;         /* g (Listing 2)                                            */
+    double J_min;               /* compression dead band (Listing 2)                        */
+    double rho_min, p_min;      /* positivity floors, physical units (Alg. 1)               */
+    double ref_rho, ref_p;      /* reference state at rest of the equilibrium shift (Sec. 2.2) */
+    double left_prim[5];        /* (rho, ux, uy, uz, p) of the x = -1 ghost                 */
+    double right_prim[5];       /* (rho, ux, uy, uz, p) of the x = nx ghost                 */
+} grlb_params;
+
+/* Diagnostics of the state a diagnostic sweep lands on (lattice units, FP64 sums). */
+typedef struct {
+    double totals[5];   /* sum over cells of Q_k (rho, m_x, m_y, m_z, E), lattice units      */
+    double ke;          /* sum of 1/2 |m|^2 / rho                                            */
+    double eps_s;       /* sum of mu |curl u|^2 (solenoidal dissipation, Sec. 3.4)          */
+    double eps_d;       /* sum of (4/3) mu (div u)^2 (dilatational dissipation, Sec. 3.4)   */
+    double rho_min;     /* minimum unfloored density                                        */
+    double p_min;       /* minimum unfloored pressure, lattice units                        */
+    int64_t n_floor;    /* cells where rho or p hit its floor                               */
+    int64_t n_nan;      /* cells with a non-finite conserved moment                         */
+    int64_t n_sensor;   /* cells with chi > 0                                                */
+    int64_t step;       /* time step the values refer to                                     */
+    double s;           /* dt/dx of the domain, for conversion to physical units            */
+    int64_t ncells;
+} grlb_diag;
+
+typedef struct grlb_domain grlb_domain;
+typedef struct grlb_batch grlb_batch;
+
+/* Last error message of the calling thread ("" if none). Never NULL. */
+const char* grlb_last_error(void);
+/* Library version string. */
+const char* grlb_version(void);
+
+/* Create a domain: validates p, allocates two population buffers (35 planes each, storage
+ * type per p->storage) and the diagnostic scratch on the current CUDA device.  stream is a
+ * cudaStream_t (may be NULL).  On success *out owns the memory; free with grlb_destroy. */
+grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out);
+void grlb_destroy(grlb_domain* d);
+grlb_status grlb_set_stream(grlb_domain* d, void* stream);
+/* Device bytes the domain holds (populations + scratch). */
+size_t grlb_device_bytes(const grlb_domain* d);
+/* Device bytes grlb_create would allocate for these parameters (0 if invalid). */
+size_t grlb_bytes_for(const grlb_params* p);
+
+/* Initialise from primitive fields (host FP64, physical units, x fastest): rho[N],
+ * u[3*N] (three planes ux, uy, uz), p[N].  Populations are set to the linear equilibrium of
+ * each cell with the advective flux (zero non-equilibrium), Sec. 2.2.  Resets the step
+ * counter.  Blocks until the host arrays have been copied. */
+grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double* u,
+                                const double* p);
+
+/* Enqueue nsteps >= 0 plain sweeps (Algorithm 1 on every cell + exact streaming). */
+grlb_status grlb_step(grlb_domain* d, int nsteps);
+
+/* Enqueue one diagnostic sweep: the same update as grlb_step(d, 1), which also reduces
+ * the grlb_diag quantities of the state it lands on into a device-side record, with
+ * FP64 block partials summed in a fixed order (bitwise deterministic). */
+grlb_status grlb_step_diag(grlb_domain* d);
+/* Synchronize and copy the record of the last diagnostic sweep to *out. */
+grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out);
+
+/* Conserved fields in physical units: out[5*N] = planes rho, m_x, m_y, m_z, E. */
+grlb_status grlb_read_conserved(grlb_domain* d, double* out);
+/* Primitive fields in physical units (no floors): rho[N], u[3*N], p[N], T[N]; any pointer
+ * may be NULL to skip that field. */
+grlb_status grlb_read_primitive(grlb_domain* d, double* rho, double* u, double* p, double* T);
+
+/* Raw checkpoint: stored populations + step counter.  grlb_save with buf == NULL sets
+ * *bytes to the size needed; otherwise *bytes must be at least that size.  grlb_load
+ * requires a buffer written by grlb_save of a domain with the same params. */
+grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes);
+grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes);
+int64_t grlb_steps_done(const grlb_domain* d);
+
+/* ---- batching: many domains, one launch per step -------------------------------------
+ * A batch references existing domains (it does not own them; destroy the batch first).
+ * One step = one launch over a tile table that concatenates the tiles of every active
+ * domain; tile shape = block_x threads along x (one cell each) x block_y rows.
+ * All domains must live on the same device; the batch runs on the stream of domains[0]
+ * (or the one set with grlb_batch_set_stream). */
+typedef struct {
+    int32_t block_x;    /* threads per block along x: 32, 64, 128, 256 (0 = default 128)   */
+    int32_t block_y;    /* rows per block: 1, 2, 4, 8 (0 = default 1)                        */
+    int32_t use_graph;  /* 1: capture grlb_batch_step's launch loop as a CUDA graph          */
+    int32_t pad0;
+} grlb_batch_config;
+
+grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_batch_config* cfg,
+                              grlb_batch** out);
+void grlb_batch_destroy(grlb_batch* b);
+grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream);
+/* Mark which domains advance (active[i] != 0); rebuilds the tile table.  active == NULL
+ * activates all. */
+grlb_status grlb_batch_set_active(grlb_batch* b, const int* active);
+/* Enqueue nsteps sweeps of every active domain, one launch per step. */
+grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRLB_H */

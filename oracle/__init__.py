@@ -1,0 +1,214 @@
+"""FP64 CPU oracle of the five-field gradient-reconstruction LBM (arxiv 2609.16361).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the CPU-baseline
+leg of the benchmark; never by the product package.  It shares no code with the CUDA path.
+
+`Oracle` wraps the C stepper in `grlb_oracle.c` (compiled here with gcc + OpenMP) and does its
+own conversion of a physical-unit case to lattice units (dx = dt = 1):
+  rho unchanged; u_L = s u; p_L, E_L, T_L = s^2 (p, E, T); mu_L = mu dt/dx^2, same for kappa;
+  with s = dt/dx.  kappa = mu c_p / Pr with c_p = gamma/(gamma - 1) (T = p/rho, R = 1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "grlb_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libgrlb_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc -O2 -fopenmp)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int),
+                ("collision", C.c_int), ("sutherland", C.c_int), ("gamma", C.c_double),
+                ("mu_ref", C.c_double), ("kappa_ref", C.c_double), ("T_ref", C.c_double),
+                ("T_S", C.c_double), ("omega", C.c_double * 5), ("omega_min", C.c_double),
+                ("gain", C.c_double), ("J_min", C.c_double), ("rho_min", C.c_double),
+                ("p_min", C.c_double), ("left", C.c_double * 5), ("right", C.c_double * 5)]
+
+
+class CellInfo(C.Structure):
+    _fields_ = [("Q", C.c_double * 5), ("rho", C.c_double), ("u", C.c_double * 3),
+                ("p", C.c_double), ("T", C.c_double), ("mu", C.c_double),
+                ("kappa", C.c_double), ("gradQ", C.c_double * 15), ("gradu", C.c_double * 9),
+                ("gradT", C.c_double * 3), ("chi", C.c_double), ("floored", C.c_int)]
+
+
+CELL_DTYPE = np.dtype([("Q", "f8", 5), ("rho", "f8"), ("u", "f8", 3), ("p", "f8"),
+                       ("T", "f8"), ("mu", "f8"), ("kappa", "f8"), ("gradQ", "f8", 15),
+                       ("gradu", "f8", 9), ("gradT", "f8", 3), ("chi", "f8"),
+                       ("floored", "i4"), ("_pad", "i4")])
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            dp = C.POINTER(C.c_double)
+            L.orc_step.argtypes = [C.POINTER(_Params), dp, dp, C.c_void_p]
+            L.orc_step.restype = C.c_int
+            L.orc_cell.argtypes = [C.POINTER(_Params), dp, dp, C.POINTER(CellInfo)]
+            L.orc_cell.restype = C.c_int
+            L.orc_init_equilibrium.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp, dp]
+            L.orc_init_equilibrium.restype = None
+            L.orc_equilibrium_state.argtypes = [C.POINTER(_Params), dp, dp]
+            L.orc_equilibrium_state.restype = None
+            L.orc_moments.argtypes = [C.POINTER(_Params), dp, dp]
+            L.orc_moments.restype = None
+            L.orc_cell_info_size.restype = C.c_size_t
+            assert L.orc_cell_info_size() == CELL_DTYPE.itemsize == C.sizeof(CellInfo)
+            _lib = L
+        return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def lattice_params(prm) -> _Params:
+    """Physical-unit CaseParams -> lattice-unit oracle parameters."""
+    s = prm.dt / prm.dx
+    g = prm.gamma
+    cp = g / (g - 1.0)
+    mu_L = prm.mu_ref * prm.dt / prm.dx ** 2
+    kap_L = mu_L * cp / prm.prandtl
+    P = _Params()
+    P.nx, P.ny, P.nz = prm.nx, prm.ny, prm.nz
+    P.bc, P.collision, P.sutherland = prm.bc, prm.collision, prm.sutherland
+    P.gamma = g
+    P.mu_ref, P.kappa_ref = mu_L, kap_L
+    P.T_ref = prm.T_ref * s * s
+    P.T_S = prm.T_S
+    om = [prm.omega_rho, prm.omega_mom, prm.omega_mom, prm.omega_mom, prm.omega_E]
+    for k in range(5):
+        P.omega[k] = om[k]
+    P.omega_min, P.gain, P.J_min = prm.omega_min, prm.sensor_gain, prm.J_min
+    P.rho_min, P.p_min = prm.rho_min, prm.p_min * s * s
+
+    def prim_L(pr):
+        return (pr[0], pr[1] * s, pr[2] * s, pr[3] * s, pr[4] * s * s)
+
+    for k, v in enumerate(prim_L(prm.left_prim)):
+        P.left[k] = v
+    for k, v in enumerate(prim_L(prm.right_prim)):
+        P.right[k] = v
+    return P
+
+
+class Oracle:
+    """FP64 stepper for one domain of a physical-unit case."""
+
+    def __init__(self, prm):
+        self.prm = prm
+        self.P = lattice_params(prm)
+        self.s = prm.dt / prm.dx
+        self.N = prm.nx * prm.ny * prm.nz
+        self.f = np.zeros((35, self.N))
+        self.g = np.zeros((35, self.N))
+        self.steps = 0
+        self.last_cells = None
+
+    # -- state --------------------------------------------------------------------------
+    def init_primitive(self, rho, u, p):
+        s = self.s
+        rho = np.ascontiguousarray(rho, np.float64)
+        ux = np.ascontiguousarray(u[0] * s)
+        uy = np.ascontiguousarray(u[1] * s)
+        uz = np.ascontiguousarray(u[2] * s)
+        pL = np.ascontiguousarray(np.asarray(p, np.float64) * s * s)
+        lib().orc_init_equilibrium(C.byref(self.P), _dp(rho), _dp(ux), _dp(uy), _dp(uz),
+                                   _dp(pL), _dp(self.f))
+        self.steps = 0
+
+    def step(self, n: int = 1, keep_cells: bool = False):
+        L = lib()
+        for it in range(n):
+            cells = None
+            if keep_cells and it == n - 1:
+                cells = np.zeros(self.N, CELL_DTYPE)
+            rc = L.orc_step(C.byref(self.P), _dp(self.f), _dp(self.g),
+                            None if cells is None else cells.ctypes.data_as(C.c_void_p))
+            if rc != 0:
+                raise RuntimeError("oracle: singular reconstruction system")
+            self.f, self.g = self.g, self.f
+            self.steps += 1
+            if cells is not None:
+                self.last_cells = cells
+
+    # -- readback (physical units) -------------------------------------------------------
+    def conserved_lattice(self):
+        Q = np.zeros((5, self.N))
+        lib().orc_moments(C.byref(self.P), _dp(self.f), _dp(Q))
+        return Q
+
+    def conserved(self):
+        """(rho, m_x, m_y, m_z, E) in physical units, shape (5, N)."""
+        Q = self.conserved_lattice()
+        s = self.s
+        Q[1:4] /= s
+        Q[4] /= s * s
+        return Q
+
+    def primitive(self):
+        """rho, u (3, N), p, T in physical units (no floors)."""
+        Q = self.conserved()
+        rho = Q[0]
+        u = Q[1:4] / rho
+        p = (self.prm.gamma - 1.0) * (Q[4] - 0.5 * rho * (u * u).sum(0))
+        return rho, u, p, p / rho
+
+    def diagnostics_from_cells(self, cells=None):
+        """Lattice-unit volume sums of the state the last step landed on (pre-collision):
+        totals of Q_k, kinetic energy 1/2|m|^2/rho, solenoidal mu|curl u|^2 and dilatational
+        (4/3) mu (div u)^2 dissipation, min rho, min p, floor hits, sensor hits."""
+        c = self.last_cells if cells is None else cells
+        gu = c["gradu"].reshape(-1, 3, 3)
+        wx = gu[:, 2, 1] - gu[:, 1, 2]
+        wy = gu[:, 0, 2] - gu[:, 2, 0]
+        wz = gu[:, 1, 0] - gu[:, 0, 1]
+        th = gu[:, 0, 0] + gu[:, 1, 1] + gu[:, 2, 2]
+        m = c["Q"][:, 1:4]
+        return dict(totals=c["Q"].sum(0),
+                    ke=float((0.5 * (m * m).sum(1) / c["rho"]).sum()),
+                    eps_s=float((c["mu"] * (wx * wx + wy * wy + wz * wz)).sum()),
+                    eps_d=float((4.0 / 3.0 * c["mu"] * th * th).sum()),
+                    rho_min=float(c["rho"].min()), p_min=float(c["p"].min()),
+                    n_floor=int(c["floored"].sum()), n_sensor=int((c["chi"] > 0).sum()))
+
+
+def cell(P: _Params, fhat: np.ndarray):
+    """Run Algorithm 1 on one cell; returns (fstar[35], CellInfo)."""
+    fhat = np.ascontiguousarray(fhat, np.float64)
+    out = np.zeros(35)
+    info = CellInfo()
+    rc = lib().orc_cell(C.byref(P), _dp(fhat), _dp(out), C.byref(info))
+    if rc != 0:
+        raise RuntimeError("oracle: singular reconstruction system")
+    return out, info
+
+
+def equilibrium_state(P: _Params, prim) -> np.ndarray:
+    out = np.zeros(35)
+    pr = np.ascontiguousarray(prim, np.float64)
+    lib().orc_equilibrium_state(C.byref(P), _dp(pr), _dp(out))
+    return out
