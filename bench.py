@@ -1,0 +1,333 @@
+"""Benchmark of the fused stream-and-collide sweep: supersonic Taylor-Green vortex at 256^3.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
+
+One bench step = one pass of the whole hot path over one batch of synthetic input: the
+Taylor-Green initial field (M0 = 1.25, Re = 1600, Pr = 0.71, Sutherland, regularized collision
+with the compression sensor, FP32 populations) is turned into populations on the device
+(init kernel), then advanced by 50 time steps = 49 plain sweeps + 1 diagnostic sweep with FP64
+reductions (+ its fixed-order finalize).  Every step restarts from the initial field, so each
+timed step does the same work on the same flow.  MLUP/s = 50 * N / step time.
+
+`value` is device-timed with the inputs resident in HBM; `e2e` is the same metric through the
+public C ABI with host (pinned) buffers: grlb_init_primitive from host FP64 fields + the 50
+sweeps + the diagnostic readback, per step.  Working set 4.7 GB >> 126 MB L2, so no L2 flush.
+
+N > 1 (torchrun): every rank runs its own replica domain (weak scaling, no collective on the
+data path); barrier + max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on the machine's host cores on a bounded slab of the
+same workload (one oracle sweep of 256 x 256 x 16 cells per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 50
+BYTES_PER_LUP = {0: 280, 1: 140, 2: 140}
+KERNEL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh",
+                  "paper_2609_16361_b300/csrc/grlb_kernels.cu"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+def cpu_oracle_sample(n, steps, slab=16, min_seconds=0.0):
+    """Time sweeps of the FP64 oracle on an n x n x slab piece of the n^3 workload: `steps`
+    sweeps, continued until at least `min_seconds` of CPU work has been timed."""
+    import oracle
+    from paper_2609_16361_b300 import inputs
+    c = inputs.tgv3d(n, nxyz=(n, n, slab))
+    o = oracle.Oracle(c.params)
+    o.init_primitive(c.rho, c.u, c.p)
+    t0 = time.perf_counter()
+    o.step(steps)
+    while time.perf_counter() - t0 < min_seconds and steps < 400:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    cells = c.params.ncells
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUP/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle sweep(s) of a {n}x{n}x{slab} slab of the {n}^3 "
+                      f"Taylor-Green workload (same per-cell parameters)"}, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.n
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n, 1)
+    times = []
+    base = None
+    for _ in range(args.steps):
+        base, dt = cpu_oracle_sample(n, 1)
+        times.append(dt)
+    cells = n * n * 16
+    total = sum(times)
+    value = cells * len(times) / total / 1e6
+    base["value"] = value
+    line = {"impl": "reference", "metric": "MLUP/s", "value": value, "unit": "MLUP/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tgv{n}_fp32_rlb_sensor (oracle: FP64, bounded slab)",
+                       "grid": [n, n, 16], "sweeps_per_step": 1},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_16361_b300 import capi, inputs
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}), flush=True)
+        return 1
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    n = args.n
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    case = inputs.tgv3d(n, storage=storage)
+    N = case.params.ncells
+    dev = torch.device("cuda", local)
+    rho_d = torch.from_numpy(case.rho).to(dev)
+    u_d = torch.from_numpy(case.u).to(dev).contiguous()
+    p_d = torch.from_numpy(case.p).to(dev)
+    dom = capi.Domain(case.params, stream=stream.cuda_stream)
+    h = dom.h
+
+    def one_step(ev=None):
+        capi.grlb_init_primitive_device(h, rho_d.data_ptr(), u_d.data_ptr(), p_d.data_ptr())
+        if ev is not None:
+            ev[0].record(stream)
+        capi.grlb_step(h, SWEEPS_PER_STEP - 1)
+        if ev is not None:
+            ev[1].record(stream)
+        capi.grlb_step_diag(h)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            t0.record(stream)
+            for k in range(args.steps):
+                one_step(kev[k])
+            t1.record(stream)
+            stream.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        ms = t0.elapsed_time(t1)
+        sweep_ms = [a.elapsed_time(b) / (SWEEPS_PER_STEP - 1) for a, b in kev]
+        diag = dom.diag()
+        clocks = clk.summary()
+
+        # ---- end to end through the public C ABI with pinned host buffers ---------------
+        rho_h = torch.from_numpy(case.rho).pin_memory()
+        u_h = torch.from_numpy(case.u).pin_memory()
+        p_h = torch.from_numpy(case.p).pin_memory()
+        rho_np, u_np, p_np = rho_h.numpy(), u_h.numpy(), p_h.numpy()
+        e2e_steps = max(2, min(args.steps, 5))
+
+        def e2e_step():
+            capi.grlb_init_primitive(h, rho_np, u_np, p_np)
+            capi.grlb_step(h, SWEEPS_PER_STEP - 1)
+            capi.grlb_step_diag(h)
+            return capi.grlb_diag_read(h)
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - te0
+        barrier()
+
+    # max over ranks
+    vals = torch.tensor([ms, te, float(np.median(sweep_ms))], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms, te, sweep_med = vals.tolist()
+    ms_per_step = ms / args.steps
+    lups = ws * N * SWEEPS_PER_STEP * args.steps / (ms / 1e3)
+    e2e_lups = ws * N * SWEEPS_PER_STEP * e2e_steps / te
+
+    peak, peak_src = measured_peaks()
+    bpl = BYTES_PER_LUP[storage]
+    achieved = bpl * N / (sweep_med / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        t = json.load(open(TRAFFIC_FILE))
+        rec = t.get(f"tgv{n}_{args.storage}")
+        if rec and rec.get("source_sha") == kernel_source_sha():
+            traffic = rec.get("dram_bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, _ = cpu_oracle_sample(n, 1, min_seconds=10.0)
+
+    if rank == 0:
+        line = {
+            "metric": "MLUP/s", "value": lups / 1e6, "unit": "MLUP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "f16-storage/f32", 2: "bf16-storage/f32"}[storage],
+            "data": "synthetic",
+            "config": {"workload": f"tgv{n}_{args.storage}_rlb_sensor", "grid": [n, n, n],
+                       "mach": 1.25, "re": 1600, "sweeps_per_step": SWEEPS_PER_STEP,
+                       "step": "init kernel + 49 sweeps + 1 diagnostic sweep (FP64 reductions)",
+                       "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (4.7 GB populations), no flush"},
+            "e2e": {"value": e2e_lups / 1e6, "unit": "MLUP/s",
+                    "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 8 * 13},
+            "gpu_launches": args.steps * (SWEEPS_PER_STEP + 2),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"sweep_kernel<{args.storage},RLB> (plain sweep)",
+                         "bytes_per_launch": bpl * N, "launch_ms_median": sweep_med,
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "diag_at_end": {"n_nan": diag["n_nan"], "n_sensor": diag["n_sensor"],
+                            "ke": diag["ke"], "step": diag["step"]},
+        }
+        print(json.dumps(line), flush=True)
+    dom.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

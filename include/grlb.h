@@ -113,6 +113,12 @@ size_t grlb_bytes_for(const grlb_params* p);
 grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double* u,
                                 const double* p);
 
+/* Same as grlb_init_primitive with the fields already resident on the domain's device (FP64,
+ * physical units, same layout, device pointers).  Only enqueues on the domain's stream; the
+ * caller keeps the arrays alive until the stream has passed this point. */
+grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const double* u,
+                                       const double* p);
+
 /* Enqueue nsteps >= 0 plain sweeps (Algorithm 1 on every cell + exact streaming). */
 grlb_status grlb_step(grlb_domain* d, int nsteps);
 

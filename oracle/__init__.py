@@ -76,6 +76,7 @@ def lib():
             L.orc_moments.argtypes = [C.POINTER(_Params), dp, dp]
             L.orc_moments.restype = None
             L.orc_cell_info_size.restype = C.c_size_t
+            L.orc_num_threads.restype = C.c_int
             assert L.orc_cell_info_size() == CELL_DTYPE.itemsize == C.sizeof(CellInfo)
             _lib = L
         return _lib
@@ -194,6 +195,10 @@ class Oracle:
                     eps_d=float((4.0 / 3.0 * c["mu"] * th * th).sum()),
                     rho_min=float(c["rho"].min()), p_min=float(c["p"].min()),
                     n_floor=int(c["floored"].sum()), n_sensor=int((c["chi"] > 0).sum()))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
 
 
 def cell(P: _Params, fhat: np.ndarray):

@@ -405,3 +405,15 @@ void orc_moments(const orc_params* P, const double* f, double* Q) {
             Q[(long)k * N + idx] = s;
         }
 }
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* Threads the OpenMP loops use (1 without OpenMP). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,287 @@
+"""ctypes binding of libgrlb (include/grlb.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does nothing but convert
+arguments; all work runs in the CUDA library.  The product path has no CPU fallback: if the
+library is missing or cannot be loaded, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs as _inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrlb.so")
+
+GRLB_OK = 0
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENUMERIC", -5: "ETIMEOUT",
+          -6: "ESTATE"}
+
+
+class GrlbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"grlb {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class grlb_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("bc", C.c_int32),
+                ("collision", C.c_int32), ("storage", C.c_int32), ("dx", C.c_double),
+                ("dt", C.c_double), ("gamma", C.c_double), ("mu_ref", C.c_double),
+                ("prandtl", C.c_double), ("T_ref", C.c_double), ("sutherland", C.c_int32),
+                ("pad0", C.c_int32), ("T_S", C.c_double), ("omega_rho", C.c_double),
+                ("omega_mom", C.c_double), ("omega_E", C.c_double), ("omega_min", C.c_double),
+                ("sensor_gain", C.c_double), ("J_min", C.c_double), ("rho_min", C.c_double),
+                ("p_min", C.c_double), ("ref_rho", C.c_double), ("ref_p", C.c_double),
+                ("left_prim", C.c_double * 5), ("right_prim", C.c_double * 5)]
+
+
+class grlb_diag(C.Structure):
+    _fields_ = [("totals", C.c_double * 5), ("ke", C.c_double), ("eps_s", C.c_double),
+                ("eps_d", C.c_double), ("rho_min", C.c_double), ("p_min", C.c_double),
+                ("n_floor", C.c_int64), ("n_nan", C.c_int64), ("n_sensor", C.c_int64),
+                ("step", C.c_int64), ("s", C.c_double), ("ncells", C.c_int64)]
+
+    def as_dict(self):
+        return dict(totals=np.array(self.totals[:]), ke=self.ke, eps_s=self.eps_s,
+                    eps_d=self.eps_d, rho_min=self.rho_min, p_min=self.p_min,
+                    n_floor=self.n_floor, n_nan=self.n_nan, n_sensor=self.n_sensor,
+                    step=self.step, s=self.s, ncells=self.ncells)
+
+
+class grlb_batch_config(C.Structure):
+    _fields_ = [("block_x", C.c_int32), ("block_y", C.c_int32), ("use_graph", C.c_int32),
+                ("pad0", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libgrlb.so (building it first if the sources are newer).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if _build.needs_build():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise GrlbError(-3, f"CUDA library missing: {LIB_PATH}")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i32, i64, sz = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int64, C.c_size_t
+        sig = {
+            "grlb_last_error": ([], C.c_char_p),
+            "grlb_version": ([], C.c_char_p),
+            "grlb_create": ([C.POINTER(grlb_params), vp, C.POINTER(vp)], i32),
+            "grlb_destroy": ([vp], None),
+            "grlb_set_stream": ([vp, vp], i32),
+            "grlb_device_bytes": ([vp], sz),
+            "grlb_bytes_for": ([C.POINTER(grlb_params)], sz),
+            "grlb_init_primitive": ([vp, dp, dp, dp], i32),
+            "grlb_init_primitive_device": ([vp, vp, vp, vp], i32),
+            "grlb_step": ([vp, i32], i32),
+            "grlb_step_diag": ([vp], i32),
+            "grlb_diag_read": ([vp, C.POINTER(grlb_diag)], i32),
+            "grlb_read_conserved": ([vp, dp], i32),
+            "grlb_read_primitive": ([vp, dp, dp, dp, dp], i32),
+            "grlb_save": ([vp, vp, C.POINTER(sz)], i32),
+            "grlb_load": ([vp, vp, sz], i32),
+            "grlb_steps_done": ([vp], i64),
+            "grlb_batch_create": ([C.POINTER(vp), i32, C.POINTER(grlb_batch_config),
+                                   C.POINTER(vp)], i32),
+            "grlb_batch_destroy": ([vp], None),
+            "grlb_batch_set_stream": ([vp, vp], i32),
+            "grlb_batch_set_active": ([vp, C.POINTER(C.c_int)], i32),
+            "grlb_batch_step": ([vp, i32], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def exported_symbols():
+    return ["grlb_last_error", "grlb_version", "grlb_create", "grlb_destroy", "grlb_set_stream",
+            "grlb_device_bytes", "grlb_bytes_for", "grlb_init_primitive",
+            "grlb_init_primitive_device", "grlb_step",
+            "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
+            "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
+            "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
+            "grlb_batch_step"]
+
+
+def check(status):
+    if status != GRLB_OK:
+        raise GrlbError(status, lib().grlb_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def to_params(prm: "_inputs.CaseParams") -> grlb_params:
+    P = grlb_params()
+    for name, _ in grlb_params._fields_:
+        if name in ("pad0",):
+            continue
+        v = getattr(prm, name)
+        if name in ("left_prim", "right_prim"):
+            arr = getattr(P, name)
+            for k in range(5):
+                arr[k] = float(v[k])
+        else:
+            setattr(P, name, v)
+    return P
+
+
+# ---- thin wrappers with the C names -------------------------------------------------------
+def grlb_create(prm, stream=None):
+    h = C.c_void_p()
+    P = to_params(prm)
+    check(lib().grlb_create(C.byref(P), stream, C.byref(h)))
+    return h
+
+
+def grlb_destroy(h):
+    lib().grlb_destroy(h)
+
+
+def grlb_bytes_for(prm) -> int:
+    P = to_params(prm)
+    return int(lib().grlb_bytes_for(C.byref(P)))
+
+
+def grlb_init_primitive(h, rho, u, p):
+    rho = np.ascontiguousarray(rho, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    p = np.ascontiguousarray(p, np.float64)
+    check(lib().grlb_init_primitive(h, _dp(rho), _dp(u), _dp(p)))
+
+
+def grlb_init_primitive_device(h, rho_ptr, u_ptr, p_ptr):
+    """Device pointers (ints, e.g. torch tensor .data_ptr()) of FP64 fields on the device."""
+    check(lib().grlb_init_primitive_device(h, rho_ptr, u_ptr, p_ptr))
+
+
+def grlb_step(h, n):
+    check(lib().grlb_step(h, int(n)))
+
+
+def grlb_step_diag(h):
+    check(lib().grlb_step_diag(h))
+
+
+def grlb_diag_read(h) -> dict:
+    d = grlb_diag()
+    check(lib().grlb_diag_read(h, C.byref(d)))
+    return d.as_dict()
+
+
+def grlb_read_conserved(h, N, out=None):
+    if out is None:
+        out = np.empty((5, N), np.float64)
+    check(lib().grlb_read_conserved(h, _dp(out)))
+    return out
+
+
+def grlb_read_primitive(h, N):
+    rho, u, p, T = np.empty(N), np.empty((3, N)), np.empty(N), np.empty(N)
+    check(lib().grlb_read_primitive(h, _dp(rho), _dp(u), _dp(p), _dp(T)))
+    return rho, u, p, T
+
+
+def grlb_save(h) -> np.ndarray:
+    """Checkpoint as a uint8 array (header + stored populations)."""
+    n = C.c_size_t(0)
+    check(lib().grlb_save(h, None, C.byref(n)))
+    buf = np.empty(n.value, np.uint8)
+    check(lib().grlb_save(h, buf.ctypes.data_as(C.c_void_p), C.byref(n)))
+    return buf
+
+
+def grlb_load(h, data):
+    buf = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, bytes) else data)
+    check(lib().grlb_load(h, buf.ctypes.data_as(C.c_void_p), buf.nbytes))
+
+
+def grlb_steps_done(h) -> int:
+    return int(lib().grlb_steps_done(h))
+
+
+def grlb_batch_create(handles, block_x=0, use_graph=1):
+    arr = (C.c_void_p * len(handles))(*[h.value for h in handles])
+    cfg = grlb_batch_config(block_x, 0, use_graph, 0)
+    b = C.c_void_p()
+    check(lib().grlb_batch_create(arr, len(handles), C.byref(cfg), C.byref(b)))
+    return b
+
+
+def grlb_batch_destroy(b):
+    lib().grlb_batch_destroy(b)
+
+
+def grlb_batch_set_stream(b, stream):
+    check(lib().grlb_batch_set_stream(b, stream))
+
+
+def grlb_batch_set_active(b, active):
+    if active is None:
+        check(lib().grlb_batch_set_active(b, None))
+    else:
+        arr = (C.c_int * len(active))(*[int(bool(a)) for a in active])
+        check(lib().grlb_batch_set_active(b, arr))
+
+
+def grlb_batch_step(b, n):
+    check(lib().grlb_batch_step(b, int(n)))
+
+
+# ---- convenience object --------------------------------------------------------------------
+class Domain:
+    """One domain on the current CUDA device (owns its C handle)."""
+
+    def __init__(self, prm, stream=None):
+        self.prm = prm
+        self.N = prm.nx * prm.ny * prm.nz
+        self.h = grlb_create(prm, stream)
+
+    def close(self):
+        if self.h is not None:
+            grlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, u, p):
+        grlb_init_primitive(self.h, rho, u, p)
+
+    def step(self, n=1):
+        grlb_step(self.h, n)
+
+    def step_diag(self):
+        grlb_step_diag(self.h)
+
+    def diag(self):
+        return grlb_diag_read(self.h)
+
+    def conserved(self, out=None):
+        return grlb_read_conserved(self.h, self.N, out)
+
+    def primitive(self):
+        return grlb_read_primitive(self.h, self.N)
+
+    @property
+    def steps(self):
+        return grlb_steps_done(self.h)

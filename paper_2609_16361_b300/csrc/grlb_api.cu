@@ -1,0 +1,581 @@
+// grlb_api.cu -- the C ABI of include/grlb.h: parameter validation and lattice conversion,
+// device memory ownership, launch configuration, readback, checkpoints and batching.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "grlb.h"
+#include "grlb_kernels.h"
+
+using grlb::DomainDev;
+using grlb::NDIAG;
+
+namespace {
+
+thread_local std::string g_err;
+
+grlb_status fail(grlb_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+grlb_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(GRLB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GRLB_CU(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+size_t elem_bytes(int storage) { return storage == GRLB_STORE_F32 ? 4 : 2; }
+
+// Power-of-two storage scale for the 16-bit modes: deviations of field k are divided by a
+// reference magnitude M_k (rho_ref, rho_ref c_ref, E_ref) and multiplied by 2^8 so that
+// typical fluctuations sit well inside the FP16 normal range.  FP32 and BF16 use 1.
+float storage_scale(int storage, double Mk) {
+    if (storage != GRLB_STORE_F16) return 1.0f;
+    const int e = (int)std::lround(std::log2(Mk));
+    return std::ldexp(1.0f, 8 - e);
+}
+
+}  // namespace
+
+struct grlb_domain {
+    grlb_params P;
+    DomainDev D;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    double s = 1.0, gm1 = 0.4, rho_ref = 1.0, p_ref = 1.0, E_ref = 1.0;
+    double* partials = nullptr;
+    int64_t nblocks = 0;
+    double* diag_dev = nullptr;
+    double* diag_host = nullptr;  // pinned, NDIAG doubles
+    int64_t steps = 0;
+    int64_t diag_step = -1;
+    dim3 grid, block;
+    size_t bytes = 0;
+};
+
+extern "C" {
+
+const char* grlb_last_error(void) { return g_err.c_str(); }
+const char* grlb_version(void) { return "grlb 0.1 (sm_103a)"; }
+
+static grlb_status validate(const grlb_params* p) {
+    if (!p) return fail(GRLB_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(GRLB_EINVAL, "nx, ny, nz must be >= 1");
+    const long double N = (long double)p->nx * p->ny * p->nz;
+    if (N >= 2147483647.0L) return fail(GRLB_EINVAL, "nx*ny*nz must be < 2^31");
+    if (p->nz > 65535) return fail(GRLB_EINVAL, "nz must be <= 65535");
+    if (p->bc != GRLB_BC_PERIODIC && p->bc != GRLB_BC_X_DIRICHLET_EQ) return fail(GRLB_EINVAL, "bad bc");
+    if (p->collision != GRLB_COLL_BGK && p->collision != GRLB_COLL_RLB_SENSOR)
+        return fail(GRLB_EINVAL, "bad collision");
+    if (p->storage < GRLB_STORE_F32 || p->storage > GRLB_STORE_BF16) return fail(GRLB_EINVAL, "bad storage");
+    if (!(p->dx > 0) || !(p->dt > 0)) return fail(GRLB_EINVAL, "dx, dt must be > 0");
+    if (!(p->gamma > 1)) return fail(GRLB_EINVAL, "gamma must be > 1");
+    if (!(p->mu_ref >= 0) || !(p->prandtl > 0) || !(p->T_ref > 0) || !(p->T_S >= 0))
+        return fail(GRLB_EINVAL, "bad transport parameters");
+    const double om[3] = {p->omega_rho, p->omega_mom, p->omega_E};
+    for (double w : om)
+        if (!(w > 0 && w <= 2)) return fail(GRLB_EINVAL, "omega must be in (0, 2]");
+    if (!(p->ref_rho > 0) || !(p->ref_p > 0)) return fail(GRLB_EINVAL, "reference state must be positive");
+    if (!(p->rho_min > 0) || !(p->p_min > 0)) return fail(GRLB_EINVAL, "floors must be > 0");
+    if (p->bc == GRLB_BC_X_DIRICHLET_EQ)
+        for (int s = 0; s < 2; ++s) {
+            const double* g = s ? p->right_prim : p->left_prim;
+            if (!(g[0] > 0) || !(g[4] > 0)) return fail(GRLB_EINVAL, "ghost states must have rho, p > 0");
+        }
+    return GRLB_OK;
+}
+
+// Deviation of the +x (sign=+1) or -x (sign=-1) equilibrium population of field k of a
+// primitive state (lattice units) from the reference equilibrium.
+static void ghost_dev(const grlb_domain* d, const double prim[5], int sign, float out[5]) {
+    const double s = d->s, g1 = d->gm1;
+    const double r = prim[0], u[3] = {prim[1] * s, prim[2] * s, prim[3] * s}, p = prim[4] * s * s;
+    const double m[3] = {r * u[0], r * u[1], r * u[2]};
+    const double ke = 0.5 * (m[0] * u[0] + m[1] * u[1] + m[2] * u[2]);
+    const double dQ[5] = {r - d->rho_ref, m[0], m[1], m[2], (p - d->p_ref) / g1 + ke};
+    const double E = d->E_ref + dQ[4];
+    double Px[5];  // x component of Phi^adv - J_ref
+    Px[0] = m[0];
+    Px[1] = m[0] * u[0] + (p - d->p_ref);
+    Px[2] = m[1] * u[0];
+    Px[3] = m[2] * u[0];
+    Px[4] = (E + p) * u[0];
+    for (int k = 0; k < 5; ++k) out[k] = (float)(0.125 * dQ[k] + sign * 0.5 * Px[k]);
+}
+
+static void fill_domain_dev(grlb_domain* d) {
+    const grlb_params& p = d->P;
+    DomainDev& D = d->D;
+    const double s = p.dt / p.dx;
+    d->s = s;
+    d->gm1 = p.gamma - 1.0;
+    d->rho_ref = p.ref_rho;
+    d->p_ref = p.ref_p * s * s;
+    d->E_ref = d->p_ref / d->gm1;
+    D.plane = (int64_t)p.nx * p.ny * p.nz;
+    D.nx = p.nx;
+    D.ny = p.ny;
+    D.nz = p.nz;
+    D.bc = p.bc;
+    D.cur = 0;
+    D.tile_x = 128;
+    D.gm1 = (float)d->gm1;
+    const double mu_L = p.mu_ref * p.dt / (p.dx * p.dx);
+    const double cp = p.gamma / (p.gamma - 1.0);
+    D.mu_ref = (float)mu_L;
+    D.kap_ref = (float)(mu_L * cp / p.prandtl);
+    D.inv_T_ref = (float)(1.0 / (p.T_ref * s * s));
+    D.T_S = (float)p.T_S;
+    D.sutherland = p.sutherland ? 1 : 0;
+    const double om[3] = {p.omega_rho, p.omega_mom, p.omega_E};
+    for (int r = 0; r < 3; ++r) {
+        D.omega[r] = (float)om[r];
+        D.omega_red[r] = (float)std::max(om[r] - p.omega_min, 0.0);
+    }
+    D.gain = (float)p.sensor_gain;
+    D.J_min = (float)p.J_min;
+    D.rho_min = (float)p.rho_min;
+    D.p_min = (float)(p.p_min * s * s);
+    D.rho_ref = (float)d->rho_ref;
+    D.p_ref = (float)d->p_ref;
+    D.E_ref = (float)d->E_ref;
+    if (p.bc == GRLB_BC_X_DIRICHLET_EQ) {
+        ghost_dev(d, p.left_prim, +1, D.ghostL);
+        ghost_dev(d, p.right_prim, -1, D.ghostR);
+    } else {
+        for (int k = 0; k < 5; ++k) D.ghostL[k] = D.ghostR[k] = 0.0f;
+    }
+    const double c_ref = std::sqrt(p.gamma * d->p_ref / d->rho_ref);
+    const double M[5] = {d->rho_ref, d->rho_ref * c_ref, d->rho_ref * c_ref, d->rho_ref * c_ref, d->E_ref};
+    for (int k = 0; k < 5; ++k) {
+        D.enc[k] = storage_scale(p.storage, M[k]);
+        D.dec[k] = 1.0f / D.enc[k];
+    }
+}
+
+static void choose_launch(grlb_domain* d) {
+    int bx = 128;
+    while (bx > 32 && bx / 2 >= d->P.nx) bx /= 2;
+    int by = 128 / bx;
+    while (by > 1 && by / 2 >= d->P.ny) by /= 2;
+    d->block = dim3(bx, by, 1);
+    d->grid = dim3((d->P.nx + bx - 1) / bx, (d->P.ny + by - 1) / by, d->P.nz);
+    d->nblocks = (int64_t)d->grid.x * d->grid.y * d->grid.z;
+}
+
+size_t grlb_bytes_for(const grlb_params* p) {
+    if (validate(p) != GRLB_OK) return 0;
+    grlb_domain tmp;
+    tmp.P = *p;
+    choose_launch(&tmp);
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    return 2 * 35 * N * elem_bytes(p->storage) + (size_t)tmp.nblocks * NDIAG * 8 + NDIAG * 8;
+}
+
+grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
+    if (!out) return fail(GRLB_EINVAL, "out is NULL");
+    *out = nullptr;
+    grlb_status st = validate(p);
+    if (st != GRLB_OK) return st;
+    grlb_domain* d = new (std::nothrow) grlb_domain();
+    if (!d) return fail(GRLB_ENOMEM, "host allocation failed");
+    d->P = *p;
+    d->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&d->device);
+    fill_domain_dev(d);
+    choose_launch(d);
+    const size_t N = (size_t)d->D.plane;
+    const size_t pop_bytes = 35 * N * elem_bytes(p->storage);
+    cudaError_t e = cudaSuccess;
+    d->D.buf[0] = d->D.buf[1] = nullptr;
+    e = cudaMalloc(&d->D.buf[0], pop_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d->D.buf[1], pop_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d->partials, (size_t)d->nblocks * NDIAG * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d->diag_dev, NDIAG * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&d->diag_host, NDIAG * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        grlb_destroy(d);
+        return fail(e == cudaErrorMemoryAllocation ? GRLB_ENOMEM : GRLB_ECUDA,
+                    std::string("grlb_create: ") + cudaGetErrorString(e));
+    }
+    d->bytes = 2 * pop_bytes + (size_t)d->nblocks * NDIAG * 8 + NDIAG * 8;
+    for (int k = 0; k < NDIAG; ++k) d->diag_host[k] = 0.0;
+    *out = d;
+    return GRLB_OK;
+}
+
+void grlb_destroy(grlb_domain* d) {
+    if (!d) return;
+    if (d->stream) cudaStreamSynchronize(d->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(d->D.buf[0]);
+    cudaFree(d->D.buf[1]);
+    cudaFree(d->partials);
+    cudaFree(d->diag_dev);
+    cudaFreeHost(d->diag_host);
+    delete d;
+}
+
+grlb_status grlb_set_stream(grlb_domain* d, void* stream) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    d->stream = static_cast<cudaStream_t>(stream);
+    return GRLB_OK;
+}
+
+size_t grlb_device_bytes(const grlb_domain* d) { return d ? d->bytes : 0; }
+int64_t grlb_steps_done(const grlb_domain* d) { return d ? d->steps : -1; }
+
+grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double* u, const double* p) {
+    if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive: NULL argument");
+    const size_t N = (size_t)d->D.plane;
+    double* stage = nullptr;
+    GRLB_CU(cudaMallocAsync(&stage, 5 * N * sizeof(double), d->stream));
+    cudaError_t e = cudaMemcpyAsync(stage, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) {
+        d->D.cur = 0;
+        e = grlb::launch_init(d->D, d->P.storage, d->D.buf[0], stage, stage + N, stage + 4 * N, d->s,
+                              d->gm1, d->rho_ref, d->p_ref, d->stream);
+    }
+    cudaError_t e2 = cudaFreeAsync(stage, d->stream);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grlb_init_primitive");
+    d->steps = 0;
+    d->diag_step = -1;
+    return GRLB_OK;
+}
+
+grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const double* u, const double* p) {
+    if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive_device: NULL argument");
+    d->D.cur = 0;
+    cudaError_t e = grlb::launch_init(d->D, d->P.storage, d->D.buf[0], rho, u, p, d->s, d->gm1, d->rho_ref,
+                                      d->p_ref, d->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grlb_init_primitive_device");
+    d->steps = 0;
+    d->diag_step = -1;
+    return GRLB_OK;
+}
+
+static grlb_status sweep_once(grlb_domain* d, bool diag) {
+    const int c = d->D.cur;
+    cudaError_t e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, d->D.buf[c], d->D.buf[c ^ 1],
+                                       diag, d->partials, d->grid, d->block, d->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    d->D.cur = c ^ 1;
+    d->steps += 1;
+    return GRLB_OK;
+}
+
+grlb_status grlb_step(grlb_domain* d, int nsteps) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
+    for (int n = 0; n < nsteps; ++n) {
+        grlb_status st = sweep_once(d, false);
+        if (st != GRLB_OK) return st;
+    }
+    return GRLB_OK;
+}
+
+grlb_status grlb_step_diag(grlb_domain* d) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    grlb_status st = sweep_once(d, true);
+    if (st != GRLB_OK) return st;
+    GRLB_CU(grlb::launch_diag_finalize(d->partials, d->nblocks, d->diag_dev, d->stream));
+    GRLB_CU(cudaMemcpyAsync(d->diag_host, d->diag_dev, NDIAG * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    d->diag_step = d->steps;
+    return GRLB_OK;
+}
+
+grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out) {
+    if (!d || !out) return fail(GRLB_EINVAL, "grlb_diag_read: NULL argument");
+    if (d->diag_step < 0) return fail(GRLB_ESTATE, "no diagnostic sweep since init");
+    GRLB_CU(cudaStreamSynchronize(d->stream));
+    const double* h = d->diag_host;
+    const double N = (double)d->D.plane;
+    const double Qref[5] = {d->rho_ref, 0.0, 0.0, 0.0, d->E_ref};
+    for (int k = 0; k < 5; ++k) out->totals[k] = N * Qref[k] + h[k];
+    out->ke = h[5];
+    out->eps_s = h[6];
+    out->eps_d = h[7];
+    out->rho_min = h[8];
+    out->p_min = h[9];
+    out->n_floor = (int64_t)h[10];
+    out->n_nan = (int64_t)h[11];
+    out->n_sensor = (int64_t)h[12];
+    out->step = d->diag_step;
+    out->s = d->s;
+    out->ncells = d->D.plane;
+    return GRLB_OK;
+}
+
+grlb_status grlb_read_conserved(grlb_domain* d, double* out) {
+    if (!d || !out) return fail(GRLB_EINVAL, "grlb_read_conserved: NULL argument");
+    const size_t N = (size_t)d->D.plane;
+    double* stage = nullptr;
+    GRLB_CU(cudaMallocAsync(&stage, 5 * N * sizeof(double), d->stream));
+    cudaError_t e = grlb::launch_conserved(d->D, d->P.storage, d->D.buf[d->D.cur], stage, d->s, d->rho_ref,
+                                           d->E_ref, d->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, stage, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, d->stream);
+    cudaError_t e2 = cudaFreeAsync(stage, d->stream);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grlb_read_conserved");
+    return GRLB_OK;
+}
+
+grlb_status grlb_read_primitive(grlb_domain* d, double* rho, double* u, double* p, double* T) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    const size_t N = (size_t)d->D.plane;
+    std::vector<double> Q;
+    try {
+        Q.resize(5 * N);
+    } catch (...) {
+        return fail(GRLB_ENOMEM, "host allocation failed");
+    }
+    grlb_status st = grlb_read_conserved(d, Q.data());
+    if (st != GRLB_OK) return st;
+    const double g1 = d->gm1;
+    for (size_t c = 0; c < N; ++c) {
+        const double r = Q[c];
+        const double ux = Q[N + c] / r, uy = Q[2 * N + c] / r, uz = Q[3 * N + c] / r;
+        const double pp = g1 * (Q[4 * N + c] - 0.5 * r * (ux * ux + uy * uy + uz * uz));
+        if (rho) rho[c] = r;
+        if (u) { u[c] = ux; u[N + c] = uy; u[2 * N + c] = uz; }
+        if (p) p[c] = pp;
+        if (T) T[c] = pp / r;
+    }
+    return GRLB_OK;
+}
+
+namespace {
+struct SaveHeader {
+    uint64_t magic;
+    int64_t steps;
+    int64_t N;
+    int32_t storage, pad;
+};
+const uint64_t kMagic = 0x3142524c47ULL;  // "GLRB1"
+}  // namespace
+
+grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
+    if (!d || !bytes) return fail(GRLB_EINVAL, "grlb_save: NULL argument");
+    const size_t pop = 35 * (size_t)d->D.plane * elem_bytes(d->P.storage);
+    const size_t need = sizeof(SaveHeader) + pop;
+    if (!buf) {
+        *bytes = need;
+        return GRLB_OK;
+    }
+    if (*bytes < need) return fail(GRLB_EINVAL, "grlb_save: buffer too small");
+    SaveHeader h{kMagic, d->steps, d->D.plane, d->P.storage, 0};
+    std::memcpy(buf, &h, sizeof h);
+    GRLB_CU(cudaMemcpyAsync(static_cast<char*>(buf) + sizeof h, d->D.buf[d->D.cur], pop, cudaMemcpyDeviceToHost,
+                            d->stream));
+    GRLB_CU(cudaStreamSynchronize(d->stream));
+    *bytes = need;
+    return GRLB_OK;
+}
+
+grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
+    if (!d || !buf) return fail(GRLB_EINVAL, "grlb_load: NULL argument");
+    const size_t pop = 35 * (size_t)d->D.plane * elem_bytes(d->P.storage);
+    if (bytes < sizeof(SaveHeader) + pop) return fail(GRLB_EINVAL, "grlb_load: buffer too small");
+    SaveHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != kMagic || h.N != d->D.plane || h.storage != d->P.storage)
+        return fail(GRLB_EINVAL, "grlb_load: checkpoint does not match this domain");
+    d->D.cur = 0;
+    GRLB_CU(cudaMemcpyAsync(d->D.buf[0], static_cast<const char*>(buf) + sizeof h, pop, cudaMemcpyHostToDevice,
+                            d->stream));
+    GRLB_CU(cudaStreamSynchronize(d->stream));
+    d->steps = h.steps;
+    d->diag_step = -1;
+    return GRLB_OK;
+}
+
+}  // extern "C"
+
+// =========================================================================================
+// Batching: one launch per step over the concatenated tile table of all active domains.
+// =========================================================================================
+struct grlb_batch {
+    std::vector<grlb_domain*> doms;
+    std::vector<int> active;
+    grlb_batch_config cfg{};
+    cudaStream_t stream = nullptr;
+    DomainDev* d_doms = nullptr;
+    DomainDev* h_doms = nullptr;  // pinned staging
+    // tiles grouped by (storage, collision): group g occupies [off[g], off[g+1])
+    int4* d_tiles = nullptr;
+    int ntiles = 0;
+    int group_off[7] = {0};
+    cudaGraphExec_t graph = nullptr;
+    bool dirty = true;
+};
+
+namespace {
+int group_of(const grlb_params& p) { return p.storage * 2 + p.collision; }
+
+int tile_width(const grlb_batch* b, const grlb_domain* d) {
+    int tx = b->cfg.block_x > 0 ? b->cfg.block_x : 128;
+    while (tx > 32 && tx / 2 >= d->P.nx) tx /= 2;
+    return tx;
+}
+
+grlb_status rebuild_tiles(grlb_batch* b) {
+    std::vector<int4> groups[6];
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        if (!b->active[i]) continue;
+        const grlb_domain* d = b->doms[i];
+        const int tx = tile_width(b, d);
+        const int ty = 128 / tx;
+        std::vector<int4>& g = groups[group_of(d->P)];
+        for (int z = 0; z < d->P.nz; ++z)
+            for (int y = 0; y < d->P.ny; y += ty)
+                for (int x = 0; x < d->P.nx; x += tx) g.push_back(make_int4((int)i, x, y, z));
+    }
+    std::vector<int4> all;
+    for (int g = 0; g < 6; ++g) {
+        b->group_off[g] = (int)all.size();
+        all.insert(all.end(), groups[g].begin(), groups[g].end());
+    }
+    b->group_off[6] = (int)all.size();
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    b->ntiles = (int)all.size();
+    if (b->ntiles > 0) {
+        GRLB_CU(cudaMalloc(&b->d_tiles, all.size() * sizeof(int4)));
+        GRLB_CU(cudaMemcpy(b->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->dirty = false;
+    return GRLB_OK;
+}
+
+cudaError_t enqueue_batch_step(grlb_batch* b, int parity) {
+    for (int g = 0; g < 6; ++g) {
+        const int n = b->group_off[g + 1] - b->group_off[g];
+        if (n == 0) continue;
+        cudaError_t e = grlb::launch_batch_sweep(g / 2, g % 2, b->d_doms, b->d_tiles + b->group_off[g], n, 128,
+                                                 parity, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_batch_config* cfg, grlb_batch** out) {
+    if (!out || !domains || n <= 0) return fail(GRLB_EINVAL, "grlb_batch_create: bad arguments");
+    *out = nullptr;
+    grlb_batch* b = new (std::nothrow) grlb_batch();
+    if (!b) return fail(GRLB_ENOMEM, "host allocation failed");
+    if (cfg) b->cfg = *cfg;
+    const int bx = b->cfg.block_x;
+    if (bx != 0 && bx != 32 && bx != 64 && bx != 128) {
+        delete b;
+        return fail(GRLB_EINVAL, "block_x must be 32, 64 or 128");
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!domains[i]) {
+            delete b;
+            return fail(GRLB_EINVAL, "NULL domain in batch");
+        }
+        b->doms.push_back(domains[i]);
+        b->active.push_back(1);
+    }
+    b->stream = domains[0]->stream;
+    cudaError_t e = cudaMalloc(&b->d_doms, n * sizeof(DomainDev));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_doms, n * sizeof(DomainDev));
+    if (e != cudaSuccess) {
+        grlb_batch_destroy(b);
+        return cuda_fail(e, "grlb_batch_create");
+    }
+    grlb_status st = rebuild_tiles(b);
+    if (st != GRLB_OK) {
+        grlb_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return GRLB_OK;
+}
+
+void grlb_batch_destroy(grlb_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_doms);
+    cudaFreeHost(b->h_doms);
+    cudaFree(b->d_tiles);
+    delete b;
+}
+
+grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream) {
+    if (!b) return fail(GRLB_EINVAL, "batch is NULL");
+    b->stream = static_cast<cudaStream_t>(stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    return GRLB_OK;
+}
+
+grlb_status grlb_batch_set_active(grlb_batch* b, const int* active) {
+    if (!b) return fail(GRLB_EINVAL, "batch is NULL");
+    for (size_t i = 0; i < b->doms.size(); ++i) b->active[i] = active ? (active[i] != 0) : 1;
+    return rebuild_tiles(b);
+}
+
+grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
+    if (!b) return fail(GRLB_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0 || b->ntiles == 0) return GRLB_OK;
+    // The staging records are rewritten below: wait for the previous call's copy to finish.
+    GRLB_CU(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        b->h_doms[i] = b->doms[i]->D;
+        b->h_doms[i].tile_x = tile_width(b, b->doms[i]);
+    }
+    GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms, b->doms.size() * sizeof(DomainDev), cudaMemcpyHostToDevice,
+                            b->stream));
+    int done = 0;
+    if (b->cfg.use_graph && b->stream != nullptr && nsteps >= 2) {
+        if (!b->graph) {
+            cudaGraph_t g;
+            GRLB_CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_batch_step(b, 0);
+            if (e == cudaSuccess) e = enqueue_batch_step(b, 1);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        for (; done + 2 <= nsteps; done += 2) GRLB_CU(cudaGraphLaunch(b->graph, b->stream));
+    }
+    for (; done < nsteps; ++done) GRLB_CU(enqueue_batch_step(b, done & 1));
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        if (!b->active[i]) continue;
+        grlb_domain* d = b->doms[i];
+        d->D.cur ^= (nsteps & 1);
+        d->steps += nsteps;
+    }
+    return GRLB_OK;
+}
+
+}  // extern "C"

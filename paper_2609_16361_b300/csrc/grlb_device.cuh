@@ -1,0 +1,301 @@
+// grlb_device.cuh -- device side of the fused stream-and-collide sweep (sm_103a).
+//
+// One thread updates one cell: pull the 35 populations f_{k,i}(x - c_i) (exact streaming,
+// Sec. 2.2), run the in-collide update of Algorithm 1 in FP32 registers, write the 35
+// post-collision populations at x into the other buffer.  Nothing but populations touches
+// HBM: the reconstructed gradients, stress, heat flux and the sensor chi stay in registers
+// (Sec. 2.5 "cell-local").
+//
+// Storage is the equilibrium shift of Sec. 2.2: the buffers hold d_{k,i} = f_{k,i} -
+// w_i (Q_ref,k + c_i . J_ref,k / cs^2), the deviation from the equilibrium of a reference
+// state at rest (Q_ref = (rho_ref, 0, 0, 0, p_ref/(gamma-1)), J_ref,m_j = p_ref e_j).  All
+// moment arithmetic is done on deviations (dQ, dJ, dp) so the FP32 significand is spent on
+// the fluctuation, not the mean.  FP16/BF16 storage multiplies the deviation by a per-field
+// power of two before rounding (RN-even) and divides after loading.
+//
+// D3Q7 links i = 0, +x, -x, +y, -y, +z, -z; w0 = 1/4, w1..6 = 1/8; cs^2 = 1/4.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace grlb {
+
+constexpr int NF = 5;
+constexpr int NQ = 7;
+constexpr int NP = NF * NQ;
+constexpr int NDIAG = 13;  // per-block partial record of the diagnostic sweep
+
+enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
+enum Collision { C_BGK = 0, C_RLB = 1 };
+
+// Per-domain lattice-unit constants.  Plain old data: passed by value as a kernel
+// parameter for single-domain launches, read from a device array by the batched sweep.
+struct DomainDev {
+    void* buf[2];          // population buffers A, B (35 planes each)
+    int64_t plane;         // elements per population plane = nx*ny*nz
+    int32_t nx, ny, nz, bc;
+    int32_t cur;           // index of the buffer holding the current state (batched sweep)
+    int32_t tile_x;        // cells along x per CTA in the batched sweep (divides blockDim.x)
+    float gm1;             // gamma - 1
+    float mu_ref, kap_ref; // lattice-unit transport at T_ref
+    float inv_T_ref, T_S;  // Sutherland law: mu = mu_ref (1+T_S) t^{3/2}/(t+T_S), t = T/T_ref
+    int32_t sutherland;
+    float omega[3];        // rho, momentum, energy (nominal 1/tau_LB)
+    float omega_red[3];    // max(omega_k - omega_min, 0): chi-scaled reduction (Listing 2)
+    float gain, J_min, rho_min, p_min;
+    float rho_ref, p_ref, E_ref;
+    float ghostL[5];       // deviation of f_{k,+x} in the x = -1 ghost (X_DIRICHLET_EQ)
+    float ghostR[5];       // deviation of f_{k,-x} in the x = nx ghost
+    float dec[5];          // per-field storage scale: value = stored * dec[k]
+    float enc[5];          // stored = value * enc[k]
+};
+
+// ---- storage traits ----------------------------------------------------------------------
+template <int S> struct Store;
+template <> struct Store<S_F32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { __stcs(p, v); }
+};
+template <> struct Store<S_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<S_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+        return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+        *p = __float2bfloat16_rn(v);
+    }
+};
+
+// Per-cell diagnostic values (FP32, reduced later in FP64).
+struct CellDiag {
+    float dQ[5];           // deviations of the conserved moments from Q_ref
+    float ke, eps_s, eps_d;
+    float rho_raw, p_raw;  // unfloored
+    int floored, nan, sensor;
+};
+
+// ---- Algorithm 1 on one cell --------------------------------------------------------------
+// In: d[k][i] = pulled deviations.  Out: o[k][i] = post-collision deviations.
+// For the regularized collision the outputs depend only on (dQ_k, J*_k), so d may alias o.
+template <int COLL, bool DIAG>
+__device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF][NQ],
+                                        float (&o)[NF][NQ], CellDiag* cd) {
+    // moments (Alg. 1): dQ_k = sum_i d_ki, dJ_k = sum_i d_ki c_i
+    float dQ[NF], dJ[NF][3];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dQ[k] = ((d[k][0] + d[k][1]) + (d[k][2] + d[k][3])) + ((d[k][4] + d[k][5]) + d[k][6]);
+        dJ[k][0] = d[k][1] - d[k][2];
+        dJ[k][1] = d[k][3] - d[k][4];
+        dJ[k][2] = d[k][5] - d[k][6];
+    }
+    const float gm1 = D.gm1;
+    // primitives with positivity floors (Alg. 1); Q_k themselves stay unfloored
+    const float rho_raw = D.rho_ref + dQ[0];
+    const float rho = fmaxf(rho_raw, D.rho_min);
+    const float irho = 1.0f / rho;
+    const float m0 = dQ[1], m1 = dQ[2], m2 = dQ[3];
+    const float u0 = m0 * irho, u1 = m1 * irho, u2 = m2 * irho;
+    const float uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const float ke = 0.5f * (m0 * u0 + m1 * u1 + m2 * u2);
+    // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
+    float dp = gm1 * (dQ[4] - ke);
+    const float p_raw = D.p_ref + dp;
+    float p = p_raw;
+    if (p_raw < D.p_min) { p = D.p_min; dp = D.p_min - D.p_ref; }
+    const float T = p * irho;
+    const float E = D.E_ref + dQ[4];
+    // transport (Listing 1)
+    float fac = 1.0f;
+    if (D.sutherland) {
+        const float t = T * D.inv_T_ref;
+        fac = (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
+    }
+    const float mu = D.mu_ref * fac;
+    const float kap = D.kap_ref * fac;
+
+    // non-equilibrium first moments J - Phi^adv (Eq. gradrecon), in deviation form
+    const float Hp = E + p;  // (E + p)
+    float nA[NF][3];
+    nA[0][0] = dJ[0][0] - m0;
+    nA[0][1] = dJ[0][1] - m1;
+    nA[0][2] = dJ[0][2] - m2;
+    const float mm[3] = {m0, m1, m2};
+    const float uv[3] = {u0, u1, u2};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nA[1 + j][c] = dJ[1 + j][c] - mm[j] * uv[c] - (j == c ? dp : 0.0f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nA[4][c] = dJ[4][c] - Hp * uv[c];
+
+    // direct reconstruction grad Q~ = -omega Pi / cs^2 (cs^-2 = 4)
+    const float w4r = -4.0f * D.omega[0], w4m = -4.0f * D.omega[1], w4e = -4.0f * D.omega[2];
+    float gr[3], G[3][3], ge[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        gr[c] = w4r * nA[0][c];  // mass row of M is zero: grad rho passes through
+        ge[c] = w4e * nA[4][c];
+    }
+    // momentum block (Eq. cnsfM row 2, Sec. 2.4): (I + b S) grad m = g~_m + b S(u (x) grad rho)
+    // with b = omega_m mu / (cs^2 rho); solved in closed form: the antisymmetric part and the
+    // trace pass through, the symmetric-deviatoric part is divided by 1 + beta, beta = 2b.
+    const float a_mu = mu * irho;
+    const float b = 4.0f * D.omega[1] * a_mu;
+    const float ugr = u0 * gr[0] + u1 * gr[1] + u2 * gr[2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            G[j][c] = w4m * nA[1 + j][c] +
+                      b * (uv[j] * gr[c] + uv[c] * gr[j] - (j == c ? (2.0f / 3.0f) * ugr : 0.0f));
+    {
+        const float trG3 = (G[0][0] + G[1][1] + G[2][2]) * (1.0f / 3.0f);
+        const float kdamp = (2.0f * b) / (1.0f + 2.0f * b);  // beta / (1 + beta)
+        float Dv[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Dv[j][c] = 0.5f * (G[j][c] + G[c][j]) - (j == c ? trG3 : 0.0f);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) G[j][c] -= kdamp * Dv[j][c];  // G := grad m
+    }
+    // energy row (Eq. cnsfE): scalar division with the corrected upstream gradients
+    const float kr = kap * irho;
+    float gmTu[3], Su[3];
+    {
+        const float trm23 = (2.0f / 3.0f) * (G[0][0] + G[1][1] + G[2][2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            gmTu[c] = G[0][c] * u0 + G[1][c] * u1 + G[2][c] * u2;  // ((grad m)^T u)_c
+            // (S(grad m) u)_c = sum_j (G_cj + G_jc) u_j - 2/3 tr(G) u_c
+            Su[c] = (G[c][0] + G[0][c]) * u0 + (G[c][1] + G[1][c]) * u1 +
+                    (G[c][2] + G[2][c]) * u2 - trm23 * uv[c];
+        }
+    }
+    {
+        const float cT = kr * (T - 0.5f * gm1 * uu);
+        const float w4 = 4.0f * D.omega[2];
+        const float inv = 1.0f / (1.0f + w4 * gm1 * kr);
+        const float ugr3 = (1.0f / 3.0f) * ugr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float MEr = a_mu * (uu * gr[c] + ugr3 * uv[c]) + cT * gr[c];
+            const float MEm = -a_mu * Su[c] + gm1 * kr * gmTu[c];
+            ge[c] = (ge[c] + w4 * (MEr + MEm)) * inv;
+        }
+    }
+    // chain rule (Sec. 2.4): grad u and grad T
+    float gu[3][3], gT[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gu[j][c] = (G[j][c] - uv[j] * gr[c]) * irho;
+    {
+        const float cr = (0.5f * gm1 * uu - T) * irho;
+        const float cg = gm1 * irho;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gT[c] = cg * (ge[c] - gmTu[c]) + cr * gr[c];
+    }
+    const float theta = gu[0][0] + gu[1][1] + gu[2][2];
+    // compression sensor (Listing 2): s = -div u / cs, cs = 1/2
+    float chi = 0.0f;
+    if (COLL == C_RLB) {
+        const float s = -2.0f * theta;
+        if (theta < 0.0f && s > D.J_min) chi = fminf(fmaxf(D.gain * s, 0.0f), 1.0f);
+    }
+    // Newtonian stress and Fourier flux (Eq. system), full flux in deviation form:
+    // Phi_rho = m; Phi_m_j - p_ref e_j = m_j u + dp e_j - tau_j; Phi_E = (E+p) u - tau u + q
+    const float t23 = (2.0f / 3.0f) * theta;
+    float tau[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tau[j][c] = mu * (gu[j][c] + gu[c][j] - (j == c ? t23 : 0.0f));
+    float Pd[NF][3];  // Phi_k - J_ref,k
+    float Fd[NF][3];  // Phi^diff_k
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Pd[0][c] = mm[c];
+        Fd[0][c] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Fd[1 + j][c] = -tau[j][c];
+            Pd[1 + j][c] = mm[j] * uv[c] + (j == c ? dp : 0.0f) - tau[j][c];
+        }
+        const float tu = tau[c][0] * u0 + tau[c][1] * u1 + tau[c][2] * u2;
+        Fd[4][c] = -tu - kap * gT[c];
+        Pd[4][c] = Hp * uv[c] + Fd[4][c];
+    }
+
+    if (COLL == C_RLB) {
+        // regularized collision with reduced rate (Sec. 2.5):
+        // f* = f^eq + (1 - omega_h) r, r = first-moment part of f - f^eq, so the outgoing
+        // set is w_i (Q + c_i . J* / cs^2) with J* = Phi + (1 - omega_h)(J - Phi).
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
+            const float omh = D.omega[r] - chi * D.omega_red[r];
+            const float onem = 1.0f - omh;
+            float js[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) js[c] = Pd[k][c] + onem * (nA[k][c] - Fd[k][c]);
+            const float q0 = 0.25f * dQ[k];
+            const float q1 = 0.125f * dQ[k];
+            o[k][0] = q0;
+            o[k][1] = q1 + 0.5f * js[0];
+            o[k][2] = q1 - 0.5f * js[0];
+            o[k][3] = q1 + 0.5f * js[1];
+            o[k][4] = q1 - 0.5f * js[1];
+            o[k][5] = q1 + 0.5f * js[2];
+            o[k][6] = q1 - 0.5f * js[2];
+        }
+    } else {
+        // BGK (Sec. 2.2): f* = f + omega (f^eq - f)
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
+            const float om = D.omega[r];
+            const float q1 = 0.125f * dQ[k];
+            float fe[NQ];
+            fe[0] = 0.25f * dQ[k];
+            fe[1] = q1 + 0.5f * Pd[k][0];
+            fe[2] = q1 - 0.5f * Pd[k][0];
+            fe[3] = q1 + 0.5f * Pd[k][1];
+            fe[4] = q1 - 0.5f * Pd[k][1];
+            fe[5] = q1 + 0.5f * Pd[k][2];
+            fe[6] = q1 - 0.5f * Pd[k][2];
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) o[k][i] = fmaf(om, fe[i] - d[k][i], d[k][i]);
+        }
+    }
+
+    if (DIAG) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) cd->dQ[k] = dQ[k];
+        cd->ke = ke;
+        const float wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
+        cd->eps_s = mu * (wx * wx + wy * wy + wz * wz);
+        cd->eps_d = (4.0f / 3.0f) * mu * theta * theta;
+        cd->rho_raw = rho_raw;
+        cd->p_raw = p_raw;
+        cd->floored = (rho_raw < D.rho_min) || (p_raw < D.p_min);
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) fin = fin && isfinite(dQ[k]);
+        cd->nan = !fin;
+        cd->sensor = chi > 0.0f;
+    }
+}
+
+}  // namespace grlb

@@ -1,0 +1,20 @@
+// grlb_kernels.h -- host-side launchers of the sweep kernels (internal to libgrlb).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grlb_device.cuh"
+
+namespace grlb {
+cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, const void* fin, void* fout,
+                         bool diag, double* partials, dim3 grid, dim3 block, cudaStream_t st);
+cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, const int4* tiles,
+                               int ntiles, int threads, int parity, cudaStream_t st);
+cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double* out,
+                                 cudaStream_t st);
+cudaError_t launch_init(const DomainDev& D, int storage, void* fout, const double* rho,
+                        const double* u, const double* p, double s, double gm1, double rho_ref,
+                        double p_ref, cudaStream_t st);
+cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, double* out,
+                             double s, double rho_ref, double E_ref, cudaStream_t st);
+}  // namespace grlb

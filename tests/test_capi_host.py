@@ -1,0 +1,77 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for sm_103a, loads, exports
+every entry point include/grlb.h declares, its struct layouts match the Python binding, and
+parameter validation rejects bad input."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2609_16361_b300 import capi, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "grlb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(grlb_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    L = capi.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), f"{n} missing from libgrlb.so"
+    assert set(capi.exported_symbols()) >= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", capi.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}$", out, re.M), n
+    assert b"sm_103a" in capi.lib().grlb_version()
+
+
+def test_struct_layouts_match_header(tmp_path):
+    src = tmp_path / "lay.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "grlb.h"
+int main(void){
+ printf("%zu %zu %zu %zu %zu %zu\n", sizeof(grlb_params), offsetof(grlb_params, T_S),
+        offsetof(grlb_params, right_prim), sizeof(grlb_diag), offsetof(grlb_diag, n_floor),
+        sizeof(grlb_batch_config));
+ return 0;}
+''')
+    exe = tmp_path / "lay"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [C.sizeof(capi.grlb_params), capi.grlb_params.T_S.offset,
+                    capi.grlb_params.right_prim.offset, C.sizeof(capi.grlb_diag),
+                    capi.grlb_diag.n_floor.offset, C.sizeof(capi.grlb_batch_config)]
+
+
+def test_parameter_validation_without_device():
+    good = inputs.tgv3d(32).params
+    assert capi.grlb_bytes_for(good) == pytest.approx(2 * 35 * 32 ** 3 * 4, rel=0.05)
+    f16 = good.replace(storage=inputs.STORE_F16)
+    assert capi.grlb_bytes_for(f16) < capi.grlb_bytes_for(good) * 0.6
+    bad = [good.replace(nx=0), good.replace(omega_mom=2.5), good.replace(dt=-1.0),
+           good.replace(gamma=1.0), good.replace(storage=7), good.replace(bc=3),
+           good.replace(ref_p=0.0), good.replace(nx=2048, ny=2048, nz=1024)]
+    for b in bad:
+        assert capi.grlb_bytes_for(b) == 0
+    h = C.c_void_p()
+    st = capi.lib().grlb_create(C.byref(capi.to_params(good.replace(nx=0))), None, C.byref(h))
+    assert st == -1 and b"nx" in capi.lib().grlb_last_error()
+
+
+@pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
+def test_create_fails_cleanly_without_device():
+    h = C.c_void_p()
+    st = capi.lib().grlb_create(C.byref(capi.to_params(inputs.tgv3d(8).params)), None, C.byref(h))
+    assert st in (-2, -3) and not h.value
+    assert len(capi.lib().grlb_last_error()) > 0

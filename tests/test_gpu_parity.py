@@ -1,0 +1,214 @@
+"""GPU parity of the CUDA sweep (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated for FP32 populations): relative L-infinity of every conserved field at
+most 1e-5 after 100 steps on smooth fields, relative L1 at most 1e-4 across shocks, totals
+conserved to 1e-6 relative.  Relative norms use per-field denominators (max|rho|, max|m| over
+the three components, max|E|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_16361_b300 import capi, inputs
+from tests.common import decode_populations, rel_l1, rel_linf, run_oracle, CI
+
+pytestmark = pytest.mark.gpu
+
+LINF_SMOOTH = 1e-5
+L1_SHOCK = 1e-4
+TOTALS = 1e-6
+
+
+def gpu_run(case, steps, diag_last=False):
+    d = capi.Domain(case.params)
+    d.init(case.rho, case.u, case.p)
+    if diag_last:
+        d.step(steps - 1)
+        d.step_diag()
+    else:
+        d.step(steps)
+    return d
+
+
+# ---- smooth fields: rel Linf <= 1e-5 after 100 steps ------------------------------------
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_BGK])
+def test_uniform_state_stays_uniform(collision):
+    c = inputs.uniform(33, 5, 3, collision=collision)
+    d = gpu_run(c, 100)
+    Q = d.conserved()
+    o = run_oracle(c, 100)
+    assert np.all(rel_linf(Q, o.conserved()) <= LINF_SMOOTH)
+    assert np.abs(Q[0] - 1.0).max() < 1e-6
+
+
+def test_taylor_green_32_rlb_sutherland():
+    c = inputs.tgv3d(32)
+    d = gpu_run(c, 100)
+    o = run_oracle(c, 100)
+    err = rel_linf(d.conserved(), o.conserved())
+    assert np.all(err <= LINF_SMOOTH), err
+
+
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_BGK])
+def test_random_smooth_ragged_tiles(collision):
+    # 40 x 21 x 7: CTA tiles of 64 x 2 leave a ragged x tail and a ragged y row
+    c = inputs.random_smooth(40, 21, 7, seed=5, collision=collision)
+    d = gpu_run(c, 100)
+    o = run_oracle(c, 100)
+    err = rel_linf(d.conserved(), o.conserved())
+    assert np.all(err <= LINF_SMOOTH), err
+
+
+def test_low_mach_decay_2d_bgk_omega_2():
+    c = inputs.tgv2d(32, mach=0.05, nu_lat=0.01)
+    d = gpu_run(c, 100)
+    o = run_oracle(c, 100)
+    err = rel_linf(d.conserved(), o.conserved())
+    assert np.all(err[[0, 1, 2, 4]] <= LINF_SMOOTH), err
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 3), (5, 1, 1), (2, 2, 2), (129, 1, 2)])
+def test_degenerate_and_tiny_shapes(shape):
+    c = inputs.random_smooth(*shape, seed=2)
+    d = gpu_run(c, 20)
+    o = run_oracle(c, 20)
+    Q, R = d.conserved(), o.conserved()
+    scale = np.maximum(np.abs(R).max(1), 1e-3)
+    assert np.all(np.abs(Q - R).max(1) / scale <= LINF_SMOOTH)
+
+
+# ---- shocks: rel L1 <= 1e-4 ----------------------------------------------------------------
+def test_sod_tube_400_cells_1000_steps():
+    c = inputs.sod(400)
+    d = gpu_run(c, 1000)
+    o = run_oracle(c, 1000)
+    err = rel_l1(d.conserved(), o.conserved())
+    assert np.all(err[[0, 1, 4]] <= L1_SHOCK), err
+
+
+def test_becker_shock_with_transverse_cells():
+    om = 1.0 / (0.5 + (1.0 / 1.99 - 0.5) * 128.0 / 8)
+    c = inputs.becker(128, cells_per_front=8, omega=om, cfl_max=0.1, ny=4, nz=4)
+    d = gpu_run(c, 600)
+    o = run_oracle(c, 600)
+    err = rel_l1(d.conserved(), o.conserved())
+    assert np.all(err[[0, 1, 4]] <= L1_SHOCK), err
+
+
+# ---- diagnostics (FP64 reductions) --------------------------------------------------------
+def test_diagnostics_match_oracle_and_conserve():
+    c = inputs.tgv3d(32)
+    d = capi.Domain(c.params)
+    d.init(c.rho, c.u, c.p)
+    d.step_diag()
+    g0 = d.diag()
+    d.step(98)
+    d.step_diag()
+    g = d.diag()
+    assert g["step"] == 100
+    o = oracle.Oracle(c.params)
+    o.init_primitive(c.rho, c.u, c.p)
+    o.step(100, keep_cells=True)
+    od = o.diagnostics_from_cells()
+    np.testing.assert_allclose(g["totals"][[0, 4]], od["totals"][[0, 4]], rtol=TOTALS)
+    np.testing.assert_allclose(g["totals"][1:4], od["totals"][1:4], atol=TOTALS * abs(od["totals"][0]) * 0.1)
+    # conservation over 99 steps in FP32
+    np.testing.assert_allclose(g["totals"][[0, 4]], g0["totals"][[0, 4]], rtol=TOTALS)
+    assert g["ke"] == pytest.approx(od["ke"], rel=1e-5)
+    assert g["eps_s"] == pytest.approx(od["eps_s"], rel=2e-3)
+    assert g["eps_d"] == pytest.approx(od["eps_d"], rel=2e-2, abs=1e-3 * od["eps_s"])
+    assert g["n_nan"] == 0 and g["n_floor"] == od["n_floor"]
+    assert g["rho_min"] == pytest.approx(od["rho_min"], rel=1e-5)
+
+
+def test_diagnostics_are_bitwise_deterministic():
+    c = inputs.tgv3d(24)
+    outs = []
+    for _ in range(2):
+        d = gpu_run(c, 10, diag_last=True)
+        outs.append(d.diag())
+    for k in ("totals", "ke", "eps_s", "eps_d"):
+        assert np.array_equal(np.asarray(outs[0][k]), np.asarray(outs[1][k]))
+
+
+# ---- checkpoint / resume -----------------------------------------------------------------
+def test_checkpoint_resume_is_bitwise():
+    c = inputs.tgv3d(16)
+    a = gpu_run(c, 30)
+    ck = capi.grlb_save(a.h)
+    a.step(20)
+    b = capi.Domain(c.params)
+    capi.grlb_load(b.h, ck)
+    assert b.steps == 30
+    b.step(20)
+    assert np.array_equal(a.conserved(), b.conserved())
+    assert np.array_equal(capi.grlb_save(a.h)[32:], capi.grlb_save(b.h)[32:])
+
+
+def test_invalid_arguments_are_rejected():
+    c = inputs.tgv3d(8)
+    with pytest.raises(capi.GrlbError):
+        capi.Domain(c.params.replace(omega_rho=0.0))
+    d = capi.Domain(c.params)
+    with pytest.raises(capi.GrlbError):
+        d.diag()  # no diagnostic sweep yet
+    with pytest.raises(capi.GrlbError):
+        capi.grlb_step(d.h, -1)
+    capi.grlb_step(d.h, 0)
+
+
+# ---- full-size configuration: sampled cells against the oracle's per-cell update --------
+def oracle_update_at(fpre_raw, prm, cells):
+    """Oracle post-collision populations at `cells` from the decoded pre-step state."""
+    P = oracle.lattice_params(prm)
+    nx, ny, nz = prm.nx, prm.ny, prm.nz
+    x = cells % nx
+    y = (cells // nx) % ny
+    z = cells // (nx * ny)
+    out = np.zeros((35, cells.size))
+    src = []
+    for i in range(7):
+        xs = (x - CI[i][0]) % nx
+        ys = (y - CI[i][1]) % ny
+        zs = (z - CI[i][2]) % nz
+        src.append(xs + nx * (ys + ny * zs))
+    planes = {}
+    for i in range(7):
+        planes[i] = decode_populations(fpre_raw, prm, cells=src[i])
+    for n in range(cells.size):
+        fhat = np.array([planes[i][7 * k + i, n] for k in range(5) for i in range(7)])
+        out[:, n], _ = oracle.cell(P, fhat)
+    return out
+
+
+@pytest.mark.parametrize("n", [256])
+def test_full_size_taylor_green_sampled_cells(n):
+    c = inputs.tgv3d(n)
+    d = gpu_run(c, 5)
+    pre = capi.grlb_save(d.h)
+    d.step(1)
+    post = capi.grlb_save(d.h)
+    rng = np.random.default_rng(0)
+    N = c.params.ncells
+    cells = np.unique(np.concatenate([rng.integers(0, N, 3000), [0, N - 1, n - 1, n * n - 1]]))
+    want = oracle_update_at(pre, c.params, cells)
+    got = decode_populations(post, c.params, cells=cells)
+    del pre, post
+    # per-field scale of the populations
+    for k in range(5):
+        blk = slice(7 * k, 7 * k + 7)
+        scale = max(np.abs(want[blk]).max(), 1e-12)
+        assert np.abs(got[blk] - want[blk]).max() / scale < 2e-6
+
+
+def test_full_size_conservation_over_diagnostic_sweeps():
+    c = inputs.tgv3d(256)
+    d = capi.Domain(c.params)
+    d.init(c.rho, c.u, c.p)
+    d.step_diag()
+    g0 = d.diag()
+    d.step(48)
+    d.step_diag()
+    g1 = d.diag()
+    np.testing.assert_allclose(g1["totals"][[0, 4]], g0["totals"][[0, 4]], rtol=TOTALS)
+    assert g1["n_nan"] == 0
