@@ -165,6 +165,40 @@ grlb_status grlb_batch_set_active(grlb_batch* b, const int* active);
 /* Enqueue nsteps sweeps of every active domain, one launch per step. */
 grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
 
+/* ---- diagnostic sweep without device allocation ---------------------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers that cannot call
+ * cudaMalloc: an application whose memory manager reserved the device memory up front (a
+ * further cudaMalloc would fail or fragment its pool), or a time-critical loop that cannot
+ * afford the implicit device synchronisation cudaMalloc and cudaFree may cause.  It performs exactly
+ * what grlb_step_diag does for one sweep, on population buffers the caller owns, and keeps
+ * its block partials in a fixed array of device memory that the library declares statically
+ * (GRLB_NOALLOC_MAX_BLOCKS x GRLB_NDIAG doubles, 6.8 MB, held by every device that loads the
+ * library until the process exits).  It never calls cudaMalloc, cudaFree or any other
+ * allocating routine.
+ *
+ *  p        domain description (as for grlb_create); validated on the host.
+ *  f_in     device pointer, current populations: 35 planes of N elements of the storage
+ *           type, the layout and equilibrium-shift format of the library's own buffers (the
+ *           bytes grlb_save writes after its 32-byte header).
+ *  f_out    device pointer, same size, receives the populations one step later; must not
+ *           overlap f_in.
+ *  diag_out device pointer to GRLB_NDIAG doubles: sums over cells of (Q_k - Q_ref,k) for
+ *           k = rho, m_x, m_y, m_z, E, then ke, eps_s, eps_d, rho_min, p_min, n_floor,
+ *           n_nan, n_sensor (the grlb_diag fields; totals[k] = N Q_ref,k + diag_out[k] with
+ *           Q_ref = (ref_rho, 0, 0, 0, ref_p s^2/(gamma-1))).
+ *  stream   cudaStream_t (may be NULL); the call only enqueues work on it.
+ * Limits and behaviour: the launch may use at most GRLB_NOALLOC_MAX_BLOCKS CTAs of 128 cells
+ * (8,388,608 cells, e.g. 128^3 or 256 x 256 x 128); larger domains return GRLB_EINVAL.  The
+ * first call on a device looks up the device address of the static array on that device, so
+ * make that first call before any stream capture begins.  Every call on a device shares the
+ * one array, which keeps the previous call's contents (each call overwrites every entry it
+ * reads, so nothing needs clearing); calls whose sweeps overlap on the GPU race on it, so
+ * serialise them (one stream, or events). */
+#define GRLB_NDIAG 13
+#define GRLB_NOALLOC_MAX_BLOCKS 65536
+grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* f_in, void* f_out,
+                                   double* diag_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

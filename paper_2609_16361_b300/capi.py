@@ -99,6 +99,7 @@ def lib():
             "grlb_batch_set_stream": ([vp, vp], i32),
             "grlb_batch_set_active": ([vp, C.POINTER(C.c_int)], i32),
             "grlb_batch_step": ([vp, i32], i32),
+            "grlb_step_diag_noalloc": ([C.POINTER(grlb_params), vp, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -115,7 +116,7 @@ def exported_symbols():
             "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
-            "grlb_batch_step"]
+            "grlb_batch_step", "grlb_step_diag_noalloc"]
 
 
 def check(status):
@@ -242,6 +243,13 @@ def grlb_batch_set_active(b, active):
 
 def grlb_batch_step(b, n):
     check(lib().grlb_batch_step(b, int(n)))
+
+
+def grlb_step_diag_noalloc(prm, f_in_ptr, f_out_ptr, diag_out_ptr, stream=None):
+    """One diagnostic sweep on caller-owned device buffers (device pointers as ints); the
+    library allocates no device memory for it."""
+    P = to_params(prm)
+    check(lib().grlb_step_diag_noalloc(C.byref(P), f_in_ptr, f_out_ptr, diag_out_ptr, stream))
 
 
 # ---- convenience object --------------------------------------------------------------------

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -579,3 +580,55 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
 }
 
 }  // extern "C"
+
+// =========================================================================================
+// Diagnostic sweep for callers that cannot allocate device memory: the block partials live
+// in a file-scope static device array instead of scratch from cudaMalloc.
+// =========================================================================================
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_partials[(size_t)GRLB_NOALLOC_MAX_BLOCKS * NDIAG];
+// Device address of g_noalloc_partials per device ordinal (host code cannot use the symbol
+// itself as a device pointer).  Filled once per device by the first call on that device.
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+grlb_status noalloc_scratch(double** out) {
+    int dev = 0;
+    GRLB_CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(GRLB_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        double* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_partials);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(static diagnostic scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GRLB_OK;
+}
+}  // namespace
+
+extern "C" grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* f_in, void* f_out,
+                                              double* diag_out, void* stream) {
+    grlb_status st = validate(p);
+    if (st != GRLB_OK) return st;
+    if (!f_in || !f_out || !diag_out) return fail(GRLB_EINVAL, "grlb_step_diag_noalloc: NULL pointer");
+    if (f_in == f_out) return fail(GRLB_EINVAL, "grlb_step_diag_noalloc: f_in and f_out must differ");
+    grlb_domain tmp;  // host-side description only; owns no memory
+    tmp.P = *p;
+    fill_domain_dev(&tmp);
+    choose_launch(&tmp);
+    tmp.D.buf[0] = tmp.D.buf[1] = nullptr;
+    if (tmp.nblocks > GRLB_NOALLOC_MAX_BLOCKS)
+        return fail(GRLB_EINVAL, "grlb_step_diag_noalloc: domain needs " + std::to_string(tmp.nblocks) +
+                                     " CTAs, more than the static scratch holds (" +
+                                     std::to_string(GRLB_NOALLOC_MAX_BLOCKS) + ")");
+    double* scratch = nullptr;
+    st = noalloc_scratch(&scratch);
+    if (st != GRLB_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GRLB_CU(grlb::launch_sweep(tmp.D, p->storage, p->collision, f_in, f_out, true, scratch, tmp.grid, tmp.block, s));
+    GRLB_CU(grlb::launch_diag_finalize(scratch, tmp.nblocks, diag_out, s));
+    return GRLB_OK;
+}
