@@ -172,8 +172,8 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
  * afford the implicit device synchronisation cudaMalloc and cudaFree may cause.  It performs exactly
  * what grlb_step_diag does for one sweep, on population buffers the caller owns, and keeps
  * its block partials in a fixed array of device memory that the library declares statically
- * (GRLB_NOALLOC_MAX_BLOCKS x GRLB_NDIAG doubles, 6.8 MB, held by every device that loads the
- * library until the process exits).  It never calls cudaMalloc, cudaFree or any other
+ * ((GRLB_NOALLOC_MAX_BLOCKS + 256) x GRLB_NDIAG doubles, 6.8 MB, held by every device that
+ * loads the library until the process exits).  It never calls cudaMalloc, cudaFree or any other
  * allocating routine.
  *
  *  p        domain description (as for grlb_create); validated on the host.

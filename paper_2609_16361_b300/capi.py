@@ -15,7 +15,7 @@ import numpy as np
 from . import inputs as _inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgrlb.so")
+LIB_PATH = os.environ.get("GRLB_LIB") or os.path.join(HERE, "libgrlb.so")
 
 GRLB_OK = 0
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENUMERIC", -5: "ETIMEOUT",
@@ -69,7 +69,7 @@ def lib():
         if _lib is not None:
             return _lib
         from . import build as _build
-        if _build.needs_build():
+        if LIB_PATH == _build.LIB and _build.needs_build():
             _build.build()
         if not os.path.exists(LIB_PATH):
             raise GrlbError(-3, f"CUDA library missing: {LIB_PATH}")

@@ -181,7 +181,8 @@ size_t grlb_bytes_for(const grlb_params* p) {
     tmp.P = *p;
     choose_launch(&tmp);
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    return 2 * 35 * N * elem_bytes(p->storage) + (size_t)tmp.nblocks * NDIAG * 8 + NDIAG * 8;
+    return 2 * 35 * N * elem_bytes(p->storage) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+           NDIAG * 8;
 }
 
 grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
@@ -202,7 +203,8 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     d->D.buf[0] = d->D.buf[1] = nullptr;
     e = cudaMalloc(&d->D.buf[0], pop_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&d->D.buf[1], pop_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&d->partials, (size_t)d->nblocks * NDIAG * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&d->diag_dev, NDIAG * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&d->diag_host, NDIAG * sizeof(double));
     if (e != cudaSuccess) {
@@ -211,7 +213,7 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
         return fail(e == cudaErrorMemoryAllocation ? GRLB_ENOMEM : GRLB_ECUDA,
                     std::string("grlb_create: ") + cudaGetErrorString(e));
     }
-    d->bytes = 2 * pop_bytes + (size_t)d->nblocks * NDIAG * 8 + NDIAG * 8;
+    d->bytes = 2 * pop_bytes + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 + NDIAG * 8;
     for (int k = 0; k < NDIAG; ++k) d->diag_host[k] = 0.0;
     *out = d;
     return GRLB_OK;
@@ -471,8 +473,8 @@ cudaError_t enqueue_batch_step(grlb_batch* b, int parity) {
     for (int g = 0; g < 6; ++g) {
         const int n = b->group_off[g + 1] - b->group_off[g];
         if (n == 0) continue;
-        cudaError_t e = grlb::launch_batch_sweep(g / 2, g % 2, b->d_doms, b->d_tiles + b->group_off[g], n, 128,
-                                                 parity, b->stream);
+        cudaError_t e = grlb::launch_batch_sweep(g / 2, g % 2, b->d_doms, b->d_tiles + b->group_off[g], n, parity,
+                                                 b->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -587,7 +589,9 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
 // =========================================================================================
 namespace {
 constexpr int kNoallocMaxDevices = 64;
-static __device__ __align__(256) double g_noalloc_partials[(size_t)GRLB_NOALLOC_MAX_BLOCKS * NDIAG];
+// Block partials followed by the records of the first finalize stage.
+static __device__ __align__(256) double
+    g_noalloc_partials[((size_t)GRLB_NOALLOC_MAX_BLOCKS + grlb::kDiagStageRecords) * NDIAG];
 // Device address of g_noalloc_partials per device ordinal (host code cannot use the symbol
 // itself as a device pointer).  Filled once per device by the first call on that device.
 double* g_noalloc_ptr[kNoallocMaxDevices] = {};

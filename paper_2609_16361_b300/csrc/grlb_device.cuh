@@ -25,6 +25,9 @@ constexpr int NF = 5;
 constexpr int NQ = 7;
 constexpr int NP = NF * NQ;
 constexpr int NDIAG = 13;  // per-block partial record of the diagnostic sweep
+// Diagnostic scratch = nblocks partial records followed by up to kDiagStageRecords records of
+// the first finalize stage.
+constexpr int kDiagStageRecords = 256;
 
 enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
 enum Collision { C_BGK = 0, C_RLB = 1 };

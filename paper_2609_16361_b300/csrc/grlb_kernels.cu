@@ -121,6 +121,9 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
 }
 
 // ---- single-domain sweep -----------------------------------------------------------------
+// One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
+// parameter, so its constants are read as constant-bank operands of the arithmetic (a record
+// held in shared memory costs a load per use and ~15% of the sweep's time).
 template <int S, int COLL, bool DIAG>
 __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ DomainDev D,
                                                     const void* __restrict__ fin_v,
@@ -147,101 +150,136 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
     }
 }
 
-// ---- batched sweep over a tile table -----------------------------------------------------
-// tiles[t] = (domain, x0, y0, z); the domain record supplies buffers, constants and its
-// tile width tile_x (one-dimensional CTA: thread t -> (x0 + t % tile_x, y0 + t / tile_x)).
-// `parity` flips every step so that each domain reads buf[cur ^ parity], writes the other.
+// ---- batched sweep: persistent CTAs over a tile table ------------------------------------
+// tiles[t] = (domain, x0, y0, z).  A CTA of 128 threads takes tiles blockIdx.x, + gridDim.x,
+// ... (grid-stride, so consecutive CTAs stream consecutive rows); the domain record (buffers,
+// constants, tile width tile_x) is copied to shared memory whenever the domain changes;
+// thread t handles cell (x0 + t % tile_x, y0 + t / tile_x, z).  Each domain reads
+// buf[cur ^ parity] and writes the other buffer, so `parity` flips every step.  A domain's
+// result does not depend on which other domains share the launch.
 template <int S, int COLL>
 __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __restrict__ doms,
-                                                          const int4* __restrict__ tiles,
+                                                          const int4* __restrict__ tiles, int ntiles,
                                                           int parity) {
     using T = typename Store<S>::T;
     __shared__ DomainDev sD;
-    const int4 tl = tiles[blockIdx.x];
-    {
-        const int nwords = sizeof(DomainDev) / 4;
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(doms + tl.x);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&sD);
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = src[w];
+    int loaded = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        if (tl.x != loaded) {  // uniform across the CTA
+            __syncthreads();
+            const int nwords = sizeof(DomainDev) / 4;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(doms + tl.x);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sD);
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            loaded = tl.x;
+        }
+        const DomainDev& D = sD;
+        const int x = tl.y + (int)threadIdx.x % D.tile_x;
+        const int y = tl.z + (int)threadIdx.x / D.tile_x;
+        const int z = tl.w;
+        if (x < D.nx && y < D.ny) {
+            const int c = D.cur ^ parity;
+            const T* __restrict__ fin = static_cast<const T*>(D.buf[c]);
+            T* __restrict__ fout = static_cast<T*>(D.buf[c ^ 1]);
+            const PullIdx P = pull_index(D, x, y, z);
+            float d[NF][NQ], o[NF][NQ];
+            load_cell<S>(D, fin, P, d);
+            collide<COLL, false>(D, d, o, nullptr);
+            store_cell<S>(D, fout, P.c, o);
+        }
     }
-    __syncthreads();
-    const DomainDev& D = sD;
-    const int x = tl.y + (int)threadIdx.x % D.tile_x;
-    const int y = tl.z + (int)threadIdx.x / D.tile_x;
-    const int z = tl.w;
-    if (x >= D.nx || y >= D.ny) return;
-    const int c = D.cur ^ parity;
-    const T* __restrict__ fin = static_cast<const T*>(D.buf[c]);
-    T* __restrict__ fout = static_cast<T*>(D.buf[c ^ 1]);
-    const PullIdx P = pull_index(D, x, y, z);
-    float d[NF][NQ], o[NF][NQ];
-    load_cell<S>(D, fin, P, d);
-    collide<COLL, false>(D, d, o, nullptr);
-    store_cell<S>(D, fout, P.c, o);
 }
 
 // ---- diagnostics: fixed-order sum of the block partials ----------------------------------
-// One CTA of 256 threads: thread t sums partials t, t+256, ... in order (FP64), then a fixed
-// shared-memory tree.  Writes the NDIAG record to out.
-__global__ void __launch_bounds__(256) diag_finalize_kernel(const double* __restrict__ partials,
-                                                            int64_t nblocks, double* __restrict__ out) {
-    __shared__ double sh[256];
-    for (int f = 0; f < NDIAG; ++f) {
-        const bool isMin = (f == 8 || f == 9);
-        double acc = isMin ? 3.0e38 : 0.0;
-        for (int64_t b = threadIdx.x; b < nblocks; b += 256) {
-            const double x = partials[b * NDIAG + f];
-            acc = isMin ? fmin(acc, x) : acc + x;
+// Two deterministic stages.  Stage 1: CTA g sums the partial records [g*per, (g+1)*per) --
+// thread t takes records g*per + t, + 256, ... in order (FP64), then a fixed shared-memory
+// tree -- and writes one record.  Stage 2: one CTA sums the G stage-1 records the same way.
+__device__ __forceinline__ void reduce_records(const double* __restrict__ rec, int64_t begin, int64_t end,
+                                               double* __restrict__ out) {
+    __shared__ double sh[NDIAG][256];
+    double acc[NDIAG];
+#pragma unroll
+    for (int f = 0; f < NDIAG; ++f) acc[f] = (f == 8 || f == 9) ? 3.0e38 : 0.0;
+    for (int64_t b = begin + threadIdx.x; b < end; b += 256) {
+#pragma unroll
+        for (int f = 0; f < NDIAG; ++f) {
+            const double x = rec[b * NDIAG + f];
+            acc[f] = (f == 8 || f == 9) ? fmin(acc[f], x) : acc[f] + x;
         }
-        sh[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                const double a = sh[threadIdx.x], b2 = sh[threadIdx.x + s];
-                sh[threadIdx.x] = isMin ? fmin(a, b2) : a + b2;
+    }
+#pragma unroll
+    for (int f = 0; f < NDIAG; ++f) sh[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int f = 0; f < NDIAG; ++f) {
+                const double a = sh[f][threadIdx.x], c = sh[f][threadIdx.x + s];
+                sh[f][threadIdx.x] = (f == 8 || f == 9) ? fmin(a, c) : a + c;
             }
-            __syncthreads();
         }
-        if (threadIdx.x == 0) out[f] = sh[0];
         __syncthreads();
     }
+    if (threadIdx.x < NDIAG) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) diag_stage1_kernel(const double* __restrict__ partials, int64_t nblocks,
+                                                          int64_t per, double* __restrict__ stage) {
+    const int64_t begin = (int64_t)blockIdx.x * per;
+    const int64_t end = begin + per < nblocks ? begin + per : nblocks;
+    reduce_records(partials, begin, end, stage + (int64_t)blockIdx.x * NDIAG);
+}
+
+__global__ void __launch_bounds__(256) diag_stage2_kernel(const double* __restrict__ stage, int64_t g,
+                                                          double* __restrict__ out) {
+    reduce_records(stage, 0, g, out);
 }
 
 // ---- initialisation: primitive (physical, FP64) -> equilibrium deviations ----------------
 // Populations f = w_i (Q + c_i . Phi^adv / cs^2) (zero non-equilibrium), stored as
 // deviations from the reference equilibrium.  Lattice conversion with s = dt/dx.
 template <int S>
-__global__ void init_kernel(const DomainDev D, void* __restrict__ fout_v, const double* __restrict__ rho,
-                            const double* __restrict__ u, const double* __restrict__ p, double s,
-                            double gm1, double rho_ref, double p_ref) {
+__global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __restrict__ fout_v,
+                                                   const double* __restrict__ rho, const double* __restrict__ u,
+                                                   const double* __restrict__ p, double s, double gm1,
+                                                   double rho_ref, double p_ref) {
     using T = typename Store<S>::T;
     T* fout = static_cast<T*>(fout_v);
     const int64_t N = D.plane;
+    const float g1 = (float)gm1;
+    const float Hp_ref = (float)(p_ref / gm1 + p_ref);  // E_ref + p_ref
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
+        // the two differences against the reference state are taken in FP64, the rest in FP32
         const double r = rho[c];
-        const double ux = u[c] * s, uy = u[N + c] * s, uz = u[2 * N + c] * s;
-        const double pp = p[c] * s * s;
-        const double uv[3] = {ux, uy, uz};
-        const double m[3] = {r * ux, r * uy, r * uz};
-        const double ke = 0.5 * (m[0] * ux + m[1] * uy + m[2] * uz);
-        const double dE = (pp - p_ref) / gm1 + ke;
-        const double dQ[5] = {r - rho_ref, m[0], m[1], m[2], dE};
-        const double E = p_ref / gm1 + dE;
-        double Pd[5][3];
+        const float drho = (float)(r - rho_ref);
+        const float dp = (float)(p[c] * s * s - p_ref);
+        const float rf = (float)r;
+        const float uv[3] = {(float)(u[c] * s), (float)(u[N + c] * s), (float)(u[2 * N + c] * s)};
+        const float m[3] = {rf * uv[0], rf * uv[1], rf * uv[2]};
+        const float ke = 0.5f * (m[0] * uv[0] + m[1] * uv[1] + m[2] * uv[2]);
+        const float dE = dp / g1 + ke;
+        const float Hp = Hp_ref + dE + dp;  // E + p
+        const float dQ[5] = {drho, m[0], m[1], m[2], dE};
+        float Pd[5][3];
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             Pd[0][a] = m[a];
-            for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? pp - p_ref : 0.0);
-            Pd[4][a] = (E + pp) * uv[a];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? dp : 0.0f);
+            Pd[4][a] = Hp * uv[a];
         }
+#pragma unroll
         for (int k = 0; k < NF; ++k) {
-            const double sc = (double)D.enc[k];
-            const double q1 = 0.125 * dQ[k];
-            const double v[NQ] = {0.25 * dQ[k], q1 + 0.5 * Pd[k][0], q1 - 0.5 * Pd[k][0],
-                                  q1 + 0.5 * Pd[k][1], q1 - 0.5 * Pd[k][1],
-                                  q1 + 0.5 * Pd[k][2], q1 - 0.5 * Pd[k][2]};
-            for (int i = 0; i < NQ; ++i)
-                Store<S>::st(fout + (int64_t)(7 * k + i) * N + c, (float)(v[i] * sc));
+            const float sc = D.enc[k];
+            const float q1 = 0.125f * dQ[k];
+            const float v[NQ] = {0.25f * dQ[k], q1 + 0.5f * Pd[k][0], q1 - 0.5f * Pd[k][0],
+                                 q1 + 0.5f * Pd[k][1], q1 - 0.5f * Pd[k][1],
+                                 q1 + 0.5f * Pd[k][2], q1 - 0.5f * Pd[k][2]};
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) Store<S>::st(fout + (int64_t)(7 * k + i) * N + c, v[i] * sc);
         }
     }
 }
@@ -290,14 +328,36 @@ cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, const void* 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, const int4* tiles,
-                               int ntiles, int threads, int parity, cudaStream_t st) {
-    if (ntiles <= 0) return cudaSuccess;
-#define GRLB_CASE(SS, CC)                                                                  \
-    if (storage == SS && coll == CC) {                                                     \
-        batch_sweep_kernel<SS, CC><<<ntiles, threads, 0, st>>>(doms, tiles, parity);         \
-        return cudaGetLastError();                                                         \
+// Persistent grid of the batched sweep: as many CTAs as can be resident at once (queried once
+// per kernel instantiation), capped by the number of tiles.
+template <typename K>
+static int resident_ctas(K kernel) {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, 0);
+        cached = (sms > 0 ? sms : 148) * (per > 0 ? per : 4);
     }
+    return cached;
+}
+
+template <int S, int COLL>
+static cudaError_t launch_batch_t(const DomainDev* doms, const int4* tiles, int ntiles, int parity,
+                                  cudaStream_t st) {
+    auto k = batch_sweep_kernel<S, COLL>;
+    int grid = resident_ctas(k);
+    if (grid > ntiles) grid = ntiles;
+    k<<<grid, 128, 0, st>>>(doms, tiles, ntiles, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, const int4* tiles, int ntiles,
+                               int parity, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+#define GRLB_CASE(SS, CC) \
+    if (storage == SS && coll == CC) return launch_batch_t<SS, CC>(doms, tiles, ntiles, parity, st);
     GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F16, C_RLB)
     GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK)
 #undef GRLB_CASE
@@ -305,7 +365,14 @@ cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, con
 }
 
 cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double* out, cudaStream_t st) {
-    diag_finalize_kernel<<<1, 256, 0, st>>>(partials, nblocks, out);
+    // stage-1 records are written right after the nblocks partial records
+    const int64_t g = nblocks < kDiagStageRecords ? nblocks : kDiagStageRecords;
+    const int64_t per = (nblocks + g - 1) / g;
+    double* stage = const_cast<double*>(partials) + nblocks * NDIAG;
+    diag_stage1_kernel<<<(int)g, 256, 0, st>>>(partials, nblocks, per, stage);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_stage2_kernel<<<1, 256, 0, st>>>(stage, g, out);
     return cudaGetLastError();
 }
 

@@ -6,10 +6,13 @@
 #include "grlb_device.cuh"
 
 namespace grlb {
+// One sweep of one domain (record by value).  diag: one partial record per CTA in partials.
 cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, const void* fin, void* fout,
                          bool diag, double* partials, dim3 grid, dim3 block, cudaStream_t st);
-cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, const int4* tiles,
-                               int ntiles, int threads, int parity, cudaStream_t st);
+// One sweep of every tile in tiles[0, ntiles) (domain records in device memory): one launch
+// of the persistent batched kernel.
+cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, const int4* tiles, int ntiles,
+                               int parity, cudaStream_t st);
 cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double* out,
                                  cudaStream_t st);
 cudaError_t launch_init(const DomainDev& D, int storage, void* fout, const double* rho,
