@@ -312,6 +312,105 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------------------
+def run_batch(args):
+    """64 uneven domains (48 Becker tubes + 16 Taylor-Green boxes, seed 0), 1000 steps each:
+    persistent batched sweep with autotuned tile widths and a CUDA-graph step loop, against
+    64 sequential single-domain runs (one launch per step, no graphs)."""
+    import torch
+    from paper_2609_16361_b300 import autotune, capi, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    st = stream.cuda_stream
+    cases = inputs.batched_mix(0)
+    cells = sum(c.params.ncells for c in cases)
+    steps = args.batch_steps
+    table = autotune.tune(cases, steps=20, stream=stream)
+    doms = []
+    for c in cases:
+        d = capi.Domain(c.params, stream=st)
+        d.init(c.rho, c.u, c.p)
+        doms.append(d)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {}
+    for label, use_graph, plan in (("batched_graph_tuned", 1, autotune.plan(cases, table)),
+                                   ("batched_graph_default", 1, None),
+                                   ("batched_nograph_default", 0, None)):
+        for d, c in zip(doms, cases):
+            d.init(c.rho, c.u, c.p)
+        b = capi.grlb_batch_create([d.h for d in doms], use_graph=use_graph)
+        capi.grlb_batch_set_stream(b, st)
+        if plan:
+            capi.grlb_batch_set_tile_x(b, plan)
+        capi.grlb_batch_step(b, 4)
+        stream.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        capi.grlb_batch_step(b, steps)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        capi.grlb_batch_destroy(b)
+        out[label] = {"mlups": cells * steps / t / 1e6, "seconds": t}
+    for d, c in zip(doms, cases):
+        d.init(c.rho, c.u, c.p)
+    stream.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for d in doms:
+        d.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    out["sequential_plain"] = {"mlups": cells * steps / t / 1e6, "seconds": t}
+    diag_ok = True
+    for d in doms:
+        d.step_diag()
+        diag_ok &= d.diag()["n_nan"] == 0
+    for d in doms:
+        d.close()
+    best = out["batched_graph_tuned"]["mlups"]
+    line = {"metric": "batched MLUP/s (64 uneven domains, 1000 steps each)", "value": best,
+            "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True,
+            "vs_sequential_plain": best / out["sequential_plain"]["mlups"],
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "48 Becker tubes (128-2048 x 4 x 4, M 1.5-5) + 16 Taylor-Green "
+                                   "boxes (32^3-96^3, M 0.5-1.25, Re 100), seed 0",
+                       "cells": cells, "steps": steps},
+            "variants": out, "autotune": table, "finite_after_run": bool(diag_ok)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson trace (seed 0, 20 requests/s): continuous-batching server against the same trace
+    served first-in first-out one domain at a time with plain launches."""
+    import torch
+    from paper_2609_16361_b300 import autotune, inputs, serve
+    torch.cuda.set_device(0)
+    trace = inputs.serving_trace(0, n_requests=args.requests, rate=20.0)
+    table = autotune.tune([r.case for r in trace[:12]], steps=10)
+    srv = serve.Server(hbm_budget=150e9, chunk=50, tile_table=table)
+    res = srv.run(trace, realtime=True)
+    s_batched = serve.summarize(res)
+    base = serve.serial_plain(trace, realtime=True)
+    s_plain = serve.summarize(base)
+    same = sum(a.digest == b.digest for a, b in zip(res, base))
+    line = {"metric": "served solves/s (continuous batching)", "value": s_batched["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "p50_latency_s": s_batched["p50_latency_s"], "p99_latency_s": s_batched["p99_latency_s"],
+            "baseline_serial_plain": s_plain,
+            "batched": s_batched, "peak_resident": srv.peak_resident,
+            "peak_hbm_bytes": srv.peak_bytes, "dtype": "f32/f16 storage, f32 arithmetic",
+            "data": "synthetic",
+            "config": {"workload": "Poisson 20/s; Sod / Becker tubes, Taylor-Green 64^3-192^3 "
+                                   "(Re 100), FP32 or FP16, 500-5000 steps; seed 0",
+                       "requests": args.requests, "hbm_budget_bytes": 150e9, "chunk": 50},
+            "bitwise_equal_to_plain": same}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,11 +420,18 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve"])
+    ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=40)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -144,14 +144,19 @@ int64_t grlb_steps_done(const grlb_domain* d);
 
 /* ---- batching: many domains, one launch per step -------------------------------------
  * A batch references existing domains (it does not own them; destroy the batch first).
- * One step = one launch over a tile table that concatenates the tiles of every active
- * domain; tile shape = block_x threads along x (one cell each) x block_y rows.
- * All domains must live on the same device; the batch runs on the stream of domains[0]
- * (or the one set with grlb_batch_set_stream). */
+ * One step = one launch of the persistent batched sweep over a tile table that concatenates
+ * the tiles of every active small domain (one launch per storage/collision group), plus one
+ * single-domain sweep per active large domain (at least solo_min_cells cells; it saturates
+ * the GPU on its own and runs the kernel grlb_step runs, so its result is bitwise that of
+ * grlb_step).  A 128-thread CTA covers tile_x cells along x times 128/tile_x rows.  A small
+ * domain's result does not depend on the other domains of the batch and matches grlb_step
+ * within FP32 rounding.  All domains must live on the same device; the batch runs on the
+ * stream of domains[0] (or the one set with grlb_batch_set_stream). */
 typedef struct {
-    int32_t block_x;    /* threads per block along x: 32, 64, 128, 256 (0 = default 128)   */
-    int32_t block_y;    /* rows per block: 1, 2, 4, 8 (0 = default 1)                        */
-    int32_t use_graph;  /* 1: capture grlb_batch_step's launch loop as a CUDA graph          */
+    int32_t block_x;        /* default tile width: 32, 64 or 128 (0 = 128, narrowed for
+                               domains with fewer cells along x)                             */
+    int32_t solo_min_cells; /* 0 = 262144 (64^3); < 0: every domain goes through the table  */
+    int32_t use_graph;      /* 1: replay the table launches of two steps from a CUDA graph  */
     int32_t pad0;
 } grlb_batch_config;
 
@@ -162,7 +167,12 @@ grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream);
 /* Mark which domains advance (active[i] != 0); rebuilds the tile table.  active == NULL
  * activates all. */
 grlb_status grlb_batch_set_active(grlb_batch* b, const int* active);
-/* Enqueue nsteps sweeps of every active domain, one launch per step. */
+/* Per-domain tile width (cells along x of a 128-thread CTA: 32, 64 or 128; 0 = the batch's
+ * block_x rule), e.g. from an autotuner; tile_x == NULL resets all to 0.  Rebuilds the tile
+ * table.  Results do not depend on the tile shape. */
+grlb_status grlb_batch_set_tile_x(grlb_batch* b, const int* tile_x);
+/* Enqueue nsteps sweeps of every active domain, one launch per step (per storage/collision
+ * group), replayed from a captured CUDA graph when use_graph is set. */
 grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
 
 /* ---- diagnostic sweep without device allocation ---------------------------------------

@@ -54,7 +54,7 @@ class grlb_diag(C.Structure):
 
 
 class grlb_batch_config(C.Structure):
-    _fields_ = [("block_x", C.c_int32), ("block_y", C.c_int32), ("use_graph", C.c_int32),
+    _fields_ = [("block_x", C.c_int32), ("solo_min_cells", C.c_int32), ("use_graph", C.c_int32),
                 ("pad0", C.c_int32)]
 
 
@@ -99,6 +99,7 @@ def lib():
             "grlb_batch_set_stream": ([vp, vp], i32),
             "grlb_batch_set_active": ([vp, C.POINTER(C.c_int)], i32),
             "grlb_batch_step": ([vp, i32], i32),
+            "grlb_batch_set_tile_x": ([vp, C.POINTER(C.c_int)], i32),
             "grlb_step_diag_noalloc": ([C.POINTER(grlb_params), vp, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
@@ -116,7 +117,7 @@ def exported_symbols():
             "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
-            "grlb_batch_step", "grlb_step_diag_noalloc"]
+            "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc"]
 
 
 def check(status):
@@ -217,9 +218,9 @@ def grlb_steps_done(h) -> int:
     return int(lib().grlb_steps_done(h))
 
 
-def grlb_batch_create(handles, block_x=0, use_graph=1):
+def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0):
     arr = (C.c_void_p * len(handles))(*[h.value for h in handles])
-    cfg = grlb_batch_config(block_x, 0, use_graph, 0)
+    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, 0)
     b = C.c_void_p()
     check(lib().grlb_batch_create(arr, len(handles), C.byref(cfg), C.byref(b)))
     return b
@@ -239,6 +240,14 @@ def grlb_batch_set_active(b, active):
     else:
         arr = (C.c_int * len(active))(*[int(bool(a)) for a in active])
         check(lib().grlb_batch_set_active(b, arr))
+
+
+def grlb_batch_set_tile_x(b, tile_x):
+    if tile_x is None:
+        check(lib().grlb_batch_set_tile_x(b, None))
+    else:
+        arr = (C.c_int * len(tile_x))(*[int(t) for t in tile_x])
+        check(lib().grlb_batch_set_tile_x(b, arr))
 
 
 def grlb_batch_step(b, n):

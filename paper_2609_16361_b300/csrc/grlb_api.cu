@@ -417,6 +417,8 @@ grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
 struct grlb_batch {
     std::vector<grlb_domain*> doms;
     std::vector<int> active;
+    std::vector<int> tile_x;  // per-domain override (0 = rule from cfg.block_x)
+    std::vector<int> solo;    // 1: large domain, advanced by the single-domain sweep
     grlb_batch_config cfg{};
     cudaStream_t stream = nullptr;
     DomainDev* d_doms = nullptr;
@@ -432,7 +434,9 @@ struct grlb_batch {
 namespace {
 int group_of(const grlb_params& p) { return p.storage * 2 + p.collision; }
 
-int tile_width(const grlb_batch* b, const grlb_domain* d) {
+int tile_width(const grlb_batch* b, size_t i) {
+    if (b->tile_x[i] > 0) return b->tile_x[i];
+    const grlb_domain* d = b->doms[i];
     int tx = b->cfg.block_x > 0 ? b->cfg.block_x : 128;
     while (tx > 32 && tx / 2 >= d->P.nx) tx /= 2;
     return tx;
@@ -441,9 +445,9 @@ int tile_width(const grlb_batch* b, const grlb_domain* d) {
 grlb_status rebuild_tiles(grlb_batch* b) {
     std::vector<int4> groups[6];
     for (size_t i = 0; i < b->doms.size(); ++i) {
-        if (!b->active[i]) continue;
+        if (!b->active[i] || b->solo[i]) continue;
         const grlb_domain* d = b->doms[i];
-        const int tx = tile_width(b, d);
+        const int tx = tile_width(b, i);
         const int ty = 128 / tx;
         std::vector<int4>& g = groups[group_of(d->P)];
         for (int z = 0; z < d->P.nz; ++z)
@@ -501,6 +505,9 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
         }
         b->doms.push_back(domains[i]);
         b->active.push_back(1);
+        b->tile_x.push_back(0);
+        const int64_t thr = b->cfg.solo_min_cells == 0 ? 262144 : b->cfg.solo_min_cells;
+        b->solo.push_back(thr > 0 && domains[i]->D.plane >= thr ? 1 : 0);
     }
     b->stream = domains[0]->stream;
     cudaError_t e = cudaMalloc(&b->d_doms, n * sizeof(DomainDev));
@@ -543,15 +550,37 @@ grlb_status grlb_batch_set_active(grlb_batch* b, const int* active) {
     return rebuild_tiles(b);
 }
 
+grlb_status grlb_batch_set_tile_x(grlb_batch* b, const int* tile_x) {
+    if (!b) return fail(GRLB_EINVAL, "batch is NULL");
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        const int t = tile_x ? tile_x[i] : 0;
+        if (t != 0 && t != 32 && t != 64 && t != 128) return fail(GRLB_EINVAL, "tile_x must be 0, 32, 64 or 128");
+    }
+    for (size_t i = 0; i < b->doms.size(); ++i) b->tile_x[i] = tile_x ? tile_x[i] : 0;
+    return rebuild_tiles(b);
+}
+
 grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
     if (!b) return fail(GRLB_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
-    if (nsteps == 0 || b->ntiles == 0) return GRLB_OK;
+    if (nsteps == 0) return GRLB_OK;
+    // large domains: the single-domain sweep, one launch per step (bitwise = grlb_step)
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        if (!b->active[i] || !b->solo[i]) continue;
+        grlb_domain* d = b->doms[i];
+        cudaStream_t keep = d->stream;
+        d->stream = b->stream;
+        grlb_status st = GRLB_OK;
+        for (int n = 0; n < nsteps && st == GRLB_OK; ++n) st = sweep_once(d, false);
+        d->stream = keep;
+        if (st != GRLB_OK) return st;
+    }
+    if (b->ntiles == 0) return GRLB_OK;
     // The staging records are rewritten below: wait for the previous call's copy to finish.
     GRLB_CU(cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < b->doms.size(); ++i) {
         b->h_doms[i] = b->doms[i]->D;
-        b->h_doms[i].tile_x = tile_width(b, b->doms[i]);
+        b->h_doms[i].tile_x = tile_width(b, i);
     }
     GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms, b->doms.size() * sizeof(DomainDev), cudaMemcpyHostToDevice,
                             b->stream));
@@ -573,7 +602,7 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
     }
     for (; done < nsteps; ++done) GRLB_CU(enqueue_batch_step(b, done & 1));
     for (size_t i = 0; i < b->doms.size(); ++i) {
-        if (!b->active[i]) continue;
+        if (!b->active[i] || b->solo[i]) continue;
         grlb_domain* d = b->doms[i];
         d->D.cur ^= (nsteps & 1);
         d->steps += nsteps;

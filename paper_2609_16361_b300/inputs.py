@@ -298,3 +298,69 @@ def random_smooth(nx: int, ny: int, nz: int, seed: int = 0, amp: float = 0.05,
                      omega_min=1.9, sensor_gain=40.0, J_min=1e-2, ref_rho=rho0, ref_p=p0,
                      name=f"rand{seed}")
     return Case(prm, _flat(rho), np.stack([_flat(ux), _flat(uy), _flat(uz)]), _flat(p))
+
+
+# --------------------------------------------------------------------------------------
+# Multi-domain workloads (seeded)
+def becker_tied_omega(cells_per_front: float, fine_cells: float = 128.0, fine_omega: float = 1.99):
+    """omega tied to dt: tau - 1/2 proportional to dt (cells_per_front under acoustic scaling),
+    equal to fine_omega at fine_cells cells per front."""
+    return 1.0 / (0.5 + (1.0 / fine_omega - 0.5) * fine_cells / cells_per_front)
+
+
+def batched_mix(seed: int = 0, n_becker: int = 48, n_tgv: int = 16, storage: int = STORE_F32):
+    """Uneven multi-domain workload: Becker tubes (nx ~ U{128..2048} x 4 x 4, shock Mach ~
+    U[1.5, 5], Pr 0.75, 8 cells per front, dt-tied omega) and Taylor-Green boxes (N ~ U{32..96},
+    M0 ~ U[0.5, 1.25], Re 100), drawn from numpy default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    om = becker_tied_omega(8.0)
+    for _ in range(n_becker):
+        nx = int(rng.integers(128, 2049))
+        M = float(rng.uniform(1.5, 5.0))
+        cases.append(becker(nx, mach=M, cells_per_front=8.0, omega=om, cfl_max=0.1, ny=4, nz=4,
+                            storage=storage))
+    for _ in range(n_tgv):
+        n = int(rng.integers(32, 97))
+        M = float(rng.uniform(0.5, 1.25))
+        cases.append(tgv3d(n, mach=M, re=100.0, storage=storage))
+    return cases
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float        # seconds after the trace start
+    kind: str
+    storage: int
+    steps: int
+    case: Case
+
+
+def serving_trace(seed: int = 0, n_requests: int = 40, rate: float = 20.0,
+                  tgv_range=(64, 192), steps_range=(500, 5000), fp16_prob: float = 0.5):
+    """Poisson arrivals (mean `rate` per second) of simulation requests drawn from
+    default_rng(seed): type uniform over {Sod tube, Becker tube, Taylor-Green box}, Taylor-Green
+    N ~ U{tgv_range}, steps ~ U{steps_range}, FP16 storage with probability fp16_prob (else
+    FP32)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    om = becker_tied_omega(8.0)
+    for rid in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        kind = ["sod", "becker", "tgv"][int(rng.integers(0, 3))]
+        storage = STORE_F16 if rng.uniform() < fp16_prob else STORE_F32
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        if kind == "sod":
+            nx = int(rng.integers(400, 4001))
+            case = sod(nx, steps=steps, storage=storage, t_end=0.08 * steps / nx)
+        elif kind == "becker":
+            nx = int(rng.integers(128, 2049))
+            case = becker(nx, mach=float(rng.uniform(1.5, 5.0)), cells_per_front=8.0, omega=om,
+                          cfl_max=0.1, ny=4, nz=4, storage=storage)
+        else:
+            n = int(rng.integers(tgv_range[0], tgv_range[1] + 1))
+            case = tgv3d(n, mach=float(rng.uniform(0.5, 1.25)), re=100.0, storage=storage)
+        reqs.append(Request(rid, t, kind, storage, steps, case))
+    return reqs

@@ -1,0 +1,197 @@
+"""Continuous-batching serving loop for simulation requests (Sod / Becker tubes, Taylor-Green
+boxes, FP32 or FP16 storage, different step counts).
+
+Requests arrive over time.  A request is admitted as soon as its populations fit in the HBM
+budget (FIFO, head of line waits) and a slot is free; its domain is created and initialised
+on the device and stays resident until it finishes.  Resident domains advance together,
+`chunk` steps at a time, so a request that arrives while others run joins at the next chunk
+boundary.  Per chunk every small resident domain advances (they share one persistent
+batched launch per step and storage/collision group, CUDA-graph step loop), and of the large
+ones (each fills the GPU on its own) only the one with the least remaining work
+(cells x steps) — shortest-remaining-work-first, so short large requests are not held
+behind long ones.  A finished request's conserved fields are read back and its memory is
+released, which may admit waiting requests.
+
+A domain's result does not depend on which other domains share its launches, so every
+request's result is bitwise the same alone and in the mix.  `serial_plain` is the baseline:
+the same trace first-in first-out, one domain at a time, one single-domain launch per step.
+"""
+from __future__ import annotations
+
+import collections
+import hashlib
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import autotune, capi
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    steps: int
+    cells: int
+    arrival: float
+    admitted: float = 0.0
+    finished: float = 0.0
+    digest: str = ""
+    totals: np.ndarray = field(default_factory=lambda: np.zeros(5))
+    fields: np.ndarray | None = None  # conserved fields, kept only when asked for
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def _finish(res: Result, dom: capi.Domain, t0: float, keep: bool):
+    Q = dom.conserved()
+    res.finished = time.perf_counter() - t0
+    res.digest = hashlib.sha256(Q.tobytes()).hexdigest()
+    res.totals = Q.sum(axis=1)
+    if keep:
+        res.fields = Q
+
+
+class Server:
+    def __init__(self, hbm_budget: float = 150e9, max_resident: int = 512, chunk: int = 50,
+                 use_graph: bool = True, tile_table: dict | None = None, stream=None,
+                 keep_fields: bool = False, large_cells: int = 262144, srpt: bool = True):
+        import torch
+        self.budget = float(hbm_budget)
+        self.max_resident = max_resident
+        self.chunk = chunk
+        self.use_graph = use_graph
+        self.tile_table = tile_table or {}
+        self.stream = stream or torch.cuda.Stream()
+        self.peak_bytes = 0
+        self.peak_resident = 0
+        self.launch_steps = 0
+        self.keep_fields = keep_fields
+        self.large_cells = large_cells  # same threshold as the batch's solo_min_cells
+        self.srpt = srpt
+
+    def run(self, trace, realtime: bool = True):
+        """Serve `trace` (list of inputs.Request sorted by arrival).  Returns Results in
+        request order.  realtime=False admits every request at t = 0 (closed-loop)."""
+        st = self.stream.cuda_stream
+        pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
+        waiting = collections.deque()
+        resident = []  # [req, dom, remaining, bytes, Result]
+        results = {}
+        used = 0.0
+        batch = None
+        mask = None
+        dirty = True
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        try:
+            while pending or waiting or resident:
+                t = now()
+                while pending and (not realtime or pending[0].arrival <= t):
+                    waiting.append(pending.popleft())
+                # admission: FIFO while the head fits in the budget and a slot is free
+                while waiting and len(resident) < self.max_resident:
+                    r = waiting[0]
+                    need = capi.grlb_bytes_for(r.case.params)
+                    if need == 0:
+                        raise capi.GrlbError(-1, f"request {r.rid}: invalid parameters")
+                    if used + need > self.budget:
+                        if not resident:
+                            raise capi.GrlbError(-2, f"request {r.rid} needs {need} B > budget")
+                        break
+                    waiting.popleft()
+                    dom = capi.Domain(r.case.params, stream=st)
+                    dom.init(r.case.rho, r.case.u, r.case.p)
+                    res = Result(r.rid, r.kind, r.steps, r.case.params.ncells,
+                                 r.arrival if realtime else 0.0, admitted=now())
+                    resident.append([r, dom, r.steps, need, res])
+                    used += need
+                    dirty = True
+                self.peak_bytes = max(self.peak_bytes, used)
+                self.peak_resident = max(self.peak_resident, len(resident))
+                if not resident:
+                    if pending:
+                        time.sleep(max(0.0, pending[0].arrival - now()))
+                    continue
+                if dirty:
+                    if batch is not None:
+                        capi.grlb_batch_destroy(batch)
+                    batch = capi.grlb_batch_create([x[1].h for x in resident],
+                                                   use_graph=int(self.use_graph),
+                                                   solo_min_cells=self.large_cells)
+                    capi.grlb_batch_set_stream(batch, st)
+                    if self.tile_table:
+                        capi.grlb_batch_set_tile_x(
+                            batch, autotune.plan([x[0].case for x in resident], self.tile_table))
+                    mask = None
+                    dirty = False
+                # every small domain; of the large ones the least remaining work first
+                large = [i for i, x in enumerate(resident) if x[1].N >= self.large_cells]
+                pick = set(range(len(resident)))
+                if self.srpt and len(large) > 1:
+                    keep = min(large, key=lambda i: resident[i][1].N * resident[i][2])
+                    pick -= set(large) - {keep}
+                new_mask = [1 if i in pick else 0 for i in range(len(resident))]
+                if new_mask != mask:
+                    capi.grlb_batch_set_active(batch, new_mask)
+                    mask = new_mask
+                k = min(self.chunk, min(resident[i][2] for i in pick))
+                capi.grlb_batch_step(batch, k)
+                self.launch_steps += k
+                self.stream.synchronize()
+                for i in pick:
+                    resident[i][2] -= k
+                done = [x for x in resident if x[2] == 0]
+                if done:
+                    for r, dom, _, need, res in done:
+                        _finish(res, dom, t0, self.keep_fields)
+                        results[r.rid] = res
+                        dom.close()
+                        used -= need
+                    resident = [x for x in resident if x[2] > 0]
+                    dirty = True
+        finally:
+            if batch is not None:
+                capi.grlb_batch_destroy(batch)
+            for x in resident:
+                x[1].close()
+        return [results[r.rid] for r in sorted(trace, key=lambda r: r.rid)]
+
+
+def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = False):
+    """Baseline: first-in first-out, one domain at a time, one single-domain launch per step
+    (no batching, no graphs)."""
+    import torch
+    stream = stream or torch.cuda.Stream()
+    st = stream.cuda_stream
+    out = []
+    t0 = time.perf_counter()
+    for r in sorted(trace, key=lambda r: r.arrival):
+        if realtime:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        res = Result(r.rid, r.kind, r.steps, r.case.params.ncells, r.arrival if realtime else 0.0,
+                     admitted=time.perf_counter() - t0)
+        dom = capi.Domain(r.case.params, stream=st)
+        dom.init(r.case.rho, r.case.u, r.case.p)
+        dom.step(r.steps)
+        _finish(res, dom, t0, keep_fields)
+        dom.close()
+        out.append(res)
+    return sorted(out, key=lambda x: x.rid)
+
+
+def summarize(results, t_span: float | None = None) -> dict:
+    lat = np.array([r.latency for r in results])
+    span = t_span if t_span is not None else max(r.finished for r in results) - min(
+        r.arrival for r in results)
+    cells = sum(r.cells * r.steps for r in results)
+    return {"solves": len(results), "solves_per_s": len(results) / span,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "span_s": span,
+            "mlups": cells / span / 1e6}

@@ -93,3 +93,25 @@ def test_inactive_domains_do_not_move():
     assert doms[1].steps == 4 and doms[0].steps == 10
     assert np.array_equal(capi.grlb_save(doms[0].h)[32:], batched_alone(cases[0], 10))
     capi.grlb_batch_destroy(b)
+
+
+def test_large_domains_run_the_single_domain_sweep_inside_a_batch():
+    """A domain of at least solo_min_cells cells is advanced by the kernel grlb_step runs:
+    bitwise equal to the solo run; the small domains beside it go through the table."""
+    big = inputs.tgv3d(40)          # 64000 cells
+    small = mixed_cases()[2:4]
+    cases = [big] + small
+    doms = []
+    for c in cases:
+        d = capi.Domain(c.params)
+        d.init(c.rho, c.u, c.p)
+        doms.append(d)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, solo_min_cells=50000)
+    capi.grlb_batch_step(b, 7)
+    capi.grlb_batch_step(b, 6)
+    _, raw_ref = solo(big, 13)
+    assert np.array_equal(capi.grlb_save(doms[0].h)[32:], raw_ref)
+    for c, d in zip(small, doms[1:]):
+        assert d.steps == 13
+        assert np.array_equal(capi.grlb_save(d.h)[32:], batched_alone(c, 13))
+    capi.grlb_batch_destroy(b)

@@ -1,0 +1,57 @@
+"""Serving loop: continuous batching of simulation requests of different sizes, step counts
+and storage types.  Each request's result is bitwise the same served alone and in the mix,
+and equals the plain single-domain path with the same storage within rounding: 1e-6 relative
+for FP32 populations; 1e-2 for FP16, where a one-ulp FP32 difference between the two kernels
+can flip one FP16 rounding (1e-3 relative) and propagate.  Admission respects the HBM
+budget."""
+import numpy as np
+import pytest
+
+from paper_2609_16361_b300 import capi, inputs, serve
+from tests.common import rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+def small_trace(n=8, seed=3):
+    return inputs.serving_trace(seed=seed, n_requests=n, rate=200.0, tgv_range=(12, 20),
+                                steps_range=(20, 130))
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    trace = small_trace()
+    assert len({r.storage for r in trace}) == 2 and len({r.kind for r in trace}) >= 2
+    mixed = serve.Server(chunk=16, keep_fields=True).run(trace, realtime=False)
+    plain = serve.serial_plain(trace, realtime=False, keep_fields=True)
+    for r, m, p in zip(trace, mixed, plain):
+        alone = serve.Server(chunk=16).run([r], realtime=False)[0]
+        assert m.rid == r.rid == alone.rid == p.rid
+        assert m.digest == alone.digest, f"request {r.rid} ({r.kind}) differs in the mix"
+        err = rel_linf(m.fields, p.fields)
+        tol = 1e-6 if r.storage == inputs.STORE_F32 else 1e-2
+        assert np.all(err <= tol), (r.rid, r.kind, r.storage, err)
+
+
+def test_shortest_remaining_work_first_keeps_results_unchanged():
+    trace = small_trace(n=6, seed=7)
+    a = serve.Server(chunk=8, large_cells=2000, srpt=True).run(trace, realtime=False)
+    b = serve.Server(chunk=8, large_cells=2000, srpt=False).run(trace, realtime=False)
+    assert [x.digest for x in a] == [y.digest for y in b]
+
+
+def test_admission_respects_a_shrunken_budget():
+    trace = small_trace(n=6, seed=4)
+    sizes = [capi.grlb_bytes_for(r.case.params) for r in trace]
+    budget = 1.5 * max(sizes)
+    srv = serve.Server(hbm_budget=budget, chunk=10)
+    res = srv.run(trace, realtime=False)
+    assert len(res) == len(trace) and all(r.digest for r in res)
+    assert srv.peak_bytes <= budget
+    ref = serve.Server(chunk=10).run(trace, realtime=False)
+    assert [a.digest for a in res] == [b.digest for b in ref]
+
+
+def test_request_larger_than_budget_is_refused():
+    trace = small_trace(n=1, seed=5)
+    with pytest.raises(capi.GrlbError):
+        serve.Server(hbm_budget=1000).run(trace, realtime=False)
