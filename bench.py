@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -46,6 +47,21 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_max_over_ranks(values, ws, device):
+    """Element-wise maximum of per-rank values (timings) over all ranks; the identity at N = 1."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_mlups(ws, cells_per_rank, sweeps, seconds):
+    """Whole-job throughput: the cell updates of all ranks over the slowest rank's time."""
+    return ws * cells_per_rank * sweeps / seconds / 1e6
 
 
 def kernel_source_sha():
@@ -258,13 +274,10 @@ def run_ours(args):
         barrier()
 
     # max over ranks
-    vals = torch.tensor([ms, te, float(np.median(sweep_ms))], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms, te, sweep_med = vals.tolist()
+    ms, te, sweep_med = reduce_max_over_ranks([ms, te, float(np.median(sweep_ms))], ws, dev)
     ms_per_step = ms / args.steps
-    lups = ws * N * SWEEPS_PER_STEP * args.steps / (ms / 1e3)
-    e2e_lups = ws * N * SWEEPS_PER_STEP * e2e_steps / te
+    lups = job_mlups(ws, N, SWEEPS_PER_STEP * args.steps, ms / 1e3) * 1e6
+    e2e_lups = job_mlups(ws, N, SWEEPS_PER_STEP * e2e_steps, te) * 1e6
 
     peak, peak_src = measured_peaks()
     bpl = BYTES_PER_LUP[storage]
@@ -411,6 +424,123 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """Storage precision modes side by side: FP32, FP16 and BF16 shifted populations (FP32
+    arithmetic).  Accuracy: Taylor-Green 64^3 after 100 steps and the Sod tube (400 cells, 1000
+    steps) against the FP64 oracle, relative L-inf / L1 of rho, u, T.  Speed: the plain sweep
+    at 256^3 (CUDA events, 40 sweeps after warm-up) against the HBM roofline of each mode."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    names = {0: "f32", 1: "f16", 2: "bf16"}
+
+    def prim(Q, gamma):
+        rho = Q[0]
+        u = Q[1:4] / rho
+        p = (gamma - 1) * (Q[4] - 0.5 * rho * (u * u).sum(0))
+        return rho, u, p / rho
+
+    def errs(a, b):
+        out = {}
+        for nm, x, y in zip(("rho", "u", "T"), a, b):
+            out[nm] = {"linf": float(np.abs(x - y).max() / np.abs(y).max()),
+                       "l1": float(np.abs(x - y).sum() / np.abs(y).sum())}
+        return out
+
+    cases = {"tgv64_100": (lambda st: inputs.tgv3d(64, storage=st), 100),
+             "sod400_1000": (lambda st: inputs.sod(400, storage=st), 1000)}
+    acc = {}
+    for cname, (mk, nsteps) in cases.items():
+        ref = mk(0)
+        o = oracle.Oracle(ref.params)
+        o.init_primitive(ref.rho, ref.u, ref.p)
+        o.step(nsteps)
+        R = prim(o.conserved(), ref.params.gamma)
+        for st in (0, 1, 2):
+            c = mk(st)
+            d = capi.Domain(c.params)
+            d.init(c.rho, c.u, c.p)
+            d.step(nsteps)
+            acc.setdefault(names[st], {})[cname] = errs(prim(d.conserved(), c.params.gamma), R)
+            d.close()
+    speed = {}
+    peak, src = measured_peaks()
+    for st in (0, 1, 2):
+        c = inputs.tgv3d(args.n, storage=st)
+        d = capi.Domain(c.params)
+        d.init(c.rho, c.u, c.p)
+        d.step(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        d.step(40)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 40
+        N = c.params.ncells
+        gbs = BYTES_PER_LUP[st] * N / (ms / 1e3) / 1e9
+        speed[names[st]] = {"ms_per_sweep": ms, "mlups": N / (ms / 1e3) / 1e6,
+                            "bytes_per_lup": BYTES_PER_LUP[st], "achieved_gbs": gbs,
+                            "roofline_frac": gbs / peak}
+        d.close()
+    line = {"metric": "precision modes: error vs FP64 oracle and sweep MLUP/s", "unit": "MLUP/s",
+            "value": speed["f16"]["mlups"], "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32 / f16 / bf16 storage, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": f"tgv{args.n} sweep speed; tgv64 x100 and sod400 x1000 accuracy",
+                       "peak_gbs": peak, "peak_source": src},
+            "accuracy": acc, "speed": speed}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tgv_series(args):
+    """Supersonic Taylor-Green at n^3 (M0 1.25, Re 1600, Sutherland, RLB + sensor, FP32) for up
+    to --run-steps steps with FP64 diagnostics every 50 steps: volume-averaged kinetic energy
+    and solenoidal / dilatational dissipation (normalised by rho0 V0^2 and rho0 V0^3 / L0) in
+    convective time t_c, until the run ends or the state stops being finite."""
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    c = inputs.tgv3d(args.n)
+    prm = c.params
+    N = prm.ncells
+    d = capi.Domain(prm)
+    d.init(c.rho, c.u, c.p)
+    s = prm.dt / prm.dx
+    series = []
+    first_bad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step = 0
+    while step < args.run_steps:
+        d.step(49)
+        d.step_diag()
+        g = d.diag()
+        step = g["step"]
+        ke = g["ke"] / (s * s) / N
+        eps_s = g["eps_s"] * prm.dx ** 2 / prm.dt ** 3 / N
+        eps_d = g["eps_d"] * prm.dx ** 2 / prm.dt ** 3 / N
+        series.append({"step": step, "t_c": step * prm.dt, "E_k": ke, "eps_s": eps_s,
+                       "eps_d": eps_d, "n_sensor": g["n_sensor"], "n_floor": g["n_floor"],
+                       "n_nan": g["n_nan"]})
+        if g["n_nan"] > 0 or not math.isfinite(ke):
+            first_bad = step
+            break
+    wall = time.perf_counter() - t0
+    d.close()
+    line = {"metric": "Taylor-Green run with FP64 diagnostics every 50 steps", "unit": "MLUP/s",
+            "value": N * step / wall / 1e6, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"tgv{args.n}_f32_rlb_sensor", "steps_requested": args.run_steps,
+                       "omega": prm.omega_mom, "fmu": c.meta["fmu"]},
+            "steps_run": step, "first_nonfinite_step": first_bad, "wall_s": wall,
+            "series": series}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,7 +550,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve"])
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series"])
+    ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=40)
     args = ap.parse_args()
@@ -432,6 +563,10 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "precision":
+        return run_precision(args)
+    if args.workload == "tgv-series":
+        return run_tgv_series(args)
     return run_ours(args)
 
 

@@ -55,18 +55,23 @@ struct DomainDev {
 };
 
 // ---- storage traits ----------------------------------------------------------------------
+// `scaled`: the stored value is deviation x enc[k] (FP16 only; FP32 and BF16 store the
+// deviation itself, so no scale multiplications are compiled in for them).
 template <int S> struct Store;
 template <> struct Store<S_F32> {
+    static constexpr bool scaled = false;
     using T = float;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { __stcs(p, v); }
 };
 template <> struct Store<S_F16> {
+    static constexpr bool scaled = true;
     using T = __half;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<S_BF16> {
+    static constexpr bool scaled = false;
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
         return __bfloat162float(__ldg(p));
@@ -85,11 +90,13 @@ struct CellDiag {
 };
 
 // ---- Algorithm 1 on one cell --------------------------------------------------------------
-// In: d[k][i] = pulled deviations.  Out: o[k][i] = post-collision deviations.
-// For the regularized collision the outputs depend only on (dQ_k, J*_k), so d may alias o.
-template <int COLL, bool DIAG>
+// In: d[k][i] = pulled stored values (deviations, x enc[k] when scaled).  Out: o[k][i] = the
+// values to store (post-collision deviations in the same units).  The storage scale is
+// applied to the 20 moments instead of the 35 populations.
+template <int S, int COLL, bool DIAG>
 __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF][NQ],
                                         float (&o)[NF][NQ], CellDiag* cd) {
+    constexpr bool SC = Store<S>::scaled;
     // moments (Alg. 1): dQ_k = sum_i d_ki, dJ_k = sum_i d_ki c_i
     float dQ[NF], dJ[NF][3];
 #pragma unroll
@@ -98,6 +105,12 @@ __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF]
         dJ[k][0] = d[k][1] - d[k][2];
         dJ[k][1] = d[k][3] - d[k][4];
         dJ[k][2] = d[k][5] - d[k][6];
+        if (SC) {
+            dQ[k] *= D.dec[k];
+            dJ[k][0] *= D.dec[k];
+            dJ[k][1] *= D.dec[k];
+            dJ[k][2] *= D.dec[k];
+        }
     }
     const float gm1 = D.gm1;
     // primitives with positivity floors (Alg. 1); Q_k themselves stay unfloored
@@ -250,11 +263,12 @@ __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF]
             const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
             const float omh = D.omega[r] - chi * D.omega_red[r];
             const float onem = 1.0f - omh;
+            const float sc = SC ? D.enc[k] : 1.0f;
             float js[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) js[c] = Pd[k][c] + onem * (nA[k][c] - Fd[k][c]);
-            const float q0 = 0.25f * dQ[k];
-            const float q1 = 0.125f * dQ[k];
+            for (int c = 0; c < 3; ++c) js[c] = (Pd[k][c] + onem * (nA[k][c] - Fd[k][c])) * sc;
+            const float q0 = 0.25f * dQ[k] * sc;
+            const float q1 = 0.125f * dQ[k] * sc;
             o[k][0] = q0;
             o[k][1] = q1 + 0.5f * js[0];
             o[k][2] = q1 - 0.5f * js[0];
@@ -269,15 +283,17 @@ __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF]
         for (int k = 0; k < NF; ++k) {
             const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
             const float om = D.omega[r];
-            const float q1 = 0.125f * dQ[k];
+            const float sc = SC ? D.enc[k] : 1.0f;
+            const float q1 = 0.125f * dQ[k] * sc;
+            const float px = 0.5f * Pd[k][0] * sc, py = 0.5f * Pd[k][1] * sc, pz = 0.5f * Pd[k][2] * sc;
             float fe[NQ];
-            fe[0] = 0.25f * dQ[k];
-            fe[1] = q1 + 0.5f * Pd[k][0];
-            fe[2] = q1 - 0.5f * Pd[k][0];
-            fe[3] = q1 + 0.5f * Pd[k][1];
-            fe[4] = q1 - 0.5f * Pd[k][1];
-            fe[5] = q1 + 0.5f * Pd[k][2];
-            fe[6] = q1 - 0.5f * Pd[k][2];
+            fe[0] = 0.25f * dQ[k] * sc;
+            fe[1] = q1 + px;
+            fe[2] = q1 - px;
+            fe[3] = q1 + py;
+            fe[4] = q1 - py;
+            fe[5] = q1 + pz;
+            fe[6] = q1 - pz;
 #pragma unroll
             for (int i = 0; i < NQ; ++i) o[k][i] = fmaf(om, fe[i] - d[k][i], d[k][i]);
         }

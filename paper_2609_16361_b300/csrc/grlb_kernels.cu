@@ -49,14 +49,16 @@ __device__ __forceinline__ void load_cell(const DomainDev& D, const typename Sto
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         const typename St::T* b = fin + (int64_t)(7 * k) * pl;
-        const float sc = D.dec[k];
-        d[k][0] = St::ld(b + P.c) * sc;
-        d[k][1] = P.gl ? D.ghostL[k] : St::ld(b + pl + P.xm) * sc;
-        d[k][2] = P.gr ? D.ghostR[k] : St::ld(b + 2 * pl + P.xp) * sc;
-        d[k][3] = St::ld(b + 3 * pl + P.ym) * sc;
-        d[k][4] = St::ld(b + 4 * pl + P.yp) * sc;
-        d[k][5] = St::ld(b + 5 * pl + P.zm) * sc;
-        d[k][6] = St::ld(b + 6 * pl + P.zp) * sc;
+        // stored units: ghosts (physical deviations) take the storage scale
+        const float gl = St::scaled ? D.ghostL[k] * D.enc[k] : D.ghostL[k];
+        const float gr = St::scaled ? D.ghostR[k] * D.enc[k] : D.ghostR[k];
+        d[k][0] = St::ld(b + P.c);
+        d[k][1] = P.gl ? gl : St::ld(b + pl + P.xm);
+        d[k][2] = P.gr ? gr : St::ld(b + 2 * pl + P.xp);
+        d[k][3] = St::ld(b + 3 * pl + P.ym);
+        d[k][4] = St::ld(b + 4 * pl + P.yp);
+        d[k][5] = St::ld(b + 5 * pl + P.zm);
+        d[k][6] = St::ld(b + 6 * pl + P.zp);
     }
 }
 
@@ -66,11 +68,9 @@ __device__ __forceinline__ void store_cell(const DomainDev& D, typename Store<S>
     using St = Store<S>;
     const int64_t pl = D.plane;
 #pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        const float sc = D.enc[k];
+    for (int k = 0; k < NF; ++k)
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) St::st(fout + (int64_t)(7 * k + i) * pl + c, o[k][i] * sc);
-    }
+        for (int i = 0; i < NQ; ++i) St::st(fout + (int64_t)(7 * k + i) * pl + c, o[k][i]);
 }
 
 // Block-level FP64 reduction of the per-cell diagnostics into one NDIAG record.
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
         const PullIdx P = pull_index(D, x, y, z);
         float d[NF][NQ], o[NF][NQ];
         load_cell<S>(D, fin, P, d);
-        collide<COLL, DIAG>(D, d, o, &cd);
+        collide<S, COLL, DIAG>(D, d, o, &cd);
         store_cell<S>(D, fout, P.c, o);
     }
     if (DIAG) {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __res
             const PullIdx P = pull_index(D, x, y, z);
             float d[NF][NQ], o[NF][NQ];
             load_cell<S>(D, fin, P, d);
-            collide<COLL, false>(D, d, o, nullptr);
+            collide<S, COLL, false>(D, d, o, nullptr);
             store_cell<S>(D, fout, P.c, o);
         }
     }
