@@ -119,6 +119,15 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
 grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const double* u,
                                        const double* p);
 
+/* Source term of the conservation laws (d_t Q + div Phi = S, Sec. 2.1), projected onto the
+ * lattice weights after the collision (Algorithm 1, last step: + w_i S_k) in every following
+ * sweep of this domain.  S is a device pointer to 5 planes of N FP32 values (rho, m_x, m_y,
+ * m_z, E rates per unit physical time, x fastest), or NULL to remove it.  The library keeps
+ * the pointer, does not own the memory, and reads it when each sweep runs: the caller may
+ * rewrite it between sweeps in stream order (e.g. S at the mid-point time of the next step).
+ * Domains with a source cannot join a batch. */
+grlb_status grlb_set_source_device(grlb_domain* d, const float* S);
+
 /* Enqueue nsteps >= 0 plain sweeps (Algorithm 1 on every cell + exact streaming). */
 grlb_status grlb_step(grlb_domain* d, int nsteps);
 

@@ -67,6 +67,8 @@ def lib():
             dp = C.POINTER(C.c_double)
             L.orc_step.argtypes = [C.POINTER(_Params), dp, dp, C.c_void_p]
             L.orc_step.restype = C.c_int
+            L.orc_step_src.argtypes = [C.POINTER(_Params), dp, dp, C.c_void_p, C.c_void_p]
+            L.orc_step_src.restype = C.c_int
             L.orc_cell.argtypes = [C.POINTER(_Params), dp, dp, C.POINTER(CellInfo)]
             L.orc_cell.restype = C.c_int
             L.orc_init_equilibrium.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp, dp]
@@ -141,14 +143,27 @@ class Oracle:
                                    _dp(pL), _dp(self.f))
         self.steps = 0
 
-    def step(self, n: int = 1, keep_cells: bool = False):
+    def source_lattice(self, S):
+        """Physical source rates (5, N) -> lattice units per step: rho dt, m dt s, E dt s^2."""
+        s, dt = self.s, self.prm.dt
+        out = np.array(S, dtype=np.float64, copy=True)
+        out[0] *= dt
+        out[1:4] *= dt * s
+        out[4] *= dt * s * s
+        return np.ascontiguousarray(out)
+
+    def step(self, n: int = 1, keep_cells: bool = False, source=None):
+        """Advance n steps.  source(step) -> physical source rates (5, N) applied in that step
+        (projected as w_i S_k after the collision, Alg. 1 step 9), or None."""
         L = lib()
         for it in range(n):
             cells = None
             if keep_cells and it == n - 1:
                 cells = np.zeros(self.N, CELL_DTYPE)
-            rc = L.orc_step(C.byref(self.P), _dp(self.f), _dp(self.g),
-                            None if cells is None else cells.ctypes.data_as(C.c_void_p))
+            S = None if source is None else self.source_lattice(source(self.steps))
+            rc = L.orc_step_src(C.byref(self.P), _dp(self.f), _dp(self.g),
+                                None if cells is None else cells.ctypes.data_as(C.c_void_p),
+                                None if S is None else S.ctypes.data_as(C.c_void_p))
             if rc != 0:
                 raise RuntimeError("oracle: singular reconstruction system")
             self.f, self.g = self.g, self.f

@@ -344,7 +344,16 @@ size_t orc_cell_info_size(void) { return sizeof(orc_cell_info); }
  * fin holds post-collision populations at time n; fout receives those at time n+1.
  * Pull form of the exact streaming f(x + c_i, n+1) = f*(x, n).
  * cell_out (nullable): per-cell info records (N entries) of the pre-collision state n+1.   */
+/* src (nullable): per-cell source S_k in lattice units per step, layout src[k*N + idx]; its
+ * projection w_i S_k is added to the post-collision populations (Alg. 1 step 9). */
+int orc_step_src(const orc_params* P, const double* fin, double* fout, orc_cell_info* cell_out,
+                 const double* src);
 int orc_step(const orc_params* P, const double* fin, double* fout, orc_cell_info* cell_out) {
+    return orc_step_src(P, fin, fout, cell_out, NULL);
+}
+
+int orc_step_src(const orc_params* P, const double* fin, double* fout, orc_cell_info* cell_out,
+                 const double* src) {
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     const long N = (long)nx * ny * nz;
     double gl[NP], gr[NP];
@@ -375,6 +384,9 @@ int orc_step(const orc_params* P, const double* fin, double* fout, orc_cell_info
                     }
                 orc_cell_info* inf = cell_out ? &cell_out[idx] : NULL;
                 if (orc_cell(P, fhat, fstar, inf) != 0) err |= 1;
+                if (src)
+                    for (int k = 0; k < NF; ++k)
+                        for (int i = 0; i < NQ; ++i) fstar[k * NQ + i] += WI[i] * src[(long)k * N + idx];
                 for (int q = 0; q < NP; ++q) fout[(long)q * N + idx] = fstar[q];
             }
     }

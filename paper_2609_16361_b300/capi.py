@@ -86,6 +86,7 @@ def lib():
             "grlb_init_primitive": ([vp, dp, dp, dp], i32),
             "grlb_init_primitive_device": ([vp, vp, vp, vp], i32),
             "grlb_step": ([vp, i32], i32),
+            "grlb_set_source_device": ([vp, vp], i32),
             "grlb_step_diag": ([vp], i32),
             "grlb_diag_read": ([vp, C.POINTER(grlb_diag)], i32),
             "grlb_read_conserved": ([vp, dp], i32),
@@ -113,7 +114,7 @@ def lib():
 def exported_symbols():
     return ["grlb_last_error", "grlb_version", "grlb_create", "grlb_destroy", "grlb_set_stream",
             "grlb_device_bytes", "grlb_bytes_for", "grlb_init_primitive",
-            "grlb_init_primitive_device", "grlb_step",
+            "grlb_init_primitive_device", "grlb_set_source_device", "grlb_step",
             "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
@@ -171,6 +172,12 @@ def grlb_init_primitive(h, rho, u, p):
 def grlb_init_primitive_device(h, rho_ptr, u_ptr, p_ptr):
     """Device pointers (ints, e.g. torch tensor .data_ptr()) of FP64 fields on the device."""
     check(lib().grlb_init_primitive_device(h, rho_ptr, u_ptr, p_ptr))
+
+
+def grlb_set_source_device(h, ptr):
+    """Device pointer (int, e.g. a float32 torch tensor's data_ptr()) of 5 x N source rates in
+    physical units, or None."""
+    check(lib().grlb_set_source_device(h, ptr))
 
 
 def grlb_step(h, n):

@@ -163,6 +163,11 @@ static void fill_domain_dev(grlb_domain* d) {
         D.enc[k] = storage_scale(p.storage, M[k]);
         D.dec[k] = 1.0f / D.enc[k];
     }
+    D.src = nullptr;
+    D.src_scale[0] = (float)p.dt;
+    D.src_scale[1] = (float)(p.dt * s);
+    D.src_scale[2] = (float)(p.dt * s * s);
+    D.pad1 = 0;
 }
 
 static void choose_launch(grlb_domain* d) {
@@ -280,6 +285,12 @@ static grlb_status sweep_once(grlb_domain* d, bool diag) {
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     d->D.cur = c ^ 1;
     d->steps += 1;
+    return GRLB_OK;
+}
+
+grlb_status grlb_set_source_device(grlb_domain* d, const float* S) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    d->D.src = S;
     return GRLB_OK;
 }
 
@@ -502,6 +513,10 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
         if (!domains[i]) {
             delete b;
             return fail(GRLB_EINVAL, "NULL domain in batch");
+        }
+        if (domains[i]->D.src) {
+            delete b;
+            return fail(GRLB_EINVAL, "batched domains cannot carry a source term");
         }
         b->doms.push_back(domains[i]);
         b->active.push_back(1);

@@ -52,6 +52,9 @@ struct DomainDev {
     float ghostR[5];       // deviation of f_{k,-x} in the x = nx ghost
     float dec[5];          // per-field storage scale: value = stored * dec[k]
     float enc[5];          // stored = value * enc[k]
+    const float* src;      // optional source S_k (5 planes, physical rates), or null
+    float src_scale[3];    // physical rate -> lattice units per step (rho, momentum, energy)
+    int32_t pad1;
 };
 
 // ---- storage traits ----------------------------------------------------------------------
@@ -88,6 +91,20 @@ struct CellDiag {
     float rho_raw, p_raw;  // unfloored
     int floored, nan, sensor;
 };
+
+// Source projection of Alg. 1 step 9: o_{k,i} += w_i S_k (lattice units, storage units).
+template <int S>
+__device__ __forceinline__ void add_source(const DomainDev& D, int32_t c, float (&o)[NF][NQ]) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
+        float sk = __ldg(D.src + (int64_t)k * D.plane + c) * D.src_scale[r];
+        if (Store<S>::scaled) sk *= D.enc[k];
+        o[k][0] += 0.25f * sk;
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) o[k][i] += 0.125f * sk;
+    }
+}
 
 // ---- Algorithm 1 on one cell --------------------------------------------------------------
 // In: d[k][i] = pulled stored values (deviations, x enc[k] when scaled).  Out: o[k][i] = the

@@ -124,7 +124,7 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
 // One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
 // parameter, so its constants are read as constant-bank operands of the arithmetic (a record
 // held in shared memory costs a load per use and ~15% of the sweep's time).
-template <int S, int COLL, bool DIAG>
+template <int S, int COLL, bool DIAG, bool SRC>
 __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ DomainDev D,
                                                     const void* __restrict__ fin_v,
                                                     void* __restrict__ fout_v,
@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
         float d[NF][NQ], o[NF][NQ];
         load_cell<S>(D, fin, P, d);
         collide<S, COLL, DIAG>(D, d, o, &cd);
+        if (SRC) add_source<S>(D, P.c, o);
         store_cell<S>(D, fout, P.c, o);
     }
     if (DIAG) {
@@ -311,10 +312,15 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
 template <int S, int COLL>
 static cudaError_t launch_sweep_t(const DomainDev& D, const void* fin, void* fout, bool diag,
                                   double* partials, dim3 grid, dim3 block, cudaStream_t st) {
-    if (diag)
-        sweep_kernel<S, COLL, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    const bool src = D.src != nullptr;
+    if (diag && src)
+        sweep_kernel<S, COLL, true, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    else if (diag)
+        sweep_kernel<S, COLL, true, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    else if (src)
+        sweep_kernel<S, COLL, false, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
     else
-        sweep_kernel<S, COLL, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
+        sweep_kernel<S, COLL, false, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
     return cudaGetLastError();
 }
 
