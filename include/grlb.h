@@ -59,7 +59,9 @@ typedef struct {
     double prandtl;             /* kappa = mu c_p / Pr, c_p = gamma/(gamma-1)  (> 0)        */
     double T_ref;               /* Sutherland reference temperature (T = p/rho, > 0)        */
     int32_t sutherland;         /* 1: mu(T) by the Sutherland law of Listing 1; 0: constant */
-    int32_t pad0;
+    int32_t streaming;          /* 0: two population buffers (pull); 1: one buffer updated in
+                                   place by the AA pattern (half the memory, same traffic,
+                                   bitwise the same results); sources and batches need 0     */
     double T_S;                 /* Sutherland constant relative to T_ref (0.4042)           */
     double omega_rho, omega_mom, omega_E; /* per-field relaxation 1/tau_LB, in (0, 2]       */
     double omega_min;           /* sensor floor rate (Listing 2)                            */

@@ -33,7 +33,7 @@ class grlb_params(C.Structure):
                 ("collision", C.c_int32), ("storage", C.c_int32), ("dx", C.c_double),
                 ("dt", C.c_double), ("gamma", C.c_double), ("mu_ref", C.c_double),
                 ("prandtl", C.c_double), ("T_ref", C.c_double), ("sutherland", C.c_int32),
-                ("pad0", C.c_int32), ("T_S", C.c_double), ("omega_rho", C.c_double),
+                ("streaming", C.c_int32), ("T_S", C.c_double), ("omega_rho", C.c_double),
                 ("omega_mom", C.c_double), ("omega_E", C.c_double), ("omega_min", C.c_double),
                 ("sensor_gain", C.c_double), ("J_min", C.c_double), ("rho_min", C.c_double),
                 ("p_min", C.c_double), ("ref_rho", C.c_double), ("ref_p", C.c_double),

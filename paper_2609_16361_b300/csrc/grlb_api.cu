@@ -38,6 +38,11 @@ grlb_status cuda_fail(cudaError_t e, const char* what) {
 
 size_t elem_bytes(int storage) { return storage == GRLB_STORE_F32 ? 4 : 2; }
 
+// One-buffer Dirichlet domains keep the populations that leave through the ends in an odd step.
+size_t outflow_bytes(const grlb_params& p) {
+    return (p.streaming && p.bc == GRLB_BC_X_DIRICHLET_EQ) ? 10 * (size_t)p.ny * p.nz * elem_bytes(p.storage) : 0;
+}
+
 // Power-of-two storage scale for the 16-bit modes: deviations of field k are divided by a
 // reference magnitude M_k (rho_ref, rho_ref c_ref, E_ref) and multiplied by 2^8 so that
 // typical fluctuations sit well inside the FP16 normal range.  FP32 and BF16 use 1.
@@ -80,6 +85,7 @@ static grlb_status validate(const grlb_params* p) {
     if (p->collision != GRLB_COLL_BGK && p->collision != GRLB_COLL_RLB_SENSOR)
         return fail(GRLB_EINVAL, "bad collision");
     if (p->storage < GRLB_STORE_F32 || p->storage > GRLB_STORE_BF16) return fail(GRLB_EINVAL, "bad storage");
+    if (p->streaming != 0 && p->streaming != 1) return fail(GRLB_EINVAL, "streaming must be 0 or 1");
     if (!(p->dx > 0) || !(p->dt > 0)) return fail(GRLB_EINVAL, "dx, dt must be > 0");
     if (!(p->gamma > 1)) return fail(GRLB_EINVAL, "gamma must be > 1");
     if (!(p->mu_ref >= 0) || !(p->prandtl > 0) || !(p->T_ref > 0) || !(p->T_S >= 0))
@@ -164,6 +170,7 @@ static void fill_domain_dev(grlb_domain* d) {
         D.dec[k] = 1.0f / D.enc[k];
     }
     D.src = nullptr;
+    D.outflow = nullptr;
     D.src_scale[0] = (float)p.dt;
     D.src_scale[1] = (float)(p.dt * s);
     D.src_scale[2] = (float)(p.dt * s * s);
@@ -186,8 +193,9 @@ size_t grlb_bytes_for(const grlb_params* p) {
     tmp.P = *p;
     choose_launch(&tmp);
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    return 2 * 35 * N * elem_bytes(p->storage) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
-           NDIAG * 8;
+    const size_t nbuf = p->streaming ? 1 : 2;
+    return nbuf * 35 * N * elem_bytes(p->storage) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+           NDIAG * 8 + outflow_bytes(*p);
 }
 
 grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
@@ -207,7 +215,12 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     cudaError_t e = cudaSuccess;
     d->D.buf[0] = d->D.buf[1] = nullptr;
     e = cudaMalloc(&d->D.buf[0], pop_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&d->D.buf[1], pop_bytes);
+    if (e == cudaSuccess) {
+        if (p->streaming) d->D.buf[1] = d->D.buf[0];  // one buffer, updated in place
+        else e = cudaMalloc(&d->D.buf[1], pop_bytes);
+    }
+    if (e == cudaSuccess && p->streaming && p->bc == GRLB_BC_X_DIRICHLET_EQ)
+        e = cudaMalloc(&d->D.outflow, outflow_bytes(*p));
     if (e == cudaSuccess)
         e = cudaMalloc(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&d->diag_dev, NDIAG * sizeof(double));
@@ -218,7 +231,8 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
         return fail(e == cudaErrorMemoryAllocation ? GRLB_ENOMEM : GRLB_ECUDA,
                     std::string("grlb_create: ") + cudaGetErrorString(e));
     }
-    d->bytes = 2 * pop_bytes + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 + NDIAG * 8;
+    d->bytes = (p->streaming ? 1 : 2) * pop_bytes + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+               NDIAG * 8 + outflow_bytes(*p);
     for (int k = 0; k < NDIAG; ++k) d->diag_host[k] = 0.0;
     *out = d;
     return GRLB_OK;
@@ -229,7 +243,8 @@ void grlb_destroy(grlb_domain* d) {
     if (d->stream) cudaStreamSynchronize(d->stream);
     else cudaDeviceSynchronize();
     cudaFree(d->D.buf[0]);
-    cudaFree(d->D.buf[1]);
+    if (d->D.buf[1] != d->D.buf[0]) cudaFree(d->D.buf[1]);
+    cudaFree(d->D.outflow);
     cudaFree(d->partials);
     cudaFree(d->diag_dev);
     cudaFreeHost(d->diag_host);
@@ -256,7 +271,7 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
     if (e == cudaSuccess) {
         d->D.cur = 0;
         e = grlb::launch_init(d->D, d->P.storage, d->D.buf[0], stage, stage + N, stage + 4 * N, d->s,
-                              d->gm1, d->rho_ref, d->p_ref, d->stream);
+                              d->gm1, d->rho_ref, d->p_ref, d->P.streaming, d->stream);
     }
     cudaError_t e2 = cudaFreeAsync(stage, d->stream);
     if (e == cudaSuccess) e = e2;
@@ -271,25 +286,35 @@ grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const 
     if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive_device: NULL argument");
     d->D.cur = 0;
     cudaError_t e = grlb::launch_init(d->D, d->P.storage, d->D.buf[0], rho, u, p, d->s, d->gm1, d->rho_ref,
-                                      d->p_ref, d->stream);
+                                      d->p_ref, d->P.streaming, d->stream);
     if (e != cudaSuccess) return cuda_fail(e, "grlb_init_primitive_device");
     d->steps = 0;
     d->diag_step = -1;
     return GRLB_OK;
 }
 
+// Two buffers: read buf[cur], write the other.  One buffer (AA): the state after an even
+// number of steps sits in swapped slots, so step n+1 is an odd-type step when n is even.
 static grlb_status sweep_once(grlb_domain* d, bool diag) {
     const int c = d->D.cur;
-    cudaError_t e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, d->D.buf[c], d->D.buf[c ^ 1],
-                                       diag, d->partials, d->grid, d->block, d->stream);
+    cudaError_t e;
+    if (d->P.streaming) {
+        const int pattern = (d->steps % 2 == 0) ? 1 : 2;
+        e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, pattern, d->D.buf[0], d->D.buf[0], diag,
+                               d->partials, d->grid, d->block, d->stream);
+    } else {
+        e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, 0, d->D.buf[c], d->D.buf[c ^ 1], diag,
+                               d->partials, d->grid, d->block, d->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
-    d->D.cur = c ^ 1;
+    if (!d->P.streaming) d->D.cur = c ^ 1;
     d->steps += 1;
     return GRLB_OK;
 }
 
 grlb_status grlb_set_source_device(grlb_domain* d, const float* S) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    if (S && d->P.streaming) return fail(GRLB_EINVAL, "a source needs two-buffer streaming (streaming = 0)");
     d->D.src = S;
     return GRLB_OK;
 }
@@ -341,8 +366,9 @@ grlb_status grlb_read_conserved(grlb_domain* d, double* out) {
     const size_t N = (size_t)d->D.plane;
     double* stage = nullptr;
     GRLB_CU(cudaMallocAsync(&stage, 5 * N * sizeof(double), d->stream));
+    const int gather = (d->P.streaming && (d->steps & 1)) ? 1 : 0;
     cudaError_t e = grlb::launch_conserved(d->D, d->P.storage, d->D.buf[d->D.cur], stage, d->s, d->rho_ref,
-                                           d->E_ref, d->stream);
+                                           d->E_ref, gather, d->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, stage, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, d->stream);
     cudaError_t e2 = cudaFreeAsync(stage, d->stream);
     if (e == cudaSuccess) e = e2;
@@ -388,7 +414,8 @@ const uint64_t kMagic = 0x3142524c47ULL;  // "GLRB1"
 grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
     if (!d || !bytes) return fail(GRLB_EINVAL, "grlb_save: NULL argument");
     const size_t pop = 35 * (size_t)d->D.plane * elem_bytes(d->P.storage);
-    const size_t need = sizeof(SaveHeader) + pop;
+    const size_t ob = outflow_bytes(d->P);
+    const size_t need = sizeof(SaveHeader) + pop + ob;
     if (!buf) {
         *bytes = need;
         return GRLB_OK;
@@ -398,6 +425,9 @@ grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
     std::memcpy(buf, &h, sizeof h);
     GRLB_CU(cudaMemcpyAsync(static_cast<char*>(buf) + sizeof h, d->D.buf[d->D.cur], pop, cudaMemcpyDeviceToHost,
                             d->stream));
+    if (ob)
+        GRLB_CU(cudaMemcpyAsync(static_cast<char*>(buf) + sizeof h + pop, d->D.outflow, ob, cudaMemcpyDeviceToHost,
+                                d->stream));
     GRLB_CU(cudaStreamSynchronize(d->stream));
     *bytes = need;
     return GRLB_OK;
@@ -406,7 +436,8 @@ grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
 grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
     if (!d || !buf) return fail(GRLB_EINVAL, "grlb_load: NULL argument");
     const size_t pop = 35 * (size_t)d->D.plane * elem_bytes(d->P.storage);
-    if (bytes < sizeof(SaveHeader) + pop) return fail(GRLB_EINVAL, "grlb_load: buffer too small");
+    const size_t ob = outflow_bytes(d->P);
+    if (bytes < sizeof(SaveHeader) + pop + ob) return fail(GRLB_EINVAL, "grlb_load: buffer too small");
     SaveHeader h;
     std::memcpy(&h, buf, sizeof h);
     if (h.magic != kMagic || h.N != d->D.plane || h.storage != d->P.storage)
@@ -414,6 +445,9 @@ grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
     d->D.cur = 0;
     GRLB_CU(cudaMemcpyAsync(d->D.buf[0], static_cast<const char*>(buf) + sizeof h, pop, cudaMemcpyHostToDevice,
                             d->stream));
+    if (ob)
+        GRLB_CU(cudaMemcpyAsync(d->D.outflow, static_cast<const char*>(buf) + sizeof h + pop, ob,
+                                cudaMemcpyHostToDevice, d->stream));
     GRLB_CU(cudaStreamSynchronize(d->stream));
     d->steps = h.steps;
     d->diag_step = -1;
@@ -514,9 +548,9 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
             delete b;
             return fail(GRLB_EINVAL, "NULL domain in batch");
         }
-        if (domains[i]->D.src) {
+        if (domains[i]->D.src || domains[i]->P.streaming) {
             delete b;
-            return fail(GRLB_EINVAL, "batched domains cannot carry a source term");
+            return fail(GRLB_EINVAL, "batched domains need two-buffer streaming and no source term");
         }
         b->doms.push_back(domains[i]);
         b->active.push_back(1);
@@ -663,6 +697,7 @@ extern "C" grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* 
     if (st != GRLB_OK) return st;
     if (!f_in || !f_out || !diag_out) return fail(GRLB_EINVAL, "grlb_step_diag_noalloc: NULL pointer");
     if (f_in == f_out) return fail(GRLB_EINVAL, "grlb_step_diag_noalloc: f_in and f_out must differ");
+    if (p->streaming) return fail(GRLB_EINVAL, "grlb_step_diag_noalloc: two-buffer streaming only");
     grlb_domain tmp;  // host-side description only; owns no memory
     tmp.P = *p;
     fill_domain_dev(&tmp);
@@ -676,7 +711,8 @@ extern "C" grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* 
     st = noalloc_scratch(&scratch);
     if (st != GRLB_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GRLB_CU(grlb::launch_sweep(tmp.D, p->storage, p->collision, f_in, f_out, true, scratch, tmp.grid, tmp.block, s));
+    GRLB_CU(grlb::launch_sweep(tmp.D, p->storage, p->collision, 0, f_in, f_out, true, scratch, tmp.grid, tmp.block,
+                               s));
     GRLB_CU(grlb::launch_diag_finalize(scratch, tmp.nblocks, diag_out, s));
     return GRLB_OK;
 }

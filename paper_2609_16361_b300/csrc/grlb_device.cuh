@@ -52,6 +52,8 @@ struct DomainDev {
     float ghostR[5];       // deviation of f_{k,-x} in the x = nx ghost
     float dec[5];          // per-field storage scale: value = stored * dec[k]
     float enc[5];          // stored = value * enc[k]
+    void* outflow;         // one-buffer X_DIRICHLET_EQ: populations leaving through x = -1 / nx in
+                           // an odd step, [side][k][y + ny z] (side 0: -x at x = 0, 1: +x at nx-1)
     const float* src;      // optional source S_k (5 planes, physical rates), or null
     float src_scale[3];    // physical rate -> lattice units per step (rho, momentum, energy)
     int32_t pad1;
@@ -65,12 +67,14 @@ template <> struct Store<S_F32> {
     static constexpr bool scaled = false;
     using T = float;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_plain(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { __stcs(p, v); }
 };
 template <> struct Store<S_F16> {
     static constexpr bool scaled = true;
     using T = __half;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_plain(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<S_BF16> {
@@ -79,6 +83,7 @@ template <> struct Store<S_BF16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
         return __bfloat162float(__ldg(p));
     }
+    static __device__ __forceinline__ float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
         *p = __float2bfloat16_rn(v);
     }

@@ -16,6 +16,7 @@ namespace grlb {
 
 struct PullIdx {
     int32_t c, xm, xp, ym, yp, zm, zp;  // cell offsets of the 7 pull sources
+    int32_t yz;                         // y + ny z (row index)
     bool gl, gr;                        // +x / -x source is a Dirichlet ghost
 };
 
@@ -30,6 +31,7 @@ __device__ __forceinline__ PullIdx pull_index(const DomainDev& D, int x, int y, 
     const int zm = (z == 0) ? nz - 1 : z - 1;
     const int zp = (z == nz - 1) ? 0 : z + 1;
     P.c = row + x;
+    P.yz = y + ny * z;
     P.xm = row + xm;
     P.xp = row + xp;
     P.ym = (ym + ny * z) * nx + x;
@@ -41,8 +43,27 @@ __device__ __forceinline__ PullIdx pull_index(const DomainDev& D, int x, int y, 
     return P;
 }
 
-template <int S>
-__device__ __forceinline__ void load_cell(const DomainDev& D, const typename Store<S>::T* __restrict__ fin,
+// ---- population access patterns ----------------------------------------------------------
+// PULL: two buffers; read f_i(x - c_i) from the input, write f*_i(x) to the output (plane i).
+// AA (one buffer, in place, alternating):
+//   AA_ODD : read f*_i(x - c_i) from slot opp(i) of the neighbour x - c_i, collide, write
+//            f*_i(x) to slot i of the neighbour x + c_i (the streamed population arrives there);
+//   AA_EVEN: read slot i of x itself, collide, write f*_i(x) to slot opp(i) of x.
+// In an AA_ODD step the location a thread writes is one it read itself and no other thread
+// touches it, so the in-place update has no races.  Ghost cells (X_DIRICHLET_EQ): an AA_ODD
+// step reads the ghost value instead of the missing neighbour, drops the population that
+// leaves the domain, and writes the ghost's incoming population into the boundary cell's own
+// slot (nobody else reads it in that step) for the AA_EVEN step to find.
+enum Pattern { PULL = 0, AA_ODD = 1, AA_EVEN = 2 };
+
+template <int S, int PAT>
+__device__ __forceinline__ float ld_pop(const typename Store<S>::T* p) {
+    if (PAT == PULL) return Store<S>::ld(p);  // read-only path: the input is not written
+    return Store<S>::ld_plain(p);             // in place: plain (coherent) load
+}
+
+template <int S, int PAT>
+__device__ __forceinline__ void load_cell(const DomainDev& D, const typename Store<S>::T* fin,
                                           const PullIdx& P, float (&d)[NF][NQ]) {
     using St = Store<S>;
     const int64_t pl = D.plane;
@@ -52,25 +73,66 @@ __device__ __forceinline__ void load_cell(const DomainDev& D, const typename Sto
         // stored units: ghosts (physical deviations) take the storage scale
         const float gl = St::scaled ? D.ghostL[k] * D.enc[k] : D.ghostL[k];
         const float gr = St::scaled ? D.ghostR[k] * D.enc[k] : D.ghostR[k];
-        d[k][0] = St::ld(b + P.c);
-        d[k][1] = P.gl ? gl : St::ld(b + pl + P.xm);
-        d[k][2] = P.gr ? gr : St::ld(b + 2 * pl + P.xp);
-        d[k][3] = St::ld(b + 3 * pl + P.ym);
-        d[k][4] = St::ld(b + 4 * pl + P.yp);
-        d[k][5] = St::ld(b + 5 * pl + P.zm);
-        d[k][6] = St::ld(b + 6 * pl + P.zp);
+        if (PAT == AA_EVEN) {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) d[k][i] = ld_pop<S, PAT>(b + i * pl + P.c);
+        } else {
+            // PULL reads plane i of the neighbour; AA_ODD reads plane opp(i) of it
+            const int o1 = PAT == PULL ? 1 : 2, o2 = PAT == PULL ? 2 : 1;
+            const int o3 = PAT == PULL ? 3 : 4, o4 = PAT == PULL ? 4 : 3;
+            const int o5 = PAT == PULL ? 5 : 6, o6 = PAT == PULL ? 6 : 5;
+            d[k][0] = ld_pop<S, PAT>(b + P.c);
+            d[k][1] = P.gl ? gl : ld_pop<S, PAT>(b + o1 * pl + P.xm);
+            d[k][2] = P.gr ? gr : ld_pop<S, PAT>(b + o2 * pl + P.xp);
+            d[k][3] = ld_pop<S, PAT>(b + o3 * pl + P.ym);
+            d[k][4] = ld_pop<S, PAT>(b + o4 * pl + P.yp);
+            d[k][5] = ld_pop<S, PAT>(b + o5 * pl + P.zm);
+            d[k][6] = ld_pop<S, PAT>(b + o6 * pl + P.zp);
+        }
     }
 }
 
-template <int S>
-__device__ __forceinline__ void store_cell(const DomainDev& D, typename Store<S>::T* __restrict__ fout,
-                                           int32_t c, const float (&o)[NF][NQ]) {
+template <int S, int PAT>
+__device__ __forceinline__ void store_cell(const DomainDev& D, typename Store<S>::T* fout,
+                                           const PullIdx& P, const float (&o)[NF][NQ]) {
     using St = Store<S>;
     const int64_t pl = D.plane;
 #pragma unroll
-    for (int k = 0; k < NF; ++k)
+    for (int k = 0; k < NF; ++k) {
+        typename St::T* b = fout + (int64_t)(7 * k) * pl;
+        if (PAT == PULL) {
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) St::st(fout + (int64_t)(7 * k + i) * pl + c, o[k][i]);
+            for (int i = 0; i < NQ; ++i) St::st(b + i * pl + P.c, o[k][i]);
+        } else if (PAT == AA_EVEN) {
+            St::st(b + P.c, o[k][0]);
+            St::st(b + 2 * pl + P.c, o[k][1]);
+            St::st(b + 1 * pl + P.c, o[k][2]);
+            St::st(b + 4 * pl + P.c, o[k][3]);
+            St::st(b + 3 * pl + P.c, o[k][4]);
+            St::st(b + 6 * pl + P.c, o[k][5]);
+            St::st(b + 5 * pl + P.c, o[k][6]);
+        } else {  // AA_ODD: push to the neighbour the population streams to
+            St::st(b + P.c, o[k][0]);
+            const int64_t nyz = (int64_t)D.ny * D.nz;
+            typename St::T* out = static_cast<typename St::T*>(D.outflow);
+            if (P.gr) {
+                St::st(b + 2 * pl + P.c, St::scaled ? D.ghostR[k] * D.enc[k] : D.ghostR[k]);
+                St::st(out + (5 + k) * nyz + P.yz, o[k][1]);
+            } else {
+                St::st(b + 1 * pl + P.xp, o[k][1]);
+            }
+            if (P.gl) {
+                St::st(b + 1 * pl + P.c, St::scaled ? D.ghostL[k] * D.enc[k] : D.ghostL[k]);
+                St::st(out + k * nyz + P.yz, o[k][2]);
+            } else {
+                St::st(b + 2 * pl + P.xm, o[k][2]);
+            }
+            St::st(b + 3 * pl + P.yp, o[k][3]);
+            St::st(b + 4 * pl + P.ym, o[k][4]);
+            St::st(b + 5 * pl + P.zp, o[k][5]);
+            St::st(b + 6 * pl + P.zm, o[k][6]);
+        }
+    }
 }
 
 // Block-level FP64 reduction of the per-cell diagnostics into one NDIAG record.
@@ -124,14 +186,13 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
 // One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
 // parameter, so its constants are read as constant-bank operands of the arithmetic (a record
 // held in shared memory costs a load per use and ~15% of the sweep's time).
-template <int S, int COLL, bool DIAG, bool SRC>
+template <int S, int COLL, bool DIAG, bool SRC, int PAT>
 __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ DomainDev D,
-                                                    const void* __restrict__ fin_v,
-                                                    void* __restrict__ fout_v,
+                                                    const void* fin_v, void* fout_v,
                                                     double* __restrict__ partials) {
     using T = typename Store<S>::T;
-    const T* __restrict__ fin = static_cast<const T*>(fin_v);
-    T* __restrict__ fout = static_cast<T*>(fout_v);
+    const T* fin = static_cast<const T*>(fin_v);
+    T* fout = static_cast<T*>(fout_v);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -140,10 +201,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
     if (active) {
         const PullIdx P = pull_index(D, x, y, z);
         float d[NF][NQ], o[NF][NQ];
-        load_cell<S>(D, fin, P, d);
+        load_cell<S, PAT>(D, fin, P, d);
         collide<S, COLL, DIAG>(D, d, o, &cd);
         if (SRC) add_source<S>(D, P.c, o);
-        store_cell<S>(D, fout, P.c, o);
+        store_cell<S, PAT>(D, fout, P, o);
     }
     if (DIAG) {
         const int64_t blk = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
@@ -186,9 +247,9 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __res
             T* __restrict__ fout = static_cast<T*>(D.buf[c ^ 1]);
             const PullIdx P = pull_index(D, x, y, z);
             float d[NF][NQ], o[NF][NQ];
-            load_cell<S>(D, fin, P, d);
+            load_cell<S, PULL>(D, fin, P, d);
             collide<S, COLL, false>(D, d, o, nullptr);
-            store_cell<S>(D, fout, P.c, o);
+            store_cell<S, PULL>(D, fout, P, o);
         }
     }
 }
@@ -245,7 +306,7 @@ template <int S>
 __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __restrict__ fout_v,
                                                    const double* __restrict__ rho, const double* __restrict__ u,
                                                    const double* __restrict__ p, double s, double gm1,
-                                                   double rho_ref, double p_ref) {
+                                                   double rho_ref, double p_ref, int swap) {
     using T = typename Store<S>::T;
     T* fout = static_cast<T*>(fout_v);
     const int64_t N = D.plane;
@@ -279,25 +340,48 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
             const float v[NQ] = {0.25f * dQ[k], q1 + 0.5f * Pd[k][0], q1 - 0.5f * Pd[k][0],
                                  q1 + 0.5f * Pd[k][1], q1 - 0.5f * Pd[k][1],
                                  q1 + 0.5f * Pd[k][2], q1 - 0.5f * Pd[k][2]};
+            // swap: the one-buffer (AA) layout keeps population i in slot opp(i) before an
+            // odd step
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) Store<S>::st(fout + (int64_t)(7 * k + i) * N + c, v[i] * sc);
+            for (int i = 0; i < NQ; ++i) {
+                const int slot = swap ? (i == 0 ? 0 : (i & 1 ? i + 1 : i - 1)) : i;
+                Store<S>::st(fout + (int64_t)(7 * k + slot) * N + c, v[i] * sc);
+            }
         }
     }
 }
 
 // ---- readback: conserved fields in physical units (FP64) ---------------------------------
 template <int S>
+// gather = 1: one-buffer state after an odd step, where f*_i(x) sits in slot i of x + c_i
+// (or in the outflow record when x + c_i is outside an X_DIRICHLET_EQ domain).
 __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin_v,
-                                 double* __restrict__ out, double s, double rho_ref, double E_ref) {
+                                 double* __restrict__ out, double s, double rho_ref, double E_ref, int gather) {
     using T = typename Store<S>::T;
     const T* fin = static_cast<const T*>(fin_v);
+    const T* outflow = static_cast<const T*>(D.outflow);
     const int64_t N = D.plane;
+    const int64_t nyz = (int64_t)D.ny * D.nz;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % D.nx), r = (int)(c / D.nx);
+        const int y = r % D.ny, z = r / D.ny;
+        const PullIdx P = pull_index(D, x, y, z);
+        // where population i of this cell lives
+        int32_t at[NQ] = {P.c, P.c, P.c, P.c, P.c, P.c, P.c};
+        if (gather) {
+            at[1] = P.xp; at[2] = P.xm; at[3] = P.yp; at[4] = P.ym; at[5] = P.zp; at[6] = P.zm;
+        }
         for (int k = 0; k < NF; ++k) {
             double acc = 0.0;
             const double sc = (double)D.dec[k];
-            for (int i = 0; i < NQ; ++i) acc += (double)Store<S>::ld(fin + (int64_t)(7 * k + i) * N + c) * sc;
+            for (int i = 0; i < NQ; ++i) {
+                double v;
+                if (gather && i == 1 && P.gr) v = (double)Store<S>::ld(outflow + (5 + k) * nyz + P.yz);
+                else if (gather && i == 2 && P.gl) v = (double)Store<S>::ld(outflow + k * nyz + P.yz);
+                else v = (double)Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
+                acc += v * sc;
+            }
             double q = acc;
             if (k == 0) q += rho_ref;
             if (k == 4) q += E_ref;
@@ -309,25 +393,36 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
 }
 
 // ---- host-side launchers ------------------------------------------------------------------
-template <int S, int COLL>
-static cudaError_t launch_sweep_t(const DomainDev& D, const void* fin, void* fout, bool diag,
+template <int S, int COLL, int PAT>
+static cudaError_t launch_sweep_p(const DomainDev& D, const void* fin, void* fout, bool diag,
                                   double* partials, dim3 grid, dim3 block, cudaStream_t st) {
-    const bool src = D.src != nullptr;
-    if (diag && src)
-        sweep_kernel<S, COLL, true, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
-    else if (diag)
-        sweep_kernel<S, COLL, true, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
-    else if (src)
-        sweep_kernel<S, COLL, false, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    if (diag)
+        sweep_kernel<S, COLL, true, false, PAT><<<grid, block, 0, st>>>(D, fin, fout, partials);
     else
-        sweep_kernel<S, COLL, false, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
+        sweep_kernel<S, COLL, false, false, PAT><<<grid, block, 0, st>>>(D, fin, fout, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, const void* fin, void* fout,
+template <int S, int COLL>
+static cudaError_t launch_sweep_t(const DomainDev& D, int pattern, const void* fin, void* fout, bool diag,
+                                  double* partials, dim3 grid, dim3 block, cudaStream_t st) {
+    if (pattern == AA_ODD) return launch_sweep_p<S, COLL, AA_ODD>(D, fin, fout, diag, partials, grid, block, st);
+    if (pattern == AA_EVEN) return launch_sweep_p<S, COLL, AA_EVEN>(D, fin, fout, diag, partials, grid, block, st);
+    if (D.src != nullptr) {  // sources: two-buffer sweeps only
+        if (diag)
+            sweep_kernel<S, COLL, true, true, PULL><<<grid, block, 0, st>>>(D, fin, fout, partials);
+        else
+            sweep_kernel<S, COLL, false, true, PULL><<<grid, block, 0, st>>>(D, fin, fout, partials);
+        return cudaGetLastError();
+    }
+    return launch_sweep_p<S, COLL, PULL>(D, fin, fout, diag, partials, grid, block, st);
+}
+
+cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern, const void* fin, void* fout,
                          bool diag, double* partials, dim3 grid, dim3 block, cudaStream_t st) {
 #define GRLB_CASE(SS, CC) \
-    if (storage == SS && coll == CC) return launch_sweep_t<SS, CC>(D, fin, fout, diag, partials, grid, block, st);
+    if (storage == SS && coll == CC)                                                               \
+        return launch_sweep_t<SS, CC>(D, pattern, fin, fout, diag, partials, grid, block, st);
     GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F16, C_RLB)
     GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK)
 #undef GRLB_CASE
@@ -383,25 +478,25 @@ cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double
 }
 
 cudaError_t launch_init(const DomainDev& D, int storage, void* fout, const double* rho, const double* u,
-                        const double* p, double s, double gm1, double rho_ref, double p_ref,
+                        const double* p, double s, double gm1, double rho_ref, double p_ref, int swap,
                         cudaStream_t st) {
     const int threads = 256;
     int64_t blocks = (D.plane + threads - 1) / threads;
     if (blocks > 148 * 32) blocks = 148 * 32;
-    if (storage == S_F32) init_kernel<S_F32><<<(int)blocks, threads, 0, st>>>(D, fout, rho, u, p, s, gm1, rho_ref, p_ref);
-    else if (storage == S_F16) init_kernel<S_F16><<<(int)blocks, threads, 0, st>>>(D, fout, rho, u, p, s, gm1, rho_ref, p_ref);
-    else init_kernel<S_BF16><<<(int)blocks, threads, 0, st>>>(D, fout, rho, u, p, s, gm1, rho_ref, p_ref);
+    if (storage == S_F32) init_kernel<S_F32><<<(int)blocks, threads, 0, st>>>(D, fout, rho, u, p, s, gm1, rho_ref, p_ref, swap);
+    else if (storage == S_F16) init_kernel<S_F16><<<(int)blocks, threads, 0, st>>>(D, fout, rho, u, p, s, gm1, rho_ref, p_ref, swap);
+    else init_kernel<S_BF16><<<(int)blocks, threads, 0, st>>>(D, fout, rho, u, p, s, gm1, rho_ref, p_ref, swap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, double* out, double s,
-                             double rho_ref, double E_ref, cudaStream_t st) {
+                             double rho_ref, double E_ref, int gather, cudaStream_t st) {
     const int threads = 256;
     int64_t blocks = (D.plane + threads - 1) / threads;
     if (blocks > 148 * 32) blocks = 148 * 32;
-    if (storage == S_F32) conserved_kernel<S_F32><<<(int)blocks, threads, 0, st>>>(D, fin, out, s, rho_ref, E_ref);
-    else if (storage == S_F16) conserved_kernel<S_F16><<<(int)blocks, threads, 0, st>>>(D, fin, out, s, rho_ref, E_ref);
-    else conserved_kernel<S_BF16><<<(int)blocks, threads, 0, st>>>(D, fin, out, s, rho_ref, E_ref);
+    if (storage == S_F32) conserved_kernel<S_F32><<<(int)blocks, threads, 0, st>>>(D, fin, out, s, rho_ref, E_ref, gather);
+    else if (storage == S_F16) conserved_kernel<S_F16><<<(int)blocks, threads, 0, st>>>(D, fin, out, s, rho_ref, E_ref, gather);
+    else conserved_kernel<S_BF16><<<(int)blocks, threads, 0, st>>>(D, fin, out, s, rho_ref, E_ref, gather);
     return cudaGetLastError();
 }
 

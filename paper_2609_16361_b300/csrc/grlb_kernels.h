@@ -6,8 +6,10 @@
 #include "grlb_device.cuh"
 
 namespace grlb {
-// One sweep of one domain (record by value).  diag: one partial record per CTA in partials.
-cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, const void* fin, void* fout,
+// One sweep of one domain (record by value).  pattern: 0 two-buffer pull (fin -> fout),
+// 1 / 2 odd / even step of the one-buffer AA pattern (fin == fout).  diag: one partial record
+// per CTA in partials.
+cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern, const void* fin, void* fout,
                          bool diag, double* partials, dim3 grid, dim3 block, cudaStream_t st);
 // One sweep of every tile in tiles[0, ntiles) (domain records in device memory): one launch
 // of the persistent batched kernel.
@@ -15,9 +17,11 @@ cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, con
                                int parity, cudaStream_t st);
 cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double* out,
                                  cudaStream_t st);
+// swap = 1 writes the one-buffer layout (population i in slot opp(i)).
 cudaError_t launch_init(const DomainDev& D, int storage, void* fout, const double* rho,
                         const double* u, const double* p, double s, double gm1, double rho_ref,
-                        double p_ref, cudaStream_t st);
+                        double p_ref, int swap, cudaStream_t st);
+// gather = 1 for a one-buffer (AA) state after an odd number of steps.
 cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, double* out,
-                             double s, double rho_ref, double E_ref, cudaStream_t st);
+                             double s, double rho_ref, double E_ref, int gather, cudaStream_t st);
 }  // namespace grlb

@@ -40,6 +40,7 @@ class CaseParams:
     bc: int = BC_PERIODIC
     collision: int = COLL_RLB_SENSOR
     storage: int = STORE_F32
+    streaming: int = 0        # 0: two buffers (pull), 1: one buffer, AA pattern
     dx: float = 1.0
     dt: float = 1.0
     gamma: float = 1.4
