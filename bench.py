@@ -541,6 +541,64 @@ def run_tgv_series(args):
     return 0
 
 
+def run_capacity(args):
+    """Largest grids on one device: the Taylor-Green workload with one population buffer (AA
+    pattern) at 1024^3 in FP16 (75 GB of populations) and 768^3 in FP32 (63 GB) -- the paper runs
+    512^3 (19 GB) on a two-GPU node.  The initial fields are generated on the device (torch) and
+    freed after the init kernel; a few sweeps are timed and the diagnostics checked finite."""
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    runs = []
+    for n, storage in ((1024, "f16"), (768, "f32")):
+        st = {"f32": 0, "f16": 1, "bf16": 2}[storage]
+        small = inputs.tgv3d(n, storage=st, nxyz=(1, 1, 1))   # parameters only
+        prm = small.params.replace(nx=n, ny=n, nz=n, streaming=1)
+        meta = small.meta
+        need = capi.grlb_bytes_for(prm)
+        dom = capi.Domain(prm)
+        x = torch.arange(n, device=dev, dtype=torch.float64) * prm.dx
+        sx, cx = torch.sin(x), torch.cos(x)
+        V0, p0, T0 = meta["V0"], meta["p0"], meta["T0"]
+        ux = (V0 * sx[None, None, :] * cx[None, :, None] * cx[:, None, None]).reshape(-1)
+        uy = (-V0 * cx[None, None, :] * sx[None, :, None] * cx[:, None, None]).reshape(-1)
+        u = torch.stack([ux, uy, torch.zeros_like(ux)])
+        del ux, uy
+        c2 = torch.cos(2 * x)
+        p = (p0 + V0 * V0 / 16.0 * (c2[None, None, :] + c2[None, :, None])
+             * (c2[:, None, None] + 2.0)).reshape(-1)
+        rho = p / T0
+        capi.grlb_init_primitive_device(dom.h, rho.data_ptr(), u.data_ptr(), p.data_ptr())
+        torch.cuda.synchronize()
+        del rho, u, p
+        torch.cuda.empty_cache()
+        dom.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dom.step(10)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        dom.step_diag()
+        g = dom.diag()
+        N = n ** 3
+        runs.append({"grid": [n, n, n], "storage": storage, "streaming": "one buffer (AA)",
+                     "device_bytes": need, "ms_per_sweep": ms, "mlups": N / (ms / 1e3) / 1e6,
+                     "achieved_gbs": BYTES_PER_LUP[st] * N / (ms / 1e3) / 1e9,
+                     "finite": g["n_nan"] == 0, "mass_total": g["totals"][0]})
+        dom.close()
+        torch.cuda.empty_cache()
+    line = {"metric": "largest Taylor-Green grids on one B300 (MLUP/s of the 1024^3 FP16 run)",
+            "value": runs[0]["mlups"], "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f16 / f32 storage, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": "tgv 1024^3 f16 and 768^3 f32, one population buffer"},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,7 +608,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series"])
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
+                             "capacity"])
     ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=40)
@@ -567,6 +626,8 @@ def main():
         return run_precision(args)
     if args.workload == "tgv-series":
         return run_tgv_series(args)
+    if args.workload == "capacity":
+        return run_capacity(args)
     return run_ours(args)
 
 

@@ -112,28 +112,48 @@ __device__ __forceinline__ void add_source(const DomainDev& D, int32_t c, float 
 }
 
 // ---- Algorithm 1 on one cell --------------------------------------------------------------
+// moments (Alg. 1): dQ_k = sum_i d_ki, dJ_k = sum_i d_ki c_i of the stored values of one field,
+// in deviation units (the storage scale is applied to the 4 moments, not the 7 populations).
+template <int S>
+__device__ __forceinline__ void field_moments(const DomainDev& D, int k, float d0, float d1, float d2,
+                                              float d3, float d4, float d5, float d6, float& dQ,
+                                              float (&dJ)[3]) {
+    dQ = ((d0 + d1) + (d2 + d3)) + ((d4 + d5) + d6);
+    dJ[0] = d1 - d2;
+    dJ[1] = d3 - d4;
+    dJ[2] = d5 - d6;
+    if (Store<S>::scaled) {
+        dQ *= D.dec[k];
+        dJ[0] *= D.dec[k];
+        dJ[1] *= D.dec[k];
+        dJ[2] *= D.dec[k];
+    }
+}
+
+template <int S, int COLL, bool DIAG>
+__device__ __forceinline__ void collide_moments(const DomainDev& D, const float (&dQ)[NF],
+                                                const float (&dJ)[NF][3], const float (&d)[NF][NQ],
+                                                float (&o)[NF][NQ], CellDiag* cd);
+
 // In: d[k][i] = pulled stored values (deviations, x enc[k] when scaled).  Out: o[k][i] = the
-// values to store (post-collision deviations in the same units).  The storage scale is
-// applied to the 20 moments instead of the 35 populations.
+// values to store (post-collision deviations in the same units).
 template <int S, int COLL, bool DIAG>
 __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF][NQ],
                                         float (&o)[NF][NQ], CellDiag* cd) {
-    constexpr bool SC = Store<S>::scaled;
-    // moments (Alg. 1): dQ_k = sum_i d_ki, dJ_k = sum_i d_ki c_i
     float dQ[NF], dJ[NF][3];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        dQ[k] = ((d[k][0] + d[k][1]) + (d[k][2] + d[k][3])) + ((d[k][4] + d[k][5]) + d[k][6]);
-        dJ[k][0] = d[k][1] - d[k][2];
-        dJ[k][1] = d[k][3] - d[k][4];
-        dJ[k][2] = d[k][5] - d[k][6];
-        if (SC) {
-            dQ[k] *= D.dec[k];
-            dJ[k][0] *= D.dec[k];
-            dJ[k][1] *= D.dec[k];
-            dJ[k][2] *= D.dec[k];
-        }
-    }
+    for (int k = 0; k < NF; ++k)
+        field_moments<S>(D, k, d[k][0], d[k][1], d[k][2], d[k][3], d[k][4], d[k][5], d[k][6], dQ[k], dJ[k]);
+    collide_moments<S, COLL, DIAG>(D, dQ, dJ, d, o, cd);
+}
+
+// Everything after the moments: primitives and floors, reconstruction, sensor, closures,
+// equilibrium and collision.  The regularized collision needs only (dQ, dJ); BGK also reads d.
+template <int S, int COLL, bool DIAG>
+__device__ __forceinline__ void collide_moments(const DomainDev& D, const float (&dQ)[NF],
+                                                const float (&dJ)[NF][3], const float (&d)[NF][NQ],
+                                                float (&o)[NF][NQ], CellDiag* cd) {
+    constexpr bool SC = Store<S>::scaled;
     const float gm1 = D.gm1;
     // primitives with positivity floors (Alg. 1); Q_k themselves stay unfloored
     const float rho_raw = D.rho_ref + dQ[0];
