@@ -130,6 +130,19 @@ grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const 
  * Domains with a source cannot join a batch. */
 grlb_status grlb_set_source_device(grlb_domain* d, const float* S);
 
+/* Pipelined initialisation, for loops that upload the next initial state while the current
+ * one is being advanced.  grlb_stage_primitive enqueues the copy of host fields (the layout of
+ * grlb_init_primitive; page-locked host memory for the copy to overlap) into one of two device
+ * staging slots on a copy stream of the domain and returns at once; it fails with GRLB_ESTATE
+ * when both slots hold states not yet consumed.  grlb_init_from_stage enqueues on the domain's
+ * stream the initialisation from the oldest staged slot, ordered after its copy (GRLB_ESTATE if
+ * nothing is staged), and resets the step counter.  The host arrays must stay unchanged until
+ * that initialisation has run.  The slots (2 x 5 N doubles) are allocated on the first call and
+ * freed with the domain. */
+grlb_status grlb_stage_primitive(grlb_domain* d, const double* rho, const double* u,
+                                 const double* p);
+grlb_status grlb_init_from_stage(grlb_domain* d);
+
 /* Enqueue nsteps >= 0 plain sweeps (Algorithm 1 on every cell + exact streaming). */
 grlb_status grlb_step(grlb_domain* d, int nsteps);
 

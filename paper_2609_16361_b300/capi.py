@@ -85,6 +85,8 @@ def lib():
             "grlb_bytes_for": ([C.POINTER(grlb_params)], sz),
             "grlb_init_primitive": ([vp, dp, dp, dp], i32),
             "grlb_init_primitive_device": ([vp, vp, vp, vp], i32),
+            "grlb_stage_primitive": ([vp, dp, dp, dp], i32),
+            "grlb_init_from_stage": ([vp], i32),
             "grlb_step": ([vp, i32], i32),
             "grlb_set_source_device": ([vp, vp], i32),
             "grlb_step_diag": ([vp], i32),
@@ -114,7 +116,8 @@ def lib():
 def exported_symbols():
     return ["grlb_last_error", "grlb_version", "grlb_create", "grlb_destroy", "grlb_set_stream",
             "grlb_device_bytes", "grlb_bytes_for", "grlb_init_primitive",
-            "grlb_init_primitive_device", "grlb_set_source_device", "grlb_step",
+            "grlb_init_primitive_device", "grlb_stage_primitive", "grlb_init_from_stage",
+            "grlb_set_source_device", "grlb_step",
             "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
@@ -167,6 +170,19 @@ def grlb_init_primitive(h, rho, u, p):
     u = np.ascontiguousarray(u, np.float64)
     p = np.ascontiguousarray(p, np.float64)
     check(lib().grlb_init_primitive(h, _dp(rho), _dp(u), _dp(p)))
+
+
+def grlb_stage_primitive(h, rho, u, p):
+    """Enqueue the upload of host FP64 fields into a staging slot (arrays must be contiguous
+    float64 and stay alive and unchanged until grlb_init_from_stage has run)."""
+    for a in (rho, u, p):
+        if not (a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+            raise GrlbError(-1, "staged arrays must be contiguous float64")
+    check(lib().grlb_stage_primitive(h, _dp(rho), _dp(u), _dp(p)))
+
+
+def grlb_init_from_stage(h):
+    check(lib().grlb_init_from_stage(h))
 
 
 def grlb_init_primitive_device(h, rho_ptr, u_ptr, p_ptr):

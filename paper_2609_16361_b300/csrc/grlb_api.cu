@@ -68,6 +68,13 @@ struct grlb_domain {
     int64_t diag_step = -1;
     dim3 grid, block;
     size_t bytes = 0;
+    // pipelined initialisation (grlb_stage_primitive / grlb_init_from_stage)
+    double* stage[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    cudaEvent_t consumed[2] = {nullptr, nullptr};
+    bool consumed_recorded[2] = {false, false};
+    int stage_head = 0, stage_count = 0;
 };
 
 extern "C" {
@@ -245,6 +252,12 @@ void grlb_destroy(grlb_domain* d) {
     cudaFree(d->D.buf[0]);
     if (d->D.buf[1] != d->D.buf[0]) cudaFree(d->D.buf[1]);
     cudaFree(d->D.outflow);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(d->stage[i]);
+        if (d->staged[i]) cudaEventDestroy(d->staged[i]);
+        if (d->consumed[i]) cudaEventDestroy(d->consumed[i]);
+    }
+    if (d->copy_stream) cudaStreamDestroy(d->copy_stream);
     cudaFree(d->partials);
     cudaFree(d->diag_dev);
     cudaFreeHost(d->diag_host);
@@ -295,6 +308,49 @@ grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const 
 
 // Two buffers: read buf[cur], write the other.  One buffer (AA): the state after an even
 // number of steps sits in swapped slots, so step n+1 is an odd-type step when n is even.
+grlb_status grlb_stage_primitive(grlb_domain* d, const double* rho, const double* u, const double* p) {
+    if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_stage_primitive: NULL argument");
+    if (d->stage_count == 2) return fail(GRLB_ESTATE, "both staging slots hold unconsumed states");
+    const size_t N = (size_t)d->D.plane;
+    if (!d->copy_stream) {
+        GRLB_CU(cudaStreamCreateWithFlags(&d->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            GRLB_CU(cudaMalloc(&d->stage[i], 5 * N * sizeof(double)));
+            GRLB_CU(cudaEventCreateWithFlags(&d->staged[i], cudaEventDisableTiming));
+            GRLB_CU(cudaEventCreateWithFlags(&d->consumed[i], cudaEventDisableTiming));
+        }
+    }
+    const int slot = d->stage_head;
+    // the slot's previous contents must have been read by their initialisation
+    if (d->consumed_recorded[slot]) GRLB_CU(cudaStreamWaitEvent(d->copy_stream, d->consumed[slot], 0));
+    double* st = d->stage[slot];
+    GRLB_CU(cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
+    GRLB_CU(cudaMemcpyAsync(st + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
+    GRLB_CU(cudaMemcpyAsync(st + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
+    GRLB_CU(cudaEventRecord(d->staged[slot], d->copy_stream));
+    d->stage_head ^= 1;
+    d->stage_count += 1;
+    return GRLB_OK;
+}
+
+grlb_status grlb_init_from_stage(grlb_domain* d) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    if (d->stage_count == 0) return fail(GRLB_ESTATE, "no staged state to initialise from");
+    const int slot = (d->stage_head + 2 - d->stage_count) & 1;  // oldest filled slot
+    const size_t N = (size_t)d->D.plane;
+    GRLB_CU(cudaStreamWaitEvent(d->stream, d->staged[slot], 0));
+    d->D.cur = 0;
+    const double* st = d->stage[slot];
+    GRLB_CU(grlb::launch_init(d->D, d->P.storage, d->D.buf[0], st, st + N, st + 4 * N, d->s, d->gm1, d->rho_ref,
+                              d->p_ref, d->P.streaming, d->stream));
+    GRLB_CU(cudaEventRecord(d->consumed[slot], d->stream));
+    d->consumed_recorded[slot] = true;
+    d->stage_count -= 1;
+    d->steps = 0;
+    d->diag_step = -1;
+    return GRLB_OK;
+}
+
 static grlb_status sweep_once(grlb_domain* d, bool diag) {
     const int c = d->D.cur;
     cudaError_t e;

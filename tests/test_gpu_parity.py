@@ -275,3 +275,33 @@ def test_manufactured_solution_with_source_matches_oracle():
     with pytest.raises(capi.GrlbError):
         capi.grlb_set_source_device(d.h, S.data_ptr())
         capi.grlb_batch_create([d.h])
+
+
+def test_pipelined_staging_equals_direct_initialisation():
+    torch = pytest.importorskip("torch")
+    c = inputs.tgv3d(24)
+    other = inputs.tgv3d(24, mach=0.8)
+    ref = capi.Domain(c.params)
+    ref.init(c.rho, c.u, c.p)
+    ref.step(5)
+    d = capi.Domain(c.params)
+    with pytest.raises(capi.GrlbError):
+        capi.grlb_init_from_stage(d.h)          # nothing staged
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    A = [pin(c.rho), pin(c.u), pin(c.p)]
+    B = [pin(other.rho), pin(other.u), pin(other.p)]
+    capi.grlb_stage_primitive(d.h, *A)
+    capi.grlb_stage_primitive(d.h, *B)
+    with pytest.raises(capi.GrlbError):
+        capi.grlb_stage_primitive(d.h, *A)      # both slots pending
+    capi.grlb_init_from_stage(d.h)              # oldest: A
+    d.step(5)
+    assert np.array_equal(d.conserved(), ref.conserved())
+    capi.grlb_init_from_stage(d.h)              # then B
+    o = capi.Domain(c.params)                    # same domain parameters, B's fields
+    o.init(other.rho, other.u, other.p)
+    assert np.array_equal(d.conserved(), o.conserved())
+    capi.grlb_stage_primitive(d.h, *A)          # slots are reusable
+    capi.grlb_init_from_stage(d.h)
+    d.step(5)
+    assert np.array_equal(d.conserved(), ref.conserved())
