@@ -409,7 +409,7 @@ def run_serve(args):
     torch.cuda.set_device(0)
     trace = inputs.serving_trace(0, n_requests=args.requests, rate=20.0)
     table = autotune.tune([r.case for r in trace[:12]], steps=10)
-    srv = serve.Server(hbm_budget=150e9, chunk=50, tile_table=table)
+    srv = serve.Server(hbm_budget=150e9, chunk=200, tile_table=table)
     res = srv.run(trace, realtime=True)
     s_batched = serve.summarize(res)
     base = serve.serial_plain(trace, realtime=True)
@@ -424,7 +424,8 @@ def run_serve(args):
             "data": "synthetic",
             "config": {"workload": "Poisson 20/s; Sod / Becker tubes, Taylor-Green 64^3-192^3 "
                                    "(Re 100), FP32 or FP16, 500-5000 steps; seed 0",
-                       "requests": args.requests, "hbm_budget_bytes": 150e9, "chunk": 50},
+                       "requests": args.requests, "hbm_budget_bytes": 150e9, "chunk": 200,
+                       "lookahead_chunks": 12},
             "bitwise_equal_to_plain": same}
     print(json.dumps(line), flush=True)
     return 0

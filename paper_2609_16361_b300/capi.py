@@ -160,6 +160,11 @@ def grlb_destroy(h):
     lib().grlb_destroy(h)
 
 
+def grlb_set_stream(h, stream):
+    """Move the domain's later work to another cudaStream_t (int handle, or None)."""
+    check(lib().grlb_set_stream(h, stream))
+
+
 def grlb_bytes_for(prm) -> int:
     P = to_params(prm)
     return int(lib().grlb_bytes_for(C.byref(P)))

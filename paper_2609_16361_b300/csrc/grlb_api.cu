@@ -52,6 +52,25 @@ float storage_scale(int storage, double Mk) {
     return std::ldexp(1.0f, 8 - e);
 }
 
+// Device memory of domains and batches comes from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync): freeing does not synchronise the device, so a serving loop
+// can release a finished request while the others keep running.  The pool keeps released
+// memory for reuse (this process only).
+void retain_pool() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
+}
+
 }  // namespace
 
 struct grlb_domain {
@@ -63,17 +82,14 @@ struct grlb_domain {
     double* partials = nullptr;
     int64_t nblocks = 0;
     double* diag_dev = nullptr;
-    double* diag_host = nullptr;  // pinned, NDIAG doubles
     int64_t steps = 0;
     int64_t diag_step = -1;
     dim3 grid, block;
     size_t bytes = 0;
     // pipelined initialisation (grlb_stage_primitive / grlb_init_from_stage)
-    double* stage[2] = {nullptr, nullptr};
+    double* stage[2] = {nullptr, nullptr};   // allocated when filled, released when consumed
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t staged[2] = {nullptr, nullptr};
-    cudaEvent_t consumed[2] = {nullptr, nullptr};
-    bool consumed_recorded[2] = {false, false};
     int stage_head = 0, stage_count = 0;
 };
 
@@ -184,13 +200,33 @@ static void fill_domain_dev(grlb_domain* d) {
     D.pad1 = 0;
 }
 
+// CTA of 128 threads = bx cells along x times by rows.  bx in {128, 64, 32} is the width that
+// pads the row least (idle lanes cost throughput: nx = 130 on 128-wide tiles leaves half the
+// lanes of every row idle), the wider one on ties.
 static void choose_launch(grlb_domain* d) {
+    const int nx = d->P.nx;
     int bx = 128;
-    while (bx > 32 && bx / 2 >= d->P.nx) bx /= 2;
+    long best = -1;
+    for (int w = 128; w >= 32; w /= 2) {
+        const long padded = (long)((nx + w - 1) / w) * w;
+        if (best < 0 || padded < best) {
+            best = padded;
+            bx = w;
+        }
+    }
     int by = 128 / bx;
     while (by > 1 && by / 2 >= d->P.ny) by /= 2;
-    d->block = dim3(bx, by, 1);
-    d->grid = dim3((d->P.nx + bx - 1) / bx, (d->P.ny + by - 1) / by, d->P.nz);
+    const double padded = (double)((nx + bx - 1) / bx * bx) * ((d->P.ny + by - 1) / by * by);
+    if (padded > 1.05 * (double)nx * d->P.ny) {
+        // rows do not fill whole tiles: take cells in storage order instead (block.y == 0
+        // tells the launcher), one 128-cell CTA after another
+        const int64_t N = (int64_t)nx * d->P.ny * d->P.nz;
+        d->block = dim3(128, 0, 1);
+        d->grid = dim3((unsigned)((N + 127) / 128), 1, 1);
+    } else {
+        d->block = dim3(bx, by, 1);
+        d->grid = dim3((d->P.nx + bx - 1) / bx, (d->P.ny + by - 1) / by, d->P.nz);
+    }
     d->nblocks = (int64_t)d->grid.x * d->grid.y * d->grid.z;
 }
 
@@ -219,19 +255,20 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     choose_launch(d);
     const size_t N = (size_t)d->D.plane;
     const size_t pop_bytes = 35 * N * elem_bytes(p->storage);
+    retain_pool();
+    cudaStream_t s = d->stream;
     cudaError_t e = cudaSuccess;
     d->D.buf[0] = d->D.buf[1] = nullptr;
-    e = cudaMalloc(&d->D.buf[0], pop_bytes);
+    e = cudaMallocAsync(&d->D.buf[0], pop_bytes, s);
     if (e == cudaSuccess) {
         if (p->streaming) d->D.buf[1] = d->D.buf[0];  // one buffer, updated in place
-        else e = cudaMalloc(&d->D.buf[1], pop_bytes);
+        else e = cudaMallocAsync(&d->D.buf[1], pop_bytes, s);
     }
     if (e == cudaSuccess && p->streaming && p->bc == GRLB_BC_X_DIRICHLET_EQ)
-        e = cudaMalloc(&d->D.outflow, outflow_bytes(*p));
+        e = cudaMallocAsync(&d->D.outflow, outflow_bytes(*p), s);
     if (e == cudaSuccess)
-        e = cudaMalloc(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&d->diag_dev, NDIAG * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&d->diag_host, NDIAG * sizeof(double));
+        e = cudaMallocAsync(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d->diag_dev, NDIAG * sizeof(double), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         grlb_destroy(d);
@@ -240,27 +277,25 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     }
     d->bytes = (p->streaming ? 1 : 2) * pop_bytes + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
                NDIAG * 8 + outflow_bytes(*p);
-    for (int k = 0; k < NDIAG; ++k) d->diag_host[k] = 0.0;
     *out = d;
     return GRLB_OK;
 }
 
+// Releases in the order of the domain's stream (no device synchronisation).
 void grlb_destroy(grlb_domain* d) {
     if (!d) return;
-    if (d->stream) cudaStreamSynchronize(d->stream);
-    else cudaDeviceSynchronize();
-    cudaFree(d->D.buf[0]);
-    if (d->D.buf[1] != d->D.buf[0]) cudaFree(d->D.buf[1]);
-    cudaFree(d->D.outflow);
+    cudaStream_t s = d->stream;
+    if (d->D.buf[0]) cudaFreeAsync(d->D.buf[0], s);
+    if (d->D.buf[1] && d->D.buf[1] != d->D.buf[0]) cudaFreeAsync(d->D.buf[1], s);
+    if (d->D.outflow) cudaFreeAsync(d->D.outflow, s);
+    if (d->partials) cudaFreeAsync(d->partials, s);
+    if (d->diag_dev) cudaFreeAsync(d->diag_dev, s);
     for (int i = 0; i < 2; ++i) {
-        cudaFree(d->stage[i]);
+        if (d->stage[i]) cudaFreeAsync(d->stage[i], d->copy_stream);  // staged, never consumed
         if (d->staged[i]) cudaEventDestroy(d->staged[i]);
-        if (d->consumed[i]) cudaEventDestroy(d->consumed[i]);
     }
     if (d->copy_stream) cudaStreamDestroy(d->copy_stream);
-    cudaFree(d->partials);
-    cudaFree(d->diag_dev);
-    cudaFreeHost(d->diag_host);
+    cudaGetLastError();
     delete d;
 }
 
@@ -314,15 +349,11 @@ grlb_status grlb_stage_primitive(grlb_domain* d, const double* rho, const double
     const size_t N = (size_t)d->D.plane;
     if (!d->copy_stream) {
         GRLB_CU(cudaStreamCreateWithFlags(&d->copy_stream, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) {
-            GRLB_CU(cudaMalloc(&d->stage[i], 5 * N * sizeof(double)));
-            GRLB_CU(cudaEventCreateWithFlags(&d->staged[i], cudaEventDisableTiming));
-            GRLB_CU(cudaEventCreateWithFlags(&d->consumed[i], cudaEventDisableTiming));
-        }
+        for (int i = 0; i < 2; ++i) GRLB_CU(cudaEventCreateWithFlags(&d->staged[i], cudaEventDisableTiming));
     }
+    retain_pool();
     const int slot = d->stage_head;
-    // the slot's previous contents must have been read by their initialisation
-    if (d->consumed_recorded[slot]) GRLB_CU(cudaStreamWaitEvent(d->copy_stream, d->consumed[slot], 0));
+    GRLB_CU(cudaMallocAsync(&d->stage[slot], 5 * N * sizeof(double), d->copy_stream));
     double* st = d->stage[slot];
     GRLB_CU(cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
     GRLB_CU(cudaMemcpyAsync(st + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
@@ -343,8 +374,8 @@ grlb_status grlb_init_from_stage(grlb_domain* d) {
     const double* st = d->stage[slot];
     GRLB_CU(grlb::launch_init(d->D, d->P.storage, d->D.buf[0], st, st + N, st + 4 * N, d->s, d->gm1, d->rho_ref,
                               d->p_ref, d->P.streaming, d->stream));
-    GRLB_CU(cudaEventRecord(d->consumed[slot], d->stream));
-    d->consumed_recorded[slot] = true;
+    GRLB_CU(cudaFreeAsync(d->stage[slot], d->stream));  // released once the init has read it
+    d->stage[slot] = nullptr;
     d->stage_count -= 1;
     d->steps = 0;
     d->diag_step = -1;
@@ -390,7 +421,6 @@ grlb_status grlb_step_diag(grlb_domain* d) {
     grlb_status st = sweep_once(d, true);
     if (st != GRLB_OK) return st;
     GRLB_CU(grlb::launch_diag_finalize(d->partials, d->nblocks, d->diag_dev, d->stream));
-    GRLB_CU(cudaMemcpyAsync(d->diag_host, d->diag_dev, NDIAG * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
     d->diag_step = d->steps;
     return GRLB_OK;
 }
@@ -398,8 +428,9 @@ grlb_status grlb_step_diag(grlb_domain* d) {
 grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out) {
     if (!d || !out) return fail(GRLB_EINVAL, "grlb_diag_read: NULL argument");
     if (d->diag_step < 0) return fail(GRLB_ESTATE, "no diagnostic sweep since init");
+    double h[NDIAG];
+    GRLB_CU(cudaMemcpyAsync(h, d->diag_dev, NDIAG * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
     GRLB_CU(cudaStreamSynchronize(d->stream));
-    const double* h = d->diag_host;
     const double N = (double)d->D.plane;
     const double Qref[5] = {d->rho_ref, 0.0, 0.0, 0.0, d->E_ref};
     for (int k = 0; k < 5; ++k) out->totals[k] = N * Qref[k] + h[k];
@@ -523,7 +554,7 @@ struct grlb_batch {
     grlb_batch_config cfg{};
     cudaStream_t stream = nullptr;
     DomainDev* d_doms = nullptr;
-    DomainDev* h_doms = nullptr;  // pinned staging
+    std::vector<DomainDev> h_doms;  // records copied before each step (pageable: staged by the copy)
     // tiles grouped by (storage, collision): group g occupies [off[g], off[g+1])
     int4* d_tiles = nullptr;
     int ntiles = 0;
@@ -561,17 +592,30 @@ grlb_status rebuild_tiles(grlb_batch* b) {
         all.insert(all.end(), groups[g].begin(), groups[g].end());
     }
     b->group_off[6] = (int)all.size();
-    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
     b->d_tiles = nullptr;
     b->ntiles = (int)all.size();
     if (b->ntiles > 0) {
-        GRLB_CU(cudaMalloc(&b->d_tiles, all.size() * sizeof(int4)));
-        GRLB_CU(cudaMemcpy(b->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        GRLB_CU(cudaMallocAsync(&b->d_tiles, all.size() * sizeof(int4), b->stream));
+        GRLB_CU(cudaMemcpyAsync(b->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                b->stream));
     }
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     b->dirty = false;
     return GRLB_OK;
+}
+
+cudaError_t order_after_domains(grlb_batch* b) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (size_t i = 0; e == cudaSuccess && i < b->doms.size(); ++i) {
+        if (b->doms[i]->stream == b->stream) continue;
+        e = cudaEventRecord(ev, b->doms[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev, 0);
+    }
+    if (ev) cudaEventDestroy(ev);
+    return e;
 }
 
 cudaError_t enqueue_batch_step(grlb_batch* b, int parity) {
@@ -615,8 +659,11 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
         b->solo.push_back(thr > 0 && domains[i]->D.plane >= thr ? 1 : 0);
     }
     b->stream = domains[0]->stream;
-    cudaError_t e = cudaMalloc(&b->d_doms, n * sizeof(DomainDev));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_doms, n * sizeof(DomainDev));
+    retain_pool();
+    b->h_doms.resize(n);
+    cudaError_t e = cudaMallocAsync(&b->d_doms, n * sizeof(DomainDev), b->stream);
+    // the batch stream must not run ahead of work already queued on the domains' streams
+    if (e == cudaSuccess) e = order_after_domains(b);
     if (e != cudaSuccess) {
         grlb_batch_destroy(b);
         return cuda_fail(e, "grlb_batch_create");
@@ -630,20 +677,33 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
     return GRLB_OK;
 }
 
+// Releases in the order of the batch stream; each domain's stream is made to wait for the
+// batch's queued work, so a later grlb_destroy of a domain cannot overtake it.
 void grlb_batch_destroy(grlb_batch* b) {
     if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    else cudaDeviceSynchronize();
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(ev, b->stream);
+        for (grlb_domain* d : b->doms)
+            if (d->stream != b->stream) cudaStreamWaitEvent(d->stream, ev, 0);
+        cudaEventDestroy(ev);
+    }
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    cudaFree(b->d_doms);
-    cudaFreeHost(b->h_doms);
-    cudaFree(b->d_tiles);
+    if (b->d_doms) cudaFreeAsync(b->d_doms, b->stream);
+    if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
+    cudaGetLastError();
     delete b;
 }
 
 grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream) {
     if (!b) return fail(GRLB_EINVAL, "batch is NULL");
+    cudaEvent_t ev = nullptr;
+    GRLB_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, b->stream);  // the batch's own allocations and copies come first
     b->stream = static_cast<cudaStream_t>(stream);
+    cudaStreamWaitEvent(b->stream, ev, 0);
+    cudaEventDestroy(ev);
+    GRLB_CU(order_after_domains(b));
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     return GRLB_OK;
@@ -681,14 +741,13 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
         if (st != GRLB_OK) return st;
     }
     if (b->ntiles == 0) return GRLB_OK;
-    // The staging records are rewritten below: wait for the previous call's copy to finish.
-    GRLB_CU(cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < b->doms.size(); ++i) {
         b->h_doms[i] = b->doms[i]->D;
         b->h_doms[i].tile_x = tile_width(b, i);
     }
-    GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms, b->doms.size() * sizeof(DomainDev), cudaMemcpyHostToDevice,
-                            b->stream));
+    // from pageable memory: the host copy is staged before the call returns, no stream wait
+    GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms.data(), b->doms.size() * sizeof(DomainDev),
+                            cudaMemcpyHostToDevice, b->stream));
     int done = 0;
     if (b->cfg.use_graph && b->stream != nullptr && nsteps >= 2) {
         if (!b->graph) {

@@ -186,17 +186,32 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
 // One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
 // parameter, so its constants are read as constant-bank operands of the arithmetic (a record
 // held in shared memory costs a load per use and ~15% of the sweep's time).
-template <int S, int COLL, bool DIAG, bool SRC, int PAT>
+// LIN: cells are taken in storage order, thread t of CTA b updating cell 128 b + t, so no lane
+// idles whatever nx is (x, y, z from one division each); otherwise a CTA is a tile of
+// blockDim.x x blockDim.y cells of one z plane.
+template <int S, int COLL, bool DIAG, bool SRC, int PAT, bool LIN>
 __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ DomainDev D,
                                                     const void* fin_v, void* fout_v,
                                                     double* __restrict__ partials) {
     using T = typename Store<S>::T;
     const T* fin = static_cast<const T*>(fin_v);
     T* fout = static_cast<T*>(fout_v);
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    const bool active = (x < D.nx) && (y < D.ny);
+    int x, y, z;
+    bool active;
+    if (LIN) {
+        const int64_t t = (int64_t)blockIdx.x * 128 + threadIdx.x;
+        active = t < D.plane;
+        const uint32_t c = active ? (uint32_t)t : 0u;
+        const uint32_t r = c / (uint32_t)D.nx;
+        x = (int)(c - r * (uint32_t)D.nx);
+        z = (int)(r / (uint32_t)D.ny);
+        y = (int)(r - (uint32_t)z * (uint32_t)D.ny);
+    } else {
+        x = blockIdx.x * blockDim.x + threadIdx.x;
+        y = blockIdx.y * blockDim.y + threadIdx.y;
+        z = blockIdx.z;
+        active = (x < D.nx) && (y < D.ny);
+    }
     CellDiag cd;
     if (active) {
         const PullIdx P = pull_index(D, x, y, z);
@@ -393,29 +408,31 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
 }
 
 // ---- host-side launchers ------------------------------------------------------------------
-template <int S, int COLL, int PAT>
+// grid.y == 0 is not a valid launch, so the linear mapping is signalled by block.y == 0
+template <int S, int COLL, int PAT, bool SRC>
 static cudaError_t launch_sweep_p(const DomainDev& D, const void* fin, void* fout, bool diag,
                                   double* partials, dim3 grid, dim3 block, cudaStream_t st) {
-    if (diag)
-        sweep_kernel<S, COLL, true, false, PAT><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    const bool lin = block.y == 0;
+    if (lin) block = dim3(128, 1, 1);
+    if (diag && lin)
+        sweep_kernel<S, COLL, true, SRC, PAT, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    else if (diag)
+        sweep_kernel<S, COLL, true, SRC, PAT, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    else if (lin)
+        sweep_kernel<S, COLL, false, SRC, PAT, true><<<grid, block, 0, st>>>(D, fin, fout, partials);
     else
-        sweep_kernel<S, COLL, false, false, PAT><<<grid, block, 0, st>>>(D, fin, fout, partials);
+        sweep_kernel<S, COLL, false, SRC, PAT, false><<<grid, block, 0, st>>>(D, fin, fout, partials);
     return cudaGetLastError();
 }
 
 template <int S, int COLL>
 static cudaError_t launch_sweep_t(const DomainDev& D, int pattern, const void* fin, void* fout, bool diag,
                                   double* partials, dim3 grid, dim3 block, cudaStream_t st) {
-    if (pattern == AA_ODD) return launch_sweep_p<S, COLL, AA_ODD>(D, fin, fout, diag, partials, grid, block, st);
-    if (pattern == AA_EVEN) return launch_sweep_p<S, COLL, AA_EVEN>(D, fin, fout, diag, partials, grid, block, st);
-    if (D.src != nullptr) {  // sources: two-buffer sweeps only
-        if (diag)
-            sweep_kernel<S, COLL, true, true, PULL><<<grid, block, 0, st>>>(D, fin, fout, partials);
-        else
-            sweep_kernel<S, COLL, false, true, PULL><<<grid, block, 0, st>>>(D, fin, fout, partials);
-        return cudaGetLastError();
-    }
-    return launch_sweep_p<S, COLL, PULL>(D, fin, fout, diag, partials, grid, block, st);
+    if (pattern == AA_ODD) return launch_sweep_p<S, COLL, AA_ODD, false>(D, fin, fout, diag, partials, grid, block, st);
+    if (pattern == AA_EVEN) return launch_sweep_p<S, COLL, AA_EVEN, false>(D, fin, fout, diag, partials, grid, block, st);
+    if (D.src != nullptr)  // sources: two-buffer sweeps only
+        return launch_sweep_p<S, COLL, PULL, true>(D, fin, fout, diag, partials, grid, block, st);
+    return launch_sweep_p<S, COLL, PULL, false>(D, fin, fout, diag, partials, grid, block, st);
 }
 
 cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern, const void* fin, void* fout,

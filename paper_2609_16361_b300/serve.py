@@ -56,7 +56,7 @@ def _finish(res: Result, dom: capi.Domain, t0: float, keep: bool):
 
 
 class Server:
-    def __init__(self, hbm_budget: float = 150e9, max_resident: int = 512, chunk: int = 50,
+    def __init__(self, hbm_budget: float = 150e9, max_resident: int = 512, chunk: int = 200,
                  use_graph: bool = True, tile_table: dict | None = None, stream=None,
                  keep_fields: bool = False, large_cells: int = 262144, srpt: bool = True):
         import torch
@@ -73,22 +73,66 @@ class Server:
         self.large_cells = large_cells  # same threshold as the batch's solo_min_cells
         self.srpt = srpt
 
-    def run(self, trace, realtime: bool = True):
+    def run(self, trace, realtime: bool = True, lookahead: int = 12):
         """Serve `trace` (list of inputs.Request sorted by arrival).  Returns Results in
-        request order.  realtime=False admits every request at t = 0 (closed-loop)."""
+        request order.  realtime=False admits every request at t = 0 (closed-loop).
+
+        The host never waits for the chunk it just enqueued: up to `lookahead` chunks are in
+        flight; new requests are created and their fields uploaded (copy stream) behind them;
+        finished requests are read back by a worker thread on a readback stream that waits only
+        for the event of the chunk they finished in."""
+        import queue
+        import threading
+
+        import torch
         st = self.stream.cuda_stream
+        rstream = torch.cuda.Stream()
         pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
         waiting = collections.deque()
-        resident = []  # [req, dom, remaining, bytes, Result]
+        resident = []   # [req, dom, remaining, bytes, Result]
         results = {}
-        used = 0.0
+        lock = threading.Lock()
+        state = {"used": 0.0, "draining": 0, "error": None}
+        inflight = collections.deque()
         batch = None
         mask = None
         dirty = True
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
+        host = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        todo = queue.Queue()
+
+        def reader():
+            while True:
+                item = todo.get()
+                if item is None:
+                    return
+                entries, ev = item
+                try:
+                    rstream.wait_event(ev)
+                    for r, dom, _, need, res in entries:
+                        capi.grlb_set_stream(dom.h, rstream.cuda_stream)
+                        _finish(res, dom, t0, self.keep_fields)
+                        dom.close()
+                        with lock:
+                            results[r.rid] = res
+                            state["used"] -= need
+                            state["draining"] -= 1
+                except Exception as e:  # surfaced by the main loop
+                    with lock:
+                        state["error"] = e
+                        state["draining"] -= len(entries)
+
+        worker = threading.Thread(target=reader, daemon=True)
+        worker.start()
         try:
-            while pending or waiting or resident:
+            while True:
+                with lock:
+                    if state["error"] is not None:
+                        raise state["error"]
+                    used, draining = state["used"], state["draining"]
+                if not (pending or waiting or resident or draining):
+                    break
                 t = now()
                 while pending and (not realtime or pending[0].arrival <= t):
                     waiting.append(pending.popleft())
@@ -98,22 +142,29 @@ class Server:
                     need = capi.grlb_bytes_for(r.case.params)
                     if need == 0:
                         raise capi.GrlbError(-1, f"request {r.rid}: invalid parameters")
+                    with lock:
+                        used = state["used"]
+                        draining = state["draining"]
                     if used + need > self.budget:
-                        if not resident:
+                        if not resident and not draining:
                             raise capi.GrlbError(-2, f"request {r.rid} needs {need} B > budget")
                         break
                     waiting.popleft()
                     dom = capi.Domain(r.case.params, stream=st)
-                    dom.init(r.case.rho, r.case.u, r.case.p)
+                    capi.grlb_stage_primitive(dom.h, host(r.case.rho), host(r.case.u), host(r.case.p))
+                    capi.grlb_init_from_stage(dom.h)
                     res = Result(r.rid, r.kind, r.steps, r.case.params.ncells,
                                  r.arrival if realtime else 0.0, admitted=now())
                     resident.append([r, dom, r.steps, need, res])
-                    used += need
+                    with lock:
+                        state["used"] += need
+                        self.peak_bytes = max(self.peak_bytes, state["used"])
                     dirty = True
-                self.peak_bytes = max(self.peak_bytes, used)
                 self.peak_resident = max(self.peak_resident, len(resident))
                 if not resident:
-                    if pending:
+                    if waiting or draining:
+                        time.sleep(0.0005)   # memory comes back as the reader finishes
+                    elif pending:
                         time.sleep(max(0.0, pending[0].arrival - now()))
                     continue
                 if dirty:
@@ -141,19 +192,24 @@ class Server:
                 k = min(self.chunk, min(resident[i][2] for i in pick))
                 capi.grlb_batch_step(batch, k)
                 self.launch_steps += k
-                self.stream.synchronize()
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+                inflight.append(ev)
                 for i in pick:
                     resident[i][2] -= k
                 done = [x for x in resident if x[2] == 0]
                 if done:
-                    for r, dom, _, need, res in done:
-                        _finish(res, dom, t0, self.keep_fields)
-                        results[r.rid] = res
-                        dom.close()
-                        used -= need
+                    with lock:
+                        state["draining"] += len(done)
+                    todo.put((done, ev))
                     resident = [x for x in resident if x[2] > 0]
                     dirty = True
+                while len(inflight) > lookahead:
+                    inflight.popleft().synchronize()
         finally:
+            todo.put(None)
+            worker.join()
+            torch.cuda.synchronize()
             if batch is not None:
                 capi.grlb_batch_destroy(batch)
             for x in resident:
