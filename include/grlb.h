@@ -191,9 +191,11 @@ grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream);
 /* Mark which domains advance (active[i] != 0); rebuilds the tile table.  active == NULL
  * activates all. */
 grlb_status grlb_batch_set_active(grlb_batch* b, const int* active);
-/* Per-domain tile width (cells along x of a 128-thread CTA: 32, 64 or 128; 0 = the batch's
- * block_x rule), e.g. from an autotuner; tile_x == NULL resets all to 0.  Rebuilds the tile
- * table.  Results do not depend on the tile shape. */
+/* Per-domain tile shape, e.g. from an autotuner: 32, 64 or 128 cells along x of a 128-thread
+ * CTA (times 4, 2, 1 rows); 1 = linear tiles of 128 consecutive cells in storage order; 0 = the
+ * default (block_x if the config sets it, else the least-padding width, or linear tiles when
+ * rows do not fill whole tiles).  tile_x == NULL resets all to 0.  Rebuilds the tile table.
+ * Results do not depend on the tile shape. */
 grlb_status grlb_batch_set_tile_x(grlb_batch* b, const int* tile_x);
 /* Enqueue nsteps sweeps of every active domain, one launch per step (per storage/collision
  * group), replayed from a captured CUDA graph when use_graph is set. */

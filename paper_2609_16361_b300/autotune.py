@@ -1,10 +1,12 @@
 """Tile-shape autotuner for the batched sweep.
 
 A CTA of the batched sweep has 128 threads, one cell each, laid out as tile_x cells along x
-times 128/tile_x rows.  Narrow domains waste lanes on wide tiles; wide tiles give the longest
-contiguous runs per plane.  The tuner groups domains into size classes by nx, times the
-batched sweep of each class for every candidate width (CUDA events on the batch's stream,
-after warm-up), and keeps the fastest width per class (highest cell updates per second).
+times 128/tile_x rows, or (tile_x = 1) as 128 consecutive cells in storage order.  Narrow or
+ragged rows waste lanes on x-tiles; linear tiles waste none but pay two integer divisions per
+cell; wide x-tiles give the longest contiguous runs per plane.  The tuner groups domains into
+size classes by nx, times the batched sweep of each class for every candidate (CUDA events on
+the batch's stream, after warm-up), and keeps the fastest per class (highest cell updates
+per second).
 Results do not depend on the tile shape, only the speed does.
 """
 from __future__ import annotations
@@ -14,7 +16,7 @@ import os
 
 from . import capi
 
-CANDIDATES = (32, 64, 128)
+CANDIDATES = (1, 32, 64, 128)
 
 
 def size_class(prm) -> str:

@@ -566,12 +566,29 @@ struct grlb_batch {
 namespace {
 int group_of(const grlb_params& p) { return p.storage * 2 + p.collision; }
 
+// Tile width of domain i: the override, else block_x if the config fixes it, else the width
+// in {128, 64, 32} that pads its rows least, or 1 (linear tiles) when rows do not fill tiles.
 int tile_width(const grlb_batch* b, size_t i) {
     if (b->tile_x[i] > 0) return b->tile_x[i];
     const grlb_domain* d = b->doms[i];
-    int tx = b->cfg.block_x > 0 ? b->cfg.block_x : 128;
-    while (tx > 32 && tx / 2 >= d->P.nx) tx /= 2;
-    return tx;
+    const int nx = d->P.nx, ny = d->P.ny;
+    if (b->cfg.block_x > 0) {
+        int tx = b->cfg.block_x;
+        while (tx > 32 && tx / 2 >= nx) tx /= 2;
+        return tx;
+    }
+    int tx = 128;
+    long best = -1;
+    for (int w = 128; w >= 32; w /= 2) {
+        const long padded = (long)((nx + w - 1) / w) * w;
+        if (best < 0 || padded < best) {
+            best = padded;
+            tx = w;
+        }
+    }
+    const int ty = 128 / tx;
+    const double padded = (double)((nx + tx - 1) / tx * tx) * ((ny + ty - 1) / ty * ty);
+    return padded > 1.05 * (double)nx * ny ? 1 : tx;
 }
 
 grlb_status rebuild_tiles(grlb_batch* b) {
@@ -580,8 +597,12 @@ grlb_status rebuild_tiles(grlb_batch* b) {
         if (!b->active[i] || b->solo[i]) continue;
         const grlb_domain* d = b->doms[i];
         const int tx = tile_width(b, i);
-        const int ty = 128 / tx;
         std::vector<int4>& g = groups[group_of(d->P)];
+        if (tx == 1) {
+            for (int64_t c = 0; c < d->D.plane; c += 128) g.push_back(make_int4((int)i, (int)c, 0, 0));
+            continue;
+        }
+        const int ty = 128 / tx;
         for (int z = 0; z < d->P.nz; ++z)
             for (int y = 0; y < d->P.ny; y += ty)
                 for (int x = 0; x < d->P.nx; x += tx) g.push_back(make_int4((int)i, x, y, z));
@@ -719,7 +740,8 @@ grlb_status grlb_batch_set_tile_x(grlb_batch* b, const int* tile_x) {
     if (!b) return fail(GRLB_EINVAL, "batch is NULL");
     for (size_t i = 0; i < b->doms.size(); ++i) {
         const int t = tile_x ? tile_x[i] : 0;
-        if (t != 0 && t != 32 && t != 64 && t != 128) return fail(GRLB_EINVAL, "tile_x must be 0, 32, 64 or 128");
+        if (t != 0 && t != 1 && t != 32 && t != 64 && t != 128)
+            return fail(GRLB_EINVAL, "tile_x must be 0, 1, 32, 64 or 128");
     }
     for (size_t i = 0; i < b->doms.size(); ++i) b->tile_x[i] = tile_x ? tile_x[i] : 0;
     return rebuild_tiles(b);

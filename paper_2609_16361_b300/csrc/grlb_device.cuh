@@ -39,7 +39,8 @@ struct DomainDev {
     int64_t plane;         // elements per population plane = nx*ny*nz
     int32_t nx, ny, nz, bc;
     int32_t cur;           // index of the buffer holding the current state (batched sweep)
-    int32_t tile_x;        // cells along x per CTA in the batched sweep (divides blockDim.x)
+    int32_t tile_x;        // cells along x per CTA in the batched sweep (divides blockDim.x);
+                           // 1: linear tiles of 128 consecutive cells
     float gm1;             // gamma - 1
     float mu_ref, kap_ref; // lattice-unit transport at T_ref
     float inv_T_ref, T_S;  // Sutherland law: mu = mu_ref (1+T_S) t^{3/2}/(t+T_S), t = T/T_ref

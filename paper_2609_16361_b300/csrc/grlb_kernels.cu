@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
 }
 
 // ---- batched sweep: persistent CTAs over a tile table ------------------------------------
-// tiles[t] = (domain, x0, y0, z).  A CTA of 128 threads takes tiles blockIdx.x, + gridDim.x,
+// tiles[t] = (domain, x0, y0, z), or (domain, first cell, 0, 0) for a domain whose tile_x is 1
+// (linear tiles: 128 consecutive cells in storage order, no idle lanes for any nx).
+// A CTA of 128 threads takes tiles blockIdx.x, + gridDim.x,
 // ... (grid-stride, so consecutive CTAs stream consecutive rows); the domain record (buffers,
 // constants, tile width tile_x) is copied to shared memory whenever the domain changes;
 // thread t handles cell (x0 + t % tile_x, y0 + t / tile_x, z).  Each domain reads
@@ -253,10 +255,23 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __res
             loaded = tl.x;
         }
         const DomainDev& D = sD;
-        const int x = tl.y + (int)threadIdx.x % D.tile_x;
-        const int y = tl.z + (int)threadIdx.x / D.tile_x;
-        const int z = tl.w;
-        if (x < D.nx && y < D.ny) {
+        int x, y, z;
+        bool active;
+        if (D.tile_x == 1) {  // linear tile: 128 consecutive cells from cell tl.y
+            const int64_t cidx = (int64_t)tl.y + threadIdx.x;
+            active = cidx < D.plane;
+            const uint32_t c = active ? (uint32_t)cidx : 0u;
+            const uint32_t r = c / (uint32_t)D.nx;
+            x = (int)(c - r * (uint32_t)D.nx);
+            z = (int)(r / (uint32_t)D.ny);
+            y = (int)(r - (uint32_t)z * (uint32_t)D.ny);
+        } else {
+            x = tl.y + (int)threadIdx.x % D.tile_x;
+            y = tl.z + (int)threadIdx.x / D.tile_x;
+            z = tl.w;
+            active = x < D.nx && y < D.ny;
+        }
+        if (active) {
             const int c = D.cur ^ parity;
             const T* __restrict__ fin = static_cast<const T*>(D.buf[c]);
             T* __restrict__ fout = static_cast<T*>(D.buf[c ^ 1]);

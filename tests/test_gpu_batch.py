@@ -115,3 +115,21 @@ def test_large_domains_run_the_single_domain_sweep_inside_a_batch():
         assert d.steps == 13
         assert np.array_equal(capi.grlb_save(d.h)[32:], batched_alone(c, 13))
     capi.grlb_batch_destroy(b)
+
+
+@pytest.mark.parametrize("tile", [1, 32, 64, 128])
+def test_every_tile_shape_gives_the_same_result(tile):
+    """Linear tiles (1) and x-tiles of every width: bitwise the same batched result."""
+    cases = mixed_cases()
+    ref = [batched_alone(c, 9) for c in cases]
+    doms = []
+    for c in cases:
+        d = capi.Domain(c.params)
+        d.init(c.rho, c.u, c.p)
+        doms.append(d)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
+    capi.grlb_batch_set_tile_x(b, [tile] * len(doms))
+    capi.grlb_batch_step(b, 9)
+    for c, d, r in zip(cases, doms, ref):
+        assert np.array_equal(capi.grlb_save(d.h)[32:], r), (c.params.name, tile)
+    capi.grlb_batch_destroy(b)
