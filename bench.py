@@ -81,6 +81,42 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def instructions_per_cell(storage):
+    """Warp instructions per cell of the plain sweep (ncu smsp__inst_executed.sum / cells),
+    recorded in the traffic file for the current kernel source; None when stale or absent."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    rec = json.load(open(TRAFFIC_FILE)).get(f"inst_{storage}")
+    if rec and rec.get("source_sha") == kernel_source_sha():
+        return float(rec["warp_inst_per_cell"])
+    return None
+
+
+def ffma_issue_rate(stream, iters=2048, reps=5):
+    """FFMA warp instructions per second of the device (grlb_ffma_probe, 8 CTAs of 256
+    threads per SM, median of `reps` event-timed launches after 3 warm-up launches): the
+    instruction-issue ceiling of a kernel whose arithmetic is FP32."""
+    import torch
+    from paper_2609_16361_b300 import capi
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ctas = 8 * sms
+    sink = torch.zeros(ctas * 256, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):
+        capi.grlb_ffma_probe(ctas, iters, sink.data_ptr(), stream.cuda_stream)
+    times = []
+    count = 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        count = capi.grlb_ffma_probe(ctas, iters, sink.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return count / statistics.median(times)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
@@ -295,6 +331,16 @@ def run_ours(args):
         if rec and rec.get("source_sha") == kernel_source_sha():
             traffic = rec.get("dram_bytes_per_launch")
 
+    issue = None
+    rate = ffma_issue_rate(stream)
+    ipc = instructions_per_cell(args.storage)
+    if ipc is not None:
+        ach = ipc * N / (sweep_med / 1e3)
+        issue = {"bound": "issue", "achieved": ach, "peak": rate, "unit": "warp-inst/s",
+                 "frac": ach / rate, "warp_inst_per_cell": ipc,
+                 "peak_source": "FFMA probe measured in this run (grlb_ffma_probe)",
+                 "inst_source": "ncu smsp__inst_executed.sum of the same kernel source"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, _ = cpu_oracle_sample(n, 1, min_seconds=10.0)
@@ -313,12 +359,15 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (4.7 GB populations), no flush"},
             "e2e": {"value": e2e_lups / 1e6, "unit": "MLUP/s",
                     "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 8 * 13},
-            "gpu_launches": args.steps * (SWEEPS_PER_STEP + 2),
+            # per step: init + 49 plain sweeps + diagnostic sweep + 2 finalize stages
+            "gpu_launches": args.steps * (SWEEPS_PER_STEP + 3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"sweep_kernel<{args.storage},RLB> (plain sweep)",
                          "bytes_per_launch": bpl * N, "launch_ms_median": sweep_med,
                          "peak_source": f"{peak_src} hbm_gbs"},
+            "issue_ceiling": issue,
+            "ffma_probe": {"warp_inst_per_s": rate, "fp32_tflops": 64.0 * rate / 1e12},
             "clocks": clocks,
             "cpu_baseline": cpu,
             "diag_at_end": {"n_nan": diag["n_nan"], "n_sensor": diag["n_sensor"],
@@ -402,12 +451,12 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """Poisson trace (seed 0, 20 requests/s): continuous-batching server against the same trace
-    served first-in first-out one domain at a time with plain launches."""
+    """Poisson trace (seed 0, --rate requests/s, default 20): continuous-batching server against
+    the same trace served first-in first-out one domain at a time with plain launches."""
     import torch
     from paper_2609_16361_b300 import autotune, inputs, serve
     torch.cuda.set_device(0)
-    trace = inputs.serving_trace(0, n_requests=args.requests, rate=20.0)
+    trace = inputs.serving_trace(0, n_requests=args.requests, rate=args.rate)
     table = autotune.tune([r.case for r in trace[:12]], steps=10)
     srv = serve.Server(hbm_budget=150e9, chunk=200, tile_table=table)
     res = srv.run(trace, realtime=True)
@@ -422,8 +471,8 @@ def run_serve(args):
             "batched": s_batched, "peak_resident": srv.peak_resident,
             "peak_hbm_bytes": srv.peak_bytes, "dtype": "f32/f16 storage, f32 arithmetic",
             "data": "synthetic",
-            "config": {"workload": "Poisson 20/s; Sod / Becker tubes, Taylor-Green 64^3-192^3 "
-                                   "(Re 100), FP32 or FP16, 500-5000 steps; seed 0",
+            "config": {"workload": f"Poisson {args.rate:g}/s; Sod / Becker tubes, Taylor-Green "
+                                   "64^3-192^3 (Re 100), FP32 or FP16, 500-5000 steps; seed 0",
                        "requests": args.requests, "hbm_budget_bytes": 150e9, "chunk": 200,
                        "lookahead_chunks": 12},
             "bitwise_equal_to_plain": same}
@@ -529,9 +578,17 @@ def run_tgv_series(args):
         ke = g["ke"] / (s * s) / N
         eps_s = g["eps_s"] * prm.dx ** 2 / prm.dt ** 3 / N
         eps_d = g["eps_d"] * prm.dx ** 2 / prm.dt ** 3 / N
-        series.append({"step": step, "t_c": step * prm.dt, "E_k": ke, "eps_s": eps_s,
-                       "eps_d": eps_d, "n_sensor": g["n_sensor"], "n_floor": g["n_floor"],
-                       "n_nan": g["n_nan"]})
+        rec = {"step": step, "t_c": step * prm.dt, "E_k": ke, "eps_s": eps_s,
+               "eps_d": eps_d, "n_sensor": g["n_sensor"], "n_floor": g["n_floor"],
+               "n_nan": g["n_nan"]}
+        if g["n_nan"] == 0 and math.isfinite(ke):
+            # the same channels with spectral derivatives (Sec. 3.4), and the spectrum
+            spec, sp = d.spectral()
+            rec["eps_s_spectral"] = sp["eps_s"] * prm.dx ** 2 / prm.dt ** 3 / N
+            rec["eps_d_spectral"] = sp["eps_d"] * prm.dx ** 2 / prm.dt ** 3 / N
+            if step % 200 == 0:
+                rec["spectrum"] = [float(v) / (s * s) for v in spec]
+        series.append(rec)
         if g["n_nan"] > 0 or not math.isfinite(ke):
             first_bad = step
             break
@@ -542,8 +599,73 @@ def run_tgv_series(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"tgv{args.n}_f32_rlb_sensor", "steps_requested": args.run_steps,
                        "omega": prm.omega_mom, "fmu": c.meta["fmu"]},
+            "spectral": "eps_*_spectral: spectral derivatives of u = m / rho on the state the "
+                        "step landed on; spectrum: shell sums of 1/2 |u^|^2 / N^2 in units of V0^2, "
+                        "every 200 steps",
             "steps_run": step, "first_nonfinite_step": first_bad, "wall_s": wall,
             "series": series}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_spectral(args):
+    """Spectral post-processing (grlb_spectral_diag) of the n^3 Taylor-Green state after 50
+    steps: time per call (CUDA events on the domain's stream, 3 warm-up calls, median of 5),
+    algorithmic bytes 596 per cell (prep 140 + 28, three forward and four inverse 3-D FFTs of
+    16 B per cell per axis pass, mode pass 24 + 32, dissipation pass 36), and the spectral
+    against the cell-local (reconstructed-gradient) dissipation."""
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n = args.n
+    c = inputs.tgv3d(n)
+    prm = c.params
+    N = prm.ncells
+    d = capi.Domain(prm, stream=stream.cuda_stream)
+    d.init(c.rho, c.u, c.p)
+    d.step(49)
+    d.step_diag()
+    g = d.diag()
+    for _ in range(3):
+        d.spectral()
+    times = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        spec, sp = d.spectral()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    # one 50-step Taylor-Green step for scale
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.step(49)
+    d.step_diag()
+    e1.record(stream)
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1)
+    d.close()
+    peak, src = measured_peaks()
+    bpc = 596
+    ach = bpc * N / (ms / 1e3) / 1e9
+    line = {"metric": "spectral diagnostics time per call", "value": ms, "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32 (FFT), f64 (sums)",
+            "data": "synthetic",
+            "config": {"workload": f"tgv{n}_f32 state after 50 steps", "grid": [n, n, n],
+                       "shells": len(spec)},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "traffic": None, "bytes_per_call": bpc * N,
+                         "peak_source": f"{src} hbm_gbs",
+                         "note": "whole call, including its two host synchronisations"},
+            "share_of_50_step_step": ms / step_ms,
+            "eps_s": {"spectral": sp["eps_s"], "cell_local": g["eps_s"]},
+            "eps_d": {"spectral": sp["eps_d"], "cell_local": g["eps_d"]},
+            # prep + 3 x 3 forward passes + mode pass + 4 x 3 inverse passes + dissipation pass
+            "gpu_launches_per_call": 1 + 9 + 1 + 12 + 1}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -616,10 +738,11 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
-                             "capacity"])
+                             "capacity", "spectral"])
     ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -633,6 +756,8 @@ def main():
         return run_precision(args)
     if args.workload == "tgv-series":
         return run_tgv_series(args)
+    if args.workload == "spectral":
+        return run_spectral(args)
     if args.workload == "capacity":
         return run_capacity(args)
     return run_ours(args)

@@ -235,6 +235,46 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
 grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* f_in, void* f_out,
                                    double* diag_out, void* stream);
 
+
+/* ---- spectral post-processing (Sec. 3.4) ------------------------------------------------
+ * The paper evaluates the Taylor-Green dissipation spectrally and shows the shell-averaged
+ * velocity spectrum.  grlb_spectral_diag computes both from the domain's current state (the
+ * state grlb_read_conserved returns), in lattice units, on the device with the library's own
+ * FFT kernels (FP32 complex, radix 2), and returns FP64 results:
+ *   u = m / rho_f with rho_f = max(rho, rho_min); p = max((gamma-1)(E - |m|^2/(2 rho_f)), p_min);
+ *   T = p / rho_f; mu(T) the closure of the collision (constant or Sutherland);
+ *   u^(m) = sum_x u(x) exp(-2 pi i m.x / n), integer wavevector m, m_a in [-n/2, n/2);
+ *   spectrum[b] = sum over m with b - 1/2 <= |m| < b + 1/2 of 1/2 |u^(m)|^2 / N^2, so that
+ *                 sum_b spectrum[b] = (1/N) sum_x 1/2 |u|^2 (Parseval);
+ *   derivatives d/dx_a <-> i k_a, k_a = 2 pi m_a / n (zero for the Nyquist index m_a = -n/2);
+ *   sums[0] = eps_s = sum_x mu |curl u|^2, sums[1] = eps_d = sum_x 4/3 mu (div u)^2 (the units
+ *   of grlb_diag's cell-local eps_s / eps_d), sums[2] = sum_x 1/2 |u|^2.
+ *  d         domain (periodic; every extent above 1 the same power of two, 2..4096: cubes and
+ *            squares with nz = 1).
+ *  nbins     entries of spectrum to fill; shells beyond grlb_spectrum_shells(p) - 1 read 0,
+ *            shells at or beyond nbins are left out of spectrum (not of sums).
+ *  spectrum  host array of nbins doubles (may be NULL when nbins == 0).
+ *  sums      host array of 3 doubles.
+ * Scratch: 36 bytes per cell plus small tables, taken from the stream-ordered pool on the
+ * domain's stream and returned before the call ends.  The call synchronises the domain's stream
+ * (twice).  Shell sums are accumulated in 64-bit fixed point (resolution 2^-60 of the total),
+ * so the result does not depend on the order of the additions and is reproducible run to run.
+ * Errors: GRLB_EINVAL for NULL pointers, negative nbins, a non-periodic domain or unsupported
+ * extents; GRLB_ENOMEM / GRLB_ECUDA from the allocation or a launch. */
+int32_t grlb_spectrum_shells(const grlb_params* p);  /* shells of the domain's spectrum, -1 if unsupported */
+grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double* spectrum, double* sums);
+
+/* ---- FP32 issue-rate probe ----------------------------------------------------------------
+ * Measurement helper with no counterpart in the paper: the 16-bit storage sweeps are bound by
+ * instruction issue, and this probe measures that ceiling.  Enqueues one launch of ctas CTAs of
+ * 256 threads; every thread runs iters x 128 FP32 fused multiply-adds in 8 independent chains.
+ * *warp_instructions receives the launch's FFMA warp-instruction count (ctas x 8 x iters x 128);
+ * that count divided by the launch's duration (events on `stream`) is the FFMA issue rate, and
+ * 64 times it the FP32 FLOP rate.  sink: device array of ctas x 256 floats (in practice never
+ * written: a thread stores to its own element only if its chain sum is exactly 0).
+ * Errors: GRLB_EINVAL for ctas or iters < 1 or NULL pointers; GRLB_ECUDA on launch failure. */
+grlb_status grlb_ffma_probe(int32_t ctas, int32_t iters, float* sink, void* stream, double* warp_instructions);
+
 #ifdef __cplusplus
 }
 #endif

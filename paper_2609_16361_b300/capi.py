@@ -104,6 +104,9 @@ def lib():
             "grlb_batch_step": ([vp, i32], i32),
             "grlb_batch_set_tile_x": ([vp, C.POINTER(C.c_int)], i32),
             "grlb_step_diag_noalloc": ([C.POINTER(grlb_params), vp, vp, vp, vp], i32),
+            "grlb_spectrum_shells": ([C.POINTER(grlb_params)], C.c_int32),
+            "grlb_spectral_diag": ([vp, C.c_int32, dp, dp], i32),
+            "grlb_ffma_probe": ([C.c_int32, C.c_int32, vp, vp, dp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -121,7 +124,8 @@ def exported_symbols():
             "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
-            "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc"]
+            "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
+            "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe"]
 
 
 def check(status):
@@ -289,6 +293,27 @@ def grlb_step_diag_noalloc(prm, f_in_ptr, f_out_ptr, diag_out_ptr, stream=None):
     check(lib().grlb_step_diag_noalloc(C.byref(P), f_in_ptr, f_out_ptr, diag_out_ptr, stream))
 
 
+def grlb_spectrum_shells(prm) -> int:
+    P = to_params(prm)
+    return int(lib().grlb_spectrum_shells(C.byref(P)))
+
+
+def grlb_spectral_diag(h, nbins):
+    """Shell spectrum (nbins,) and dict(eps_s, eps_d, ke_u) of the domain's current state
+    (lattice units; spectral derivatives)."""
+    spec = np.zeros(max(int(nbins), 1))
+    sums = np.zeros(3)
+    check(lib().grlb_spectral_diag(h, int(nbins), _dp(spec), _dp(sums)))
+    return spec[:int(nbins)], dict(eps_s=float(sums[0]), eps_d=float(sums[1]), ke_u=float(sums[2]))
+
+
+def grlb_ffma_probe(ctas, iters, sink_ptr, stream=None) -> float:
+    """Enqueue the FFMA issue-rate probe; returns its FFMA warp-instruction count."""
+    n = C.c_double(0.0)
+    check(lib().grlb_ffma_probe(int(ctas), int(iters), sink_ptr, stream, C.byref(n)))
+    return n.value
+
+
 # ---- convenience object --------------------------------------------------------------------
 class Domain:
     """One domain on the current CUDA device (owns its C handle)."""
@@ -326,6 +351,10 @@ class Domain:
 
     def primitive(self):
         return grlb_read_primitive(self.h, self.N)
+
+    def spectral(self, nbins=None):
+        nb = grlb_spectrum_shells(self.prm) if nbins is None else nbins
+        return grlb_spectral_diag(self.h, nb)
 
     @property
     def steps(self):

@@ -853,3 +853,165 @@ extern "C" grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* 
     GRLB_CU(grlb::launch_diag_finalize(scratch, tmp.nblocks, diag_out, s));
     return GRLB_OK;
 }
+
+// ---- spectral post-processing -------------------------------------------------------------
+namespace {
+
+int ilog2_exact(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return (1 << l) == n ? l : -1;
+}
+
+// Extent n shared by every axis longer than 1, and how many such axes; 0 if they differ.
+int spectral_extent(const grlb_params& p, int* dims) {
+    int n = 0;
+    *dims = 0;
+    for (int e : {p.nx, p.ny, p.nz}) {
+        if (e <= 1) continue;
+        if (n && e != n) return 0;
+        n = e;
+        ++*dims;
+    }
+    return n;
+}
+
+int64_t shell_of_host(int64_t M) {
+    int64_t b = (int64_t)std::floor(std::sqrt((double)M) + 0.5);
+    while (b * b + b < M) ++b;
+    while (b > 0 && b * b - b + 1 > M) --b;
+    return b;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int32_t grlb_spectrum_shells(const grlb_params* p) {
+    if (!p) return -1;
+    int dims = 0;
+    const int n = spectral_extent(*p, &dims);
+    if (dims == 0) return 1;
+    if (n == 0) return -1;
+    const int64_t h = n / 2;
+    return (int32_t)(shell_of_host(dims * h * h) + 1);
+}
+
+extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double* spectrum, double* sums) {
+    if (!d || !sums || nbins < 0 || (nbins > 0 && !spectrum))
+        return fail(GRLB_EINVAL, "grlb_spectral_diag: NULL or negative argument");
+    const grlb_params& P = d->P;
+    if (P.bc != GRLB_BC_PERIODIC) return fail(GRLB_EINVAL, "grlb_spectral_diag: periodic domains only");
+    int dims = 0;
+    const int n = spectral_extent(P, &dims);
+    const int lg = n > 1 ? ilog2_exact(n) : 0;
+    if (dims == 0 || n == 0 || lg < 1 || n > 4096)
+        return fail(GRLB_EINVAL, "grlb_spectral_diag: every extent above 1 must be the same power of two "
+                                 "between 2 and 4096");
+    const int shells = grlb_spectrum_shells(&P);
+    const int nb = std::min<int>(nbins, shells);
+    const int64_t N = d->D.plane;
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, 148 * 8);
+    cudaStream_t st = d->stream;
+
+    // scratch: 4 complex planes, mu plane, twiddles, per-CTA partials, shell bins
+    const size_t oU = 0, oMu = align256(oU + 4 * (size_t)N * sizeof(float2));
+    const size_t oTw = align256(oMu + (size_t)N * sizeof(float));
+    const size_t oPart = align256(oTw + (size_t)(n / 2) * sizeof(float2));
+    const size_t oBins = align256(oPart + 2 * (size_t)grid * sizeof(double));
+    const size_t bytes = align256(oBins + (size_t)std::max(nb, 1) * sizeof(unsigned long long));
+    char* base = nullptr;
+    GRLB_CU(cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, st));
+    float2* U = reinterpret_cast<float2*>(base + oU);
+    float* mu = reinterpret_cast<float*>(base + oMu);
+    float2* tw = reinterpret_cast<float2*>(base + oTw);
+    double* part = reinterpret_cast<double*>(base + oPart);
+    unsigned long long* bins = reinterpret_cast<unsigned long long*>(base + oBins);
+
+    std::vector<float2> htw(n / 2);
+    for (int j = 0; j < n / 2; ++j) {
+        const double a = -2.0 * M_PI * (double)j / (double)n;
+        htw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    std::vector<double> hpart(2 * (size_t)grid);
+    std::vector<unsigned long long> hbins(std::max(nb, 1));
+    const int gather = (P.streaming && (d->steps & 1)) ? 1 : 0;
+    double ke_sum = 0.0;
+    cudaError_t e = cudaMemcpyAsync(tw, htw.data(), htw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, std::max(nb, 1) * sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+        e = grlb::launch_spectral_prep(d->D, P.storage, d->D.buf[d->D.cur], gather, d->rho_ref, d->E_ref, d->gm1,
+                                       U, mu, part, grid, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hpart.data(), part, grid * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < grid; ++i) ke_sum += hpart[i];
+        // fixed point for the shell sums: total 1/2|u^|^2/N^2 = ke_sum / N stays below 2^60
+        int ex = 0;
+        const double mean = ke_sum / (double)N;
+        if (mean > 0) std::frexp(mean, &ex);
+        const int fx = std::max(-1000, std::min(1000, 60 - ex));
+        const double fx_scale = std::ldexp(1.0, fx);
+        const int64_t dimsz[3] = {P.nx, P.ny, P.nz};
+        auto axes = [&](float2* plane, bool inverse) -> cudaError_t {
+            for (int a = 0; a < 3; ++a) {
+                if (dimsz[a] <= 1) continue;
+                grlb::FftAxis A;
+                A.log2n = lg;
+                if (a == 0) {
+                    A.stride = 1; A.inner = 1; A.inner_stride = 0; A.outer_stride = P.nx;
+                    A.nlines = (int64_t)P.ny * P.nz;
+                } else if (a == 1) {
+                    A.stride = P.nx; A.inner = P.nx; A.inner_stride = 1; A.outer_stride = (int64_t)P.nx * P.ny;
+                    A.nlines = (int64_t)P.nx * P.nz;
+                } else {
+                    A.stride = (int64_t)P.nx * P.ny; A.inner = (int64_t)P.nx * P.ny; A.inner_stride = 1;
+                    A.outer_stride = 0; A.nlines = (int64_t)P.nx * P.ny;
+                }
+                A.L = grlb::fft_lines_per_cta(lg, A.nlines);
+                cudaError_t r = grlb::launch_fft_axis(plane, tw, A, inverse, st);
+                if (r != cudaSuccess) return r;
+            }
+            return cudaSuccess;
+        };
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = axes(U + c * N, false);
+        if (e == cudaSuccess)
+            e = grlb::launch_spectral_modes(U, U + 3 * N, P.nx, P.ny, P.nz, nb,
+                                            1.0 / ((double)N * (double)N), fx_scale, bins, grid, st);
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c) e = axes(U + c * N, true);
+        if (e == cudaSuccess) e = grlb::launch_spectral_eps(U, mu, N, part, grid, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hpart.data(), part, 2 * grid * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && nb > 0)
+            e = cudaMemcpyAsync(hbins.data(), bins, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        cudaError_t e2 = cudaFreeAsync(base, st);
+        if (e == cudaSuccess) e = e2;
+        base = nullptr;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            double es = 0.0, ed = 0.0;
+            for (int i = 0; i < grid; ++i) {
+                es += hpart[2 * i];
+                ed += hpart[2 * i + 1];
+            }
+            const double inv_N2 = 1.0 / ((double)N * (double)N);
+            sums[0] = es * inv_N2;
+            sums[1] = ed * inv_N2;
+            sums[2] = ke_sum;
+            for (int b = 0; b < nbins; ++b) spectrum[b] = b < nb ? (double)hbins[b] / fx_scale : 0.0;
+        }
+    }
+    if (base) cudaFreeAsync(base, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grlb_spectral_diag");
+    return GRLB_OK;
+}
+
+extern "C" grlb_status grlb_ffma_probe(int32_t ctas, int32_t iters, float* sink, void* stream,
+                                       double* warp_instructions) {
+    if (ctas < 1 || iters < 1 || !sink || !warp_instructions)
+        return fail(GRLB_EINVAL, "grlb_ffma_probe: ctas and iters must be >= 1, pointers non-NULL");
+    GRLB_CU(grlb::launch_ffma_probe(sink, ctas, iters, static_cast<cudaStream_t>(stream)));
+    *warp_instructions = (double)ctas * 8.0 * (double)iters * 128.0;
+    return GRLB_OK;
+}

@@ -75,3 +75,11 @@ def test_create_fails_cleanly_without_device():
     st = capi.lib().grlb_create(C.byref(capi.to_params(inputs.tgv3d(8).params)), None, C.byref(h))
     assert st in (-2, -3) and not h.value
     assert len(capi.lib().grlb_last_error()) > 0
+
+
+def test_spectrum_shell_count_without_device():
+    from oracle import spectral
+    for n in (2, 16, 64, 256):
+        assert capi.grlb_spectrum_shells(inputs.tgv3d(n).params) == spectral.shells(n, n, n)
+    assert capi.grlb_spectrum_shells(inputs.tgv2d(64).params) == spectral.shells(64, 64, 1)
+    assert capi.grlb_spectrum_shells(inputs.random_smooth(16, 8, 8).params) == -1
