@@ -236,6 +236,24 @@ grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* f_in, void*
                                    double* diag_out, void* stream);
 
 
+/* ---- initialisation mode ------------------------------------------------------------------
+ * ce_init = 0 (default): grlb_init_primitive, grlb_init_primitive_device and
+ * grlb_init_from_stage write the equilibrium f^eq(Q, Phi^adv) (no non-equilibrium part).
+ * ce_init = 1: they write the Chapman-Enskog state of the fields instead (Sec. 2.3: the
+ * non-equilibrium first moment of field k carries its gradient), the state a smooth flow has
+ * after a collision: w_i (Q_k + c_i . (Phi^adv_k + A_k) / cs^2) with
+ *   A_k = Phi^diff_k - (tau_k - 1) cs^2 grad Q_k,   tau_k = 1 / omega_k (nominal rates),
+ * Phi^diff = (0, -tau_visc, -tau_visc u + q) from tau_visc = mu (grad u + grad u^T -
+ * 2/3 div u I) and q = -kappa grad T at the local temperature, and gradients by central
+ * differences (phi(x + e_a) - phi(x - e_a)) / 2 in lattice units of Q, u and T (periodic
+ * wrap, or the ghost state beyond the ends of an X_DIRICHLET_EQ tube; zero along an axis of
+ * extent 1).  With omega near 2 the equilibrium start leaves a non-equilibrium part that
+ * changes sign every step for thousands of steps, and the cell-local diagnostics alternate
+ * with it; the Chapman-Enskog start does not.  The conserved fields are the same in both modes.
+ * The mode stays with the domain until changed.  Errors: GRLB_EINVAL for a NULL domain or a
+ * value other than 0 / 1. */
+grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init);
+
 /* ---- spectral post-processing (Sec. 3.4) ------------------------------------------------
  * The paper evaluates the Taylor-Green dissipation spectrally and shows the shell-averaged
  * velocity spectrum.  grlb_spectral_diag computes both from the domain's current state (the

@@ -132,7 +132,9 @@ class Oracle:
         self.last_cells = None
 
     # -- state --------------------------------------------------------------------------
-    def init_primitive(self, rho, u, p):
+    def init_primitive(self, rho, u, p, ce_init: bool = False):
+        """Populations of the physical primitive fields: the equilibrium f^eq(Q, Phi^adv), plus
+        with ce_init the Chapman-Enskog non-equilibrium part (chapman_enskog_moments)."""
         s = self.s
         rho = np.ascontiguousarray(rho, np.float64)
         ux = np.ascontiguousarray(u[0] * s)
@@ -141,7 +143,80 @@ class Oracle:
         pL = np.ascontiguousarray(np.asarray(p, np.float64) * s * s)
         lib().orc_init_equilibrium(C.byref(self.P), _dp(rho), _dp(ux), _dp(uy), _dp(uz),
                                    _dp(pL), _dp(self.f))
+        if ce_init:
+            A = self.chapman_enskog_moments(rho, u, p)
+            # w_i c_i . A_k / cs^2 with w_i / cs^2 = 1/2 on the six links
+            for k in range(5):
+                for a in range(3):
+                    self.f[7 * k + 1 + 2 * a] += 0.5 * A[k, a]
+                    self.f[7 * k + 2 + 2 * a] -= 0.5 * A[k, a]
         self.steps = 0
+
+    def chapman_enskog_moments(self, rho, u, p):
+        """Non-equilibrium first moments A_k (5, 3, N), lattice units, of the Chapman-Enskog
+        state the first sweep streams (Sec. 2.3: the non-equilibrium first moment of field k
+        carries its gradient).  Before the collision the streamed first moment is
+        J_k = Phi^adv_k + Phi^diff_k - tau_k cs^2 grad Q_k; after the collision (regularized
+        or BGK, nominal tau_k = 1/omega_k) the stored populations carry
+        A_k = Phi^diff_k - (tau_k - 1) cs^2 grad Q_k on top of f^eq(Q, Phi^adv).
+        Gradients: central differences (phi(x + e_a) - phi(x - e_a)) / 2 of Q_k, u and T,
+        periodic, or with the ghost states beyond the ends of an X_DIRICHLET_EQ tube; zero
+        along an axis of extent 1.  Phi^diff: 0 (rho), -tau_visc (momentum),
+        -tau_visc u + q (energy); tau_visc = mu (grad u + grad u^T - 2/3 div u I),
+        q = -kappa grad T, mu and kappa at the local T (constant or Sutherland)."""
+        P, s, prm = self.P, self.s, self.prm
+        nx, ny, nz = prm.nx, prm.ny, prm.nz
+        g = prm.gamma
+        rho = np.asarray(rho, np.float64)
+        uL = np.asarray(u, np.float64) * s
+        pL = np.asarray(p, np.float64) * s * s
+        T = pL / rho
+        Q = np.stack([rho, rho * uL[0], rho * uL[1], rho * uL[2],
+                      pL / (g - 1.0) + 0.5 * rho * (uL * uL).sum(0)])
+
+        def ghost(prim):
+            r, gx, gy, gz, gp = prim[0], prim[1] * s, prim[2] * s, prim[3] * s, prim[4] * s * s
+            return dict(Q=[r, r * gx, r * gy, r * gz, gp / (g - 1.0) + 0.5 * r * (gx * gx + gy * gy + gz * gz)],
+                        u=[gx, gy, gz], T=gp / r)
+
+        gl, gr = ghost(prm.left_prim), ghost(prm.right_prim)
+
+        def grad(phi, left, right):
+            a = phi.reshape(nz, ny, nx)
+            out = np.zeros((3,) + a.shape)
+            if nx > 1:
+                if prm.bc == 1:
+                    pad = np.concatenate([np.full((nz, ny, 1), left), a, np.full((nz, ny, 1), right)], axis=2)
+                    out[0] = 0.5 * (pad[:, :, 2:] - pad[:, :, :-2])
+                else:
+                    out[0] = 0.5 * (np.roll(a, -1, axis=2) - np.roll(a, 1, axis=2))
+            if ny > 1:
+                out[1] = 0.5 * (np.roll(a, -1, axis=1) - np.roll(a, 1, axis=1))
+            if nz > 1:
+                out[2] = 0.5 * (np.roll(a, -1, axis=0) - np.roll(a, 1, axis=0))
+            return out.reshape(3, -1)
+
+        gQ = np.stack([grad(Q[k], gl["Q"][k], gr["Q"][k]) for k in range(5)])   # [k, a]
+        gu = np.stack([grad(uL[j], gl["u"][j], gr["u"][j]) for j in range(3)])  # [j, a] = d_a u_j
+        gT = grad(T, gl["T"], gr["T"])
+        fac = np.ones_like(T)
+        if P.sutherland:
+            t = T / P.T_ref
+            fac = (1.0 + P.T_S) * t ** 1.5 / (t + P.T_S)
+        mu, kap = P.mu_ref * fac, P.kappa_ref * fac
+        th = gu[0, 0] + gu[1, 1] + gu[2, 2]
+        tv = np.empty((3, 3) + T.shape)
+        for j in range(3):
+            for a in range(3):
+                tv[j, a] = mu * (gu[j, a] + gu[a, j] - (2.0 / 3.0 * th if j == a else 0.0))
+        q = -kap * gT
+        diff = np.zeros((5, 3) + T.shape)
+        for j in range(3):
+            diff[1 + j] = -tv[j]
+        for a in range(3):
+            diff[4, a] = -(tv[a, 0] * uL[0] + tv[a, 1] * uL[1] + tv[a, 2] * uL[2]) + q[a]
+        tau = 1.0 / np.array([P.omega[0], P.omega[1], P.omega[2], P.omega[3], P.omega[4]])
+        return diff - ((tau - 1.0) * 0.25)[:, None, None] * gQ
 
     def source_lattice(self, S):
         """Physical source rates (5, N) -> lattice units per step: rho dt, m dt s, E dt s^2."""

@@ -107,6 +107,7 @@ def lib():
             "grlb_spectrum_shells": ([C.POINTER(grlb_params)], C.c_int32),
             "grlb_spectral_diag": ([vp, C.c_int32, dp, dp], i32),
             "grlb_ffma_probe": ([C.c_int32, C.c_int32, vp, vp, dp], i32),
+            "grlb_set_init_mode": ([vp, C.c_int32], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -125,7 +126,8 @@ def exported_symbols():
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
-            "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe"]
+            "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe",
+            "grlb_set_init_mode"]
 
 
 def check(status):
@@ -293,6 +295,10 @@ def grlb_step_diag_noalloc(prm, f_in_ptr, f_out_ptr, diag_out_ptr, stream=None):
     check(lib().grlb_step_diag_noalloc(C.byref(P), f_in_ptr, f_out_ptr, diag_out_ptr, stream))
 
 
+def grlb_set_init_mode(h, ce_init):
+    check(lib().grlb_set_init_mode(h, int(ce_init)))
+
+
 def grlb_spectrum_shells(prm) -> int:
     P = to_params(prm)
     return int(lib().grlb_spectrum_shells(C.byref(P)))
@@ -334,7 +340,11 @@ class Domain:
         except Exception:
             pass
 
-    def init(self, rho, u, p):
+    def init(self, rho, u, p, ce_init=None):
+        """Initialise from host FP64 primitive fields; ce_init = True / False sets the domain's
+        init mode first (None keeps it)."""
+        if ce_init is not None:
+            grlb_set_init_mode(self.h, 1 if ce_init else 0)
         grlb_init_primitive(self.h, rho, u, p)
 
     def step(self, n=1):

@@ -91,6 +91,7 @@ struct grlb_domain {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t staged[2] = {nullptr, nullptr};
     int stage_head = 0, stage_count = 0;
+    int ce_init = 0;  // grlb_set_init_mode
 };
 
 extern "C" {
@@ -308,6 +309,32 @@ grlb_status grlb_set_stream(grlb_domain* d, void* stream) {
 size_t grlb_device_bytes(const grlb_domain* d) { return d ? d->bytes : 0; }
 int64_t grlb_steps_done(const grlb_domain* d) { return d ? d->steps : -1; }
 
+
+// The initialisation kernel the domain's init mode asks for (equilibrium or Chapman-Enskog).
+static cudaError_t launch_domain_init(grlb_domain* d, const double* rho, const double* u, const double* p) {
+    if (!d->ce_init)
+        return grlb::launch_init(d->D, d->P.storage, d->D.buf[0], rho, u, p, d->s, d->gm1, d->rho_ref, d->p_ref,
+                                 d->P.streaming, d->stream);
+    const grlb_params& P = d->P;
+    grlb::CeInit C;
+    C.s = d->s;
+    C.gm1 = d->gm1;
+    C.mu = P.mu_ref * P.dt / (P.dx * P.dx);
+    C.kap = C.mu * (P.gamma / (P.gamma - 1.0)) / P.prandtl;
+    C.inv_T_ref = 1.0 / (P.T_ref * d->s * d->s);
+    C.T_S = P.T_S;
+    const double om[5] = {P.omega_rho, P.omega_mom, P.omega_mom, P.omega_mom, P.omega_E};
+    for (int k = 0; k < 5; ++k) {
+        C.tau[k] = 1.0 / om[k];
+        C.ghostL[k] = P.left_prim[k];
+        C.ghostR[k] = P.right_prim[k];
+    }
+    C.sutherland = P.sutherland;
+    C.bc = P.bc;
+    return grlb::launch_init_ce(d->D, P.storage, d->D.buf[0], rho, u, p, d->rho_ref, d->p_ref, P.streaming, C,
+                                d->stream);
+}
+
 grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double* u, const double* p) {
     if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive: NULL argument");
     const size_t N = (size_t)d->D.plane;
@@ -318,8 +345,7 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
     if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
     if (e == cudaSuccess) {
         d->D.cur = 0;
-        e = grlb::launch_init(d->D, d->P.storage, d->D.buf[0], stage, stage + N, stage + 4 * N, d->s,
-                              d->gm1, d->rho_ref, d->p_ref, d->P.streaming, d->stream);
+        e = launch_domain_init(d, stage, stage + N, stage + 4 * N);
     }
     cudaError_t e2 = cudaFreeAsync(stage, d->stream);
     if (e == cudaSuccess) e = e2;
@@ -333,8 +359,7 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
 grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const double* u, const double* p) {
     if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive_device: NULL argument");
     d->D.cur = 0;
-    cudaError_t e = grlb::launch_init(d->D, d->P.storage, d->D.buf[0], rho, u, p, d->s, d->gm1, d->rho_ref,
-                                      d->p_ref, d->P.streaming, d->stream);
+    cudaError_t e = launch_domain_init(d, rho, u, p);
     if (e != cudaSuccess) return cuda_fail(e, "grlb_init_primitive_device");
     d->steps = 0;
     d->diag_step = -1;
@@ -372,8 +397,7 @@ grlb_status grlb_init_from_stage(grlb_domain* d) {
     GRLB_CU(cudaStreamWaitEvent(d->stream, d->staged[slot], 0));
     d->D.cur = 0;
     const double* st = d->stage[slot];
-    GRLB_CU(grlb::launch_init(d->D, d->P.storage, d->D.buf[0], st, st + N, st + 4 * N, d->s, d->gm1, d->rho_ref,
-                              d->p_ref, d->P.streaming, d->stream));
+    GRLB_CU(launch_domain_init(d, st, st + N, st + 4 * N));
     GRLB_CU(cudaFreeAsync(d->stage[slot], d->stream));  // released once the init has read it
     d->stage[slot] = nullptr;
     d->stage_count -= 1;
@@ -1004,6 +1028,13 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     }
     if (base) cudaFreeAsync(base, st);
     if (e != cudaSuccess) return cuda_fail(e, "grlb_spectral_diag");
+    return GRLB_OK;
+}
+
+extern "C" grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    if (ce_init != 0 && ce_init != 1) return fail(GRLB_EINVAL, "grlb_set_init_mode: ce_init must be 0 or 1");
+    d->ce_init = ce_init;
     return GRLB_OK;
 }
 

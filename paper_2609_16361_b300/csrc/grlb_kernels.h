@@ -21,6 +21,17 @@ cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double
 cudaError_t launch_init(const DomainDev& D, int storage, void* fout, const double* rho,
                         const double* u, const double* p, double s, double gm1, double rho_ref,
                         double p_ref, int swap, cudaStream_t st);
+// Chapman-Enskog initialisation (grlb_init_ce.cu): FP64 parameters in lattice units, ghost
+// primitives (rho, ux, uy, uz, p) in physical units, nominal tau_k = 1 / omega_k.
+struct CeInit {
+    double s, gm1, mu, kap, inv_T_ref, T_S;
+    double tau[5];
+    double ghostL[5], ghostR[5];
+    int sutherland, bc;
+};
+cudaError_t launch_init_ce(const DomainDev& D, int storage, void* fout, const double* rho, const double* u,
+                           const double* p, double rho_ref, double p_ref, int swap, const CeInit& C,
+                           cudaStream_t st);
 // gather = 1 for a one-buffer (AA) state after an odd number of steps.
 cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, double* out,
                              double s, double rho_ref, double E_ref, int gather, cudaStream_t st);
