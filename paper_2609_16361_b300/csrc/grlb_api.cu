@@ -909,6 +909,8 @@ int64_t shell_of_host(int64_t M) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+int lgs_of(int e) { return e > 1 ? ilog2_exact(e) : 0; }
+
 }  // namespace
 
 extern "C" int32_t grlb_spectrum_shells(const grlb_params* p) {
@@ -941,7 +943,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     // scratch: 4 complex planes, mu plane, twiddles, per-CTA partials, shell bins
     const size_t oU = 0, oMu = align256(oU + 4 * (size_t)N * sizeof(float2));
     const size_t oTw = align256(oMu + (size_t)N * sizeof(float));
-    const size_t oPart = align256(oTw + (size_t)(n / 2) * sizeof(float2));
+    const size_t oPart = align256(oTw + (size_t)n * sizeof(float2));
     const size_t oBins = align256(oPart + 2 * (size_t)grid * sizeof(double));
     const size_t bytes = align256(oBins + (size_t)std::max(nb, 1) * sizeof(unsigned long long));
     char* base = nullptr;
@@ -952,8 +954,8 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     double* part = reinterpret_cast<double*>(base + oPart);
     unsigned long long* bins = reinterpret_cast<unsigned long long*>(base + oBins);
 
-    std::vector<float2> htw(n / 2);
-    for (int j = 0; j < n / 2; ++j) {
+    std::vector<float2> htw(n);
+    for (int j = 0; j < n; ++j) {
         const double a = -2.0 * M_PI * (double)j / (double)n;
         htw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
@@ -964,8 +966,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     cudaError_t e = cudaMemcpyAsync(tw, htw.data(), htw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, std::max(nb, 1) * sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = grlb::launch_spectral_prep(d->D, P.storage, d->D.buf[d->D.cur], gather, d->rho_ref, d->E_ref, d->gm1,
-                                       U, mu, part, grid, st);
+        e = grlb::launch_spectral_prep(d->D, P.storage, d->D.buf[d->D.cur], gather, U, mu, part, grid, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hpart.data(), part, grid * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -975,25 +976,33 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
         int ex = 0;
         const double mean = ke_sum / (double)N;
         if (mean > 0) std::frexp(mean, &ex);
-        const int fx = std::max(-1000, std::min(1000, 60 - ex));
+        // 2^fx / N^2 must stay a normal FP32 number: fx within [-126 + lg N^2, 127 + lg N^2]
+        const int lgN2 = 2 * (lgs_of(P.nx) + lgs_of(P.ny) + lgs_of(P.nz));
+        const int fx = std::max(-126 + lgN2, std::min(127 + lgN2, 60 - ex));
         const double fx_scale = std::ldexp(1.0, fx);
+        const float scale = std::ldexp(1.0f, fx - lgN2);
         const int64_t dimsz[3] = {P.nx, P.ny, P.nz};
+        const int lgs[3] = {lgs_of(P.nx), lgs_of(P.ny), lgs_of(P.nz)};
         auto axes = [&](float2* plane, bool inverse) -> cudaError_t {
             for (int a = 0; a < 3; ++a) {
                 if (dimsz[a] <= 1) continue;
                 grlb::FftAxis A;
                 A.log2n = lg;
+                int lg_in = 0;
                 if (a == 0) {
-                    A.stride = 1; A.inner = 1; A.inner_stride = 0; A.outer_stride = P.nx;
+                    A.stride = 1; lg_in = 0; A.inner_stride = 0; A.outer_stride = P.nx;
                     A.nlines = (int64_t)P.ny * P.nz;
                 } else if (a == 1) {
-                    A.stride = P.nx; A.inner = P.nx; A.inner_stride = 1; A.outer_stride = (int64_t)P.nx * P.ny;
+                    A.stride = P.nx; lg_in = lgs[0]; A.inner_stride = 1; A.outer_stride = (int64_t)P.nx * P.ny;
                     A.nlines = (int64_t)P.nx * P.nz;
                 } else {
-                    A.stride = (int64_t)P.nx * P.ny; A.inner = (int64_t)P.nx * P.ny; A.inner_stride = 1;
+                    A.stride = (int64_t)P.nx * P.ny; lg_in = lgs[0] + lgs[1]; A.inner_stride = 1;
                     A.outer_stride = 0; A.nlines = (int64_t)P.nx * P.ny;
                 }
+                A.lg_inner = lg_in;
+                A.inner_mask = ((int64_t)1 << lg_in) - 1;
                 A.L = grlb::fft_lines_per_cta(lg, A.nlines);
+                A.lgL = ilog2_exact(A.L);
                 cudaError_t r = grlb::launch_fft_axis(plane, tw, A, inverse, st);
                 if (r != cudaSuccess) return r;
             }
@@ -1001,8 +1010,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
         };
         for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = axes(U + c * N, false);
         if (e == cudaSuccess)
-            e = grlb::launch_spectral_modes(U, U + 3 * N, P.nx, P.ny, P.nz, nb,
-                                            1.0 / ((double)N * (double)N), fx_scale, bins, grid, st);
+            e = grlb::launch_spectral_modes(U, U + 3 * N, lgs[0], lgs[1], lgs[2], nb, scale, bins, grid, st);
         for (int c = 0; c < 4 && e == cudaSuccess; ++c) e = axes(U + c * N, true);
         if (e == cudaSuccess) e = grlb::launch_spectral_eps(U, mu, N, part, grid, st);
         if (e == cudaSuccess)

@@ -38,21 +38,22 @@ cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, d
 
 // ---- spectral post-processing (grlb_spectral.cu) ------------------------------------------
 // One batched FFT pass: lines of 2^log2n complex values `stride` apart; line l starts at
-// (l % inner) * inner_stride + (l / inner) * outer_stride; L lines per CTA.
+// (l & inner_mask) * inner_stride + (l >> lg_inner) * outer_stride (inner_mask = 2^lg_inner - 1);
+// L = 2^lgL lines per CTA, L divides nlines.
 struct FftAxis {
-    int log2n, L;
-    int64_t stride, inner, inner_stride, outer_stride, nlines;
+    int log2n, L, lgL, lg_inner;
+    int64_t stride, inner_mask, inner_stride, outer_stride, nlines;
 };
 constexpr int kFftSmemBytes = 32768;
 int fft_lines_per_cta(int log2n, int64_t nlines);
 cudaError_t launch_fft_axis(float2* data, const float2* tw, const FftAxis& A, bool inverse, cudaStream_t st);
 // Populations -> u (3 complex planes) and mu(T) (float plane), per-CTA sums of 1/2 |u|^2
 // (lattice units).  gather as for launch_conserved.
-cudaError_t launch_spectral_prep(const DomainDev& D, int storage, const void* fin, int gather, double rho_ref,
-                                 double E_ref, double gm1, float2* U, float* mu, double* partials, int grid,
-                                 cudaStream_t st);
-cudaError_t launch_spectral_modes(float2* U, float2* TH, int nx, int ny, int nz, int nbins, double inv_N2,
-                                  double fx_scale, unsigned long long* bins, int grid, cudaStream_t st);
+cudaError_t launch_spectral_prep(const DomainDev& D, int storage, const void* fin, int gather, float2* U, float* mu,
+                                 double* partials, int grid, cudaStream_t st);
+// scale = 2^fx / N^2 (a power of two): shell sums in fixed point with 2^-fx resolution
+cudaError_t launch_spectral_modes(float2* U, float2* TH, int lgx, int lgy, int lgz, int nbins, float scale,
+                                  unsigned long long* bins, int grid, cudaStream_t st);
 cudaError_t launch_spectral_eps(const float2* W, const float* mu, int64_t N, double* partials, int grid,
                                 cudaStream_t st);
 // FP32 FFMA issue-rate probe: ctas x 256 threads x iters x 128 FFMAs.

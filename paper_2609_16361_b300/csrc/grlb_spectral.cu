@@ -5,9 +5,10 @@
 // Pipeline (one stream, scratch from the stream-ordered pool, see grlb_api.cu):
 //   prep     populations -> u (3 complex planes, imaginary part 0) and mu(T) (one float
 //            plane); per-CTA FP64 sums of 1/2 |u|^2
-//   forward  FFT of each velocity plane along x, y and z: batched radix-2 lines in shared
-//            memory, L lines per CTA with consecutive bases so that the strided axes still
-//            read 16 consecutive x per row (128-byte segments)
+//   forward  FFT of each velocity plane along x, y and z: self-sorting (Stockham) passes of
+//            radix 16 / 8 / 4 / 2 on lines held in padded shared memory, 16 values per thread
+//            in registers; L lines per CTA with consecutive bases, so that the strided axes
+//            still read 16 consecutive x per row (128-byte segments)
 //   modes    shell binning of 1/2 |u^(m)|^2 into fixed-point integer sums (order independent,
 //            hence deterministic), then u^ -> (i k x u^, i k . u^) in place plus one plane
 //   inverse  FFT of the four derivative planes along x, y and z
@@ -20,18 +21,16 @@
 namespace grlb {
 
 // ---- prep: velocity and viscosity planes ---------------------------------------------------
-// Lattice-unit moments of the stored state (FP64 sums of the decoded deviations plus the
-// reference state), then rho_f = max(rho, rho_min), u = m / rho_f,
-// p = max((gamma-1)(E - |m|^2 / (2 rho_f)), p_min), T = p / rho_f and mu(T) (constant or
-// Sutherland, the closure of the collision, Sec. 2.4).  U receives u_x, u_y, u_z as complex
-// planes (imaginary part 0), mu the viscosity; each CTA writes its FP64 sum of 1/2 |u|^2
-// (fixed-order tree).  Periodic domains only.  gather = 1: one-buffer state after an odd
-// step, where f*_i(x) sits in slot i of x + c_i.
+// Lattice-unit moments of the stored state in FP32 deviation form (as the sweep takes them),
+// then rho_f = max(rho, rho_min), u = m / rho_f, p = max((gamma-1)(E - |m|^2 / (2 rho_f)),
+// p_min), T = p / rho_f and mu(T) (constant or Sutherland, the closure of the collision,
+// Sec. 2.4).  U receives u_x, u_y, u_z as complex planes (imaginary part 0), mu the viscosity;
+// each CTA writes its FP64 sum of 1/2 |u|^2 (fixed-order tree).  Periodic domains only.
+// gather = 1: one-buffer state after an odd step, where f*_i(x) sits in slot i of x + c_i.
 template <int S>
 __global__ void __launch_bounds__(256) spectral_prep_kernel(const DomainDev D, const void* __restrict__ fin_v,
-                                                            int gather, double rho_ref, double E_ref, double gm1,
-                                                            float2* __restrict__ U, float* __restrict__ mu_out,
-                                                            double* __restrict__ partials) {
+                                                            int gather, float2* __restrict__ U,
+                                                            float* __restrict__ mu_out, double* __restrict__ partials) {
     using T = typename Store<S>::T;
     __shared__ double red[256];
     const T* fin = static_cast<const T*>(fin_v);
@@ -52,29 +51,30 @@ __global__ void __launch_bounds__(256) spectral_prep_kernel(const DomainDev D, c
             at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
             at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
         }
-        double Q[NF];
+        float dQ[NF];
+#pragma unroll
         for (int k = 0; k < NF; ++k) {
-            double acc = 0.0;
-            for (int i = 0; i < NQ; ++i) acc += (double)Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
-            Q[k] = acc * (double)D.dec[k];
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
+            dQ[k] = acc * D.dec[k];
         }
-        Q[0] += rho_ref;
-        Q[4] += E_ref;
-        const double rf = fmax(Q[0], (double)D.rho_min);
-        const double u0 = Q[1] / rf, u1 = Q[2] / rf, u2 = Q[3] / rf;
-        const double mm = Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3];
-        const double p = fmax(gm1 * (Q[4] - 0.5 * mm / rf), (double)D.p_min);
-        double mu = (double)D.mu_ref;
+        const float rho = D.rho_ref + dQ[0];
+        const float rf = fmaxf(rho, D.rho_min);
+        const float u0 = dQ[1] / rf, u1 = dQ[2] / rf, u2 = dQ[3] / rf;
+        const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
+        // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
+        const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
+        float mu = D.mu_ref;
         if (D.sutherland) {
-            const double t = (p / rf) * (double)D.inv_T_ref;
-            const double ts = (double)D.T_S;
-            mu *= (1.0 + ts) * t * sqrt(t) / (t + ts);
+            const float t = (p / rf) * D.inv_T_ref;
+            mu *= (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
         }
-        U[c] = make_float2((float)u0, 0.0f);
-        U[N + c] = make_float2((float)u1, 0.0f);
-        U[2 * N + c] = make_float2((float)u2, 0.0f);
-        mu_out[c] = (float)mu;
-        ke += 0.5 * (u0 * u0 + u1 * u1 + u2 * u2);
+        U[c] = make_float2(u0, 0.0f);
+        U[N + c] = make_float2(u1, 0.0f);
+        U[2 * N + c] = make_float2(u2, 0.0f);
+        mu_out[c] = mu;
+        ke += (double)(0.5f * (u0 * u0 + u1 * u1 + u2 * u2));
     }
     red[threadIdx.x] = ke;
     __syncthreads();
@@ -85,15 +85,172 @@ __global__ void __launch_bounds__(256) spectral_prep_kernel(const DomainDev D, c
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
-// ---- batched radix-2 FFT along one axis ---------------------------------------------------
-// Line `line` (0 <= line < nlines) starts at (line % inner) * inner_stride +
-// (line / inner) * outer_stride and has n = 2^log2n elements `stride` apart.  A CTA transforms
-// L consecutive lines in shared memory: load in bit-reversed order, log2n in-place butterfly
-// stages (decimation in time), store in natural order.  tw[j] = exp(-2 pi i j / n),
-// j < n/2 (host-computed in FP64, rounded to FP32); INV uses the conjugate (unnormalised).
+// ---- batched FFTs along one axis ----------------------------------------------------------
+// Line `line` (0 <= line < nlines) starts at (line & (inner - 1)) * inner_stride +
+// (line >> lg_inner) * outer_stride and has n = 2^log2n elements `stride` apart (extents are
+// powers of two, so no integer division).  A CTA transforms L lines held in shared memory.
+// Global loads and stores of a strided axis run across the L lines (consecutive x), so a warp
+// touches 16-element (128-byte) row segments.  tw[m] = exp(-2 pi i m / n), m < n, host-computed
+// in FP64 and rounded to FP32; INV uses the conjugate (unnormalised inverse).
+
+// element (l, j) of the CTA's lines in shared memory: one pad slot per 16 elements and one per
+// line, so that stride-16 and line-to-line accesses fall in distinct banks
+__device__ __forceinline__ int sm_index(int l, int j, int LS) { return l * LS + j + (j >> 4); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// 16th roots of unity exp(-2 pi i k / 16), k = 0..7 (cos and sin of multiples of pi/8); k is a
+// compile-time constant wherever this is called, so the selection folds away
+__device__ __forceinline__ float2 root16(int k, bool inv) {
+    const float c = k == 0 ? 1.0f : k == 1 ? 0.92387953251128674f : k == 2 ? 0.70710678118654752f
+                  : k == 3 ? 0.38268343236508977f : k == 4 ? 0.0f : k == 5 ? -0.38268343236508977f
+                  : k == 6 ? -0.70710678118654752f : -0.92387953251128674f;
+    const float sn = k == 0 ? 0.0f : k == 1 ? 0.38268343236508977f : k == 2 ? 0.70710678118654752f
+                   : k == 3 ? 0.92387953251128674f : k == 4 ? 1.0f : k == 5 ? 0.92387953251128674f
+                   : k == 6 ? 0.70710678118654752f : 0.38268343236508977f;
+    return make_float2(c, inv ? sn : -sn);
+}
+
+// In-register DFT of R = 2, 4, 8 or 16 points: bit-reversal permutation, then radix-2
+// butterflies with the 16th roots of unity (all indices resolve at compile time).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2* v) {
+    constexpr int B = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 0; b < B; ++b) r |= ((i >> b) & 1) << (B - 1 - b);
+        if (r > i) {
+            const float2 t = v[i];
+            v[i] = v[r];
+            v[r] = t;
+        }
+    }
+#pragma unroll
+    for (int len = 2; len <= R; len <<= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += len) {
+#pragma unroll
+            for (int p = 0; p < len / 2; ++p) {
+                const float2 a = v[g + p];
+                const float2 b = p == 0 ? v[g + p + len / 2] : cmul(v[g + p + len / 2], root16(p * (16 / len), INV));
+                v[g + p] = make_float2(a.x + b.x, a.y + b.y);
+                v[g + p + len / 2] = make_float2(a.x - b.x, a.y - b.y);
+            }
+        }
+    }
+}
+
+// One Stockham (self-sorting) pass of radix R = 2^rb over a line of n = 2^lg points held in
+// shared memory, after passes whose radices multiply to Ns = 2^lgNs.  Thread q of the line
+// owns the items j = q + it n/16 (it < 16/R): it reads x[j + r n/R], multiplies by the twiddle
+// exp(-2 pi i r (j mod Ns) / (Ns R)), takes the R-point DFT and writes
+// y[(j div Ns) Ns R + (j mod Ns) + r Ns].  Reads complete (barrier) before writes.
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_pass(float2* line, int lg, int lgNs, int q, const float2* __restrict__ tw) {
+    constexpr int rb = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    constexpr int IT = 16 / R;
+    const int n16 = 1 << (lg - 4);
+    const int nR = 1 << (lg - rb);
+    float2 v[16];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = q + it * n16;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int a = j + r * nR;
+            v[it * R + r] = line[a + (a >> 4)];
+        }
+    }
+    __syncthreads();
+    const int Ns = 1 << lgNs;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = q + it * n16;
+        const int k = j & (Ns - 1);
+        const int step = k << (lg - lgNs - rb);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            float2 w = tw[r * step];
+            if (INV) w.y = -w.y;
+            v[it * R + r] = cmul(v[it * R + r], w);
+        }
+        dft_reg<R, INV>(v + it * R);
+        const int idx = ((j >> lgNs) << (lgNs + rb)) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int a = idx + r * Ns;
+            line[a + (a >> 4)] = v[it * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int64_t line_base(const FftAxis& A, int64_t line) {
+    return (line & A.inner_mask) * A.inner_stride + (line >> A.lg_inner) * A.outer_stride;
+}
+
+// n >= 16: L lines of n points per CTA, L n / 16 threads, each holding 16 values.
 template <bool INV>
-__global__ void __launch_bounds__(256) fft_axis_kernel(float2* __restrict__ data,
-                                                       const float2* __restrict__ tw, FftAxis A) {
+__global__ void __launch_bounds__(256, 3) fft16_axis_kernel(float2* __restrict__ data, const float2* __restrict__ tw,
+                                                         FftAxis A) {
+    extern __shared__ float2 sm[];
+    const int lg = A.log2n;
+    const int n = 1 << lg;
+    const int L = A.L;
+    const int LS = n + (n >> 4) + 1;
+    const int tot = L * n;
+    const int64_t l0 = (int64_t)blockIdx.x * L;
+    // every thread moves exactly 16 elements (L n = 16 blockDim): all 16 global loads are in
+    // flight before the first shared-memory store
+    float2 tmp[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int t = threadIdx.x + e * blockDim.x;
+        int l, j;
+        if (A.stride == 1) { l = t >> lg; j = t & (n - 1); }
+        else { j = t >> A.lgL; l = t & (L - 1); }
+        tmp[e] = data[line_base(A, l0 + l) + (int64_t)j * A.stride];
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int t = threadIdx.x + e * blockDim.x;
+        int l, j;
+        if (A.stride == 1) { l = t >> lg; j = t & (n - 1); }
+        else { j = t >> A.lgL; l = t & (L - 1); }
+        sm[sm_index(l, j, LS)] = tmp[e];
+    }
+    __syncthreads();
+    (void)tot;
+    const int l = threadIdx.x >> (lg - 4);
+    const int q = threadIdx.x & ((1 << (lg - 4)) - 1);
+    float2* line = sm + l * LS;
+    int lgNs = 0;
+    while (lgNs < lg) {
+        const int rem = lg - lgNs;
+        if (rem >= 4) { stockham_pass<16, INV>(line, lg, lgNs, q, tw); lgNs += 4; }
+        else if (rem == 3) { stockham_pass<8, INV>(line, lg, lgNs, q, tw); lgNs += 3; }
+        else if (rem == 2) { stockham_pass<4, INV>(line, lg, lgNs, q, tw); lgNs += 2; }
+        else { stockham_pass<2, INV>(line, lg, lgNs, q, tw); lgNs += 1; }
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int t = threadIdx.x + e * blockDim.x;
+        int ll, j;
+        if (A.stride == 1) { ll = t >> lg; j = t & (n - 1); }
+        else { j = t >> A.lgL; ll = t & (L - 1); }
+        data[line_base(A, l0 + ll) + (int64_t)j * A.stride] = sm[sm_index(ll, j, LS)];
+    }
+}
+
+// n < 16 (tiny domains): radix-2 decimation in time, bit-reversed load, one line per thread
+// group of n/2 butterflies per stage.
+template <bool INV>
+__global__ void __launch_bounds__(256) fft_small_axis_kernel(float2* __restrict__ data, const float2* __restrict__ tw,
+                                                             FftAxis A) {
     extern __shared__ float2 sm[];
     const int lg = A.log2n;
     const int n = 1 << lg;
@@ -101,43 +258,30 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(float2* __restrict__ data
     const int tot = L * n;
     const int64_t l0 = (int64_t)blockIdx.x * L;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int l, j;
-        if (A.stride == 1) { l = t >> lg; j = t & (n - 1); }
-        else { j = t / L; l = t - j * L; }
-        const int64_t line = l0 + l;
-        if (line >= A.nlines) continue;
-        const int64_t base = (line % A.inner) * A.inner_stride + (line / A.inner) * A.outer_stride;
+        const int l = t >> lg, j = t & (n - 1);
         const int r = (int)(__brev((unsigned)j) >> (32 - lg));
-        sm[l * n + r] = data[base + (int64_t)j * A.stride];
+        sm[l * n + r] = data[line_base(A, l0 + l) + (int64_t)j * A.stride];
     }
     __syncthreads();
     for (int s = 1; s <= lg; ++s) {
         const int half = 1 << (s - 1);
-        const int tshift = lg - s;
         for (int t = threadIdx.x; t < (tot >> 1); t += blockDim.x) {
             const int l = t >> (lg - 1);
             const int b = t & ((n >> 1) - 1);
             const int pos = b & (half - 1);
             const int i0 = ((b >> (s - 1)) << s) + pos;
-            const int i1 = i0 + half;
-            float2 w = tw[pos << tshift];
+            float2 w = tw[pos << (lg - s)];
             if (INV) w.y = -w.y;
             float2* row = sm + l * n;
-            const float2 a = row[i0], c = row[i1];
-            const float2 cw = make_float2(c.x * w.x - c.y * w.y, c.x * w.y + c.y * w.x);
-            row[i0] = make_float2(a.x + cw.x, a.y + cw.y);
-            row[i1] = make_float2(a.x - cw.x, a.y - cw.y);
+            const float2 a = row[i0], c = cmul(row[i0 + half], w);
+            row[i0] = make_float2(a.x + c.x, a.y + c.y);
+            row[i0 + half] = make_float2(a.x - c.x, a.y - c.y);
         }
         __syncthreads();
     }
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int l, j;
-        if (A.stride == 1) { l = t >> lg; j = t & (n - 1); }
-        else { j = t / L; l = t - j * L; }
-        const int64_t line = l0 + l;
-        if (line >= A.nlines) continue;
-        const int64_t base = (line % A.inner) * A.inner_stride + (line / A.inner) * A.outer_stride;
-        data[base + (int64_t)j * A.stride] = sm[l * n + j];
+        const int l = t >> lg, j = t & (n - 1);
+        data[line_base(A, l0 + l) + (int64_t)j * A.stride] = sm[l * n + j];
     }
 }
 
@@ -156,42 +300,74 @@ __device__ __forceinline__ int shell_of(int64_t M) {
 
 // ---- mode kernel: shell energies and spectral derivatives ---------------------------------
 // U: three planes of u^ (FP32 complex) for the nx x ny x nz index box; TH: one more plane.
-// Shell energy 1/2 |u^|^2 / N^2 is added to bins[shell] in fixed point (value * 2^fx_exp,
-// rounded to nearest): integer sums do not depend on the order of the additions.  Then the
-// planes are overwritten with i k x u^ (U) and i k . u^ (TH), k_a = 2 pi m_a / n_a, and a zero
-// derivative for the Nyquist index m_a = -n_a/2.
+// The shell energy 1/2 |u^|^2 / N^2 goes to bins[shell] in fixed point: value * scale with
+// scale = 2^fx / N^2 a power of two (exact in FP32), rounded to the nearest integer; integer
+// sums do not depend on the order of the additions.  The 32 lanes of a warp hold consecutive
+// cells; within one row and one sign half of m_x the shell index is monotone in x, so lanes of
+// equal (row, half, shell) are contiguous and a segmented shuffle scan leaves each group's sum
+// in its last lane, which adds it to the CTA's shared bins (distinct groups, distinct bins).
+// Then the planes are overwritten with i k x u^ (U) and i k . u^ (TH), k_a = 2 pi m_a / n_a,
+// zero for the Nyquist index m_a = -n_a/2.  Grid-stride over whole warps, 4 cells per lane per
+// trip (loads first); the loop bound is uniform across the CTA.
 __global__ void __launch_bounds__(256) spectral_modes_kernel(float2* __restrict__ U, float2* __restrict__ TH,
-                                                             int nx, int ny, int nz, int nbins, double inv_N2,
-                                                             double fx_scale, unsigned long long* __restrict__ bins) {
+                                                             int lgx, int lgy, int lgz, int nbins, float scale,
+                                                             unsigned long long* __restrict__ bins) {
     extern __shared__ unsigned long long sbins[];
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) sbins[b] = 0ull;
     __syncthreads();
-    const int64_t N = (int64_t)nx * ny * nz;
+    const int nx = 1 << lgx, ny = 1 << lgy, nz = 1 << lgz;
+    const int64_t N = (int64_t)1 << (lgx + lgy + lgz);
     const float tpx = 6.283185307179586f / (float)nx;
     const float tpy = 6.283185307179586f / (float)ny;
     const float tpz = 6.283185307179586f / (float)nz;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
-        const int jx = (int)(c % nx);
-        const int64_t r = c / nx;
-        const int jy = (int)(r % ny), jz = (int)(r / ny);
-        const int mx = signed_mode(jx, nx), my = signed_mode(jy, ny), mz = signed_mode(jz, nz);
-        const float2 a = U[c], b = U[N + c], d = U[2 * N + c];
-        const double e = 0.5 * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x + (double)b.y * b.y +
-                                (double)d.x * d.x + (double)d.y * d.y) * inv_N2;
-        const int sh = shell_of((int64_t)mx * mx + (int64_t)my * my + (int64_t)mz * mz);
-        if (sh < nbins) atomicAdd(&sbins[sh], (unsigned long long)__double2ull_rn(e * fx_scale));
-        const float kx = (nx > 1 && jx == (nx >> 1)) ? 0.0f : tpx * (float)mx;
-        const float ky = (ny > 1 && jy == (ny >> 1)) ? 0.0f : tpy * (float)my;
-        const float kz = (nz > 1 && jz == (nz >> 1)) ? 0.0f : tpz * (float)mz;
-        // i (k x u^): i (p + i q) = -q + i p with p + i q = (k x u^)_a
-        const float2 cx = make_float2(ky * d.x - kz * b.x, ky * d.y - kz * b.y);
-        const float2 cy = make_float2(kz * a.x - kx * d.x, kz * a.y - kx * d.y);
-        const float2 cz = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
-        const float2 dv = make_float2(kx * a.x + ky * b.x + kz * d.x, kx * a.y + ky * b.y + kz * d.y);
-        U[c] = make_float2(-cx.y, cx.x);
-        U[N + c] = make_float2(-cy.y, cy.x);
-        U[2 * N + c] = make_float2(-cz.y, cz.x);
-        TH[c] = make_float2(-dv.y, dv.x);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 - threadIdx.x < N; c0 += 4 * stride) {
+        float2 A[4], B[4], D[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t c = c0 + e * stride;
+            if (c < N) { A[e] = U[c]; B[e] = U[N + c]; D[e] = U[2 * N + c]; }
+            else { A[e] = B[e] = D[e] = make_float2(0.0f, 0.0f); }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t c = c0 + e * stride;
+            const bool in = c < N;
+            const float2 a = A[e], b = B[e], d = D[e];
+            const int jx = (int)(c & (nx - 1));
+            const int jy = (int)((c >> lgx) & (ny - 1));
+            const int jz = (int)(c >> (lgx + lgy));
+            const int mx = signed_mode(jx, nx), my = signed_mode(jy, ny), mz = signed_mode(jz, nz);
+            const float en = 0.5f * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + d.x * d.x + d.y * d.y);
+            const int sh = shell_of((int64_t)mx * mx + (int64_t)my * my + (int64_t)mz * mz);
+            const bool valid = in && sh < nbins;
+            // group key: (row, sign half of m_x, shell); lanes outside the domain get unique keys
+            const long long key = valid ? ((((c >> lgx) << 1) | (mx < 0 ? 1 : 0)) << 24) | sh : -1 - lane;
+            unsigned long long v = valid ? __float2ull_rn(en * scale) : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long t = __shfl_up_sync(0xffffffffu, v, off);
+                const long long k = __shfl_up_sync(0xffffffffu, key, off);
+                if (lane >= off && k == key) v += t;
+            }
+            const long long knext = __shfl_down_sync(0xffffffffu, key, 1);
+            if (valid && (lane == 31 || knext != key) && v) atomicAdd(&sbins[sh], v);
+            if (in) {
+                const float kx = (nx > 1 && jx == (nx >> 1)) ? 0.0f : tpx * (float)mx;
+                const float ky = (ny > 1 && jy == (ny >> 1)) ? 0.0f : tpy * (float)my;
+                const float kz = (nz > 1 && jz == (nz >> 1)) ? 0.0f : tpz * (float)mz;
+                // i (k x u^): i (p + i q) = -q + i p with p + i q = (k x u^)_a
+                const float2 cx = make_float2(ky * d.x - kz * b.x, ky * d.y - kz * b.y);
+                const float2 cy = make_float2(kz * a.x - kx * d.x, kz * a.y - kx * d.y);
+                const float2 cz = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
+                const float2 dv = make_float2(kx * a.x + ky * b.x + kz * d.x, kx * a.y + ky * b.y + kz * d.y);
+                U[c] = make_float2(-cx.y, cx.x);
+                U[N + c] = make_float2(-cy.y, cy.x);
+                U[2 * N + c] = make_float2(-cz.y, cz.x);
+                TH[c] = make_float2(-dv.y, dv.x);
+            }
+        }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x)
@@ -207,10 +383,10 @@ __global__ void __launch_bounds__(256) spectral_eps_kernel(const float2* __restr
     __shared__ double red[2][256];
     double es = 0.0, ed = 0.0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
-        const double wx = W[c].x, wy = W[N + c].x, wz = W[2 * N + c].x, th = W[3 * N + c].x;
-        const double m = mu[c];
-        es += m * (wx * wx + wy * wy + wz * wz);
-        ed += (4.0 / 3.0) * m * th * th;
+        const float wx = W[c].x, wy = W[N + c].x, wz = W[2 * N + c].x, th = W[3 * N + c].x;
+        const float m = mu[c];
+        es += (double)(m * (wx * wx + wy * wy + wz * wz));
+        ed += (double)((4.0f / 3.0f) * m * th * th);
     }
     red[0][threadIdx.x] = es;
     red[1][threadIdx.x] = ed;
@@ -248,37 +424,45 @@ __global__ void __launch_bounds__(256) ffma_probe_kernel(float* __restrict__ sin
 
 // ---- launchers ----------------------------------------------------------------------------
 int fft_lines_per_cta(int log2n, int64_t nlines) {
-    int L = kFftSmemBytes / (int)(sizeof(float2) << log2n);
-    if (L > 16) L = 16;
+    // n >= 16: L n = 4096 points per CTA (256 threads); smaller n: 32 KB of lines
+    int64_t L = log2n >= 4 ? (int64_t)4096 >> log2n : (int64_t)(kFftSmemBytes / (int)(sizeof(float2) << log2n));
     if (L < 1) L = 1;
-    while (L > 1 && (int64_t)L > nlines) L >>= 1;
-    return L;
+    if (log2n < 4 && L > 16) L = 16;
+    while (L > 1 && L > nlines) L >>= 1;
+    return (int)L;
 }
 
 cudaError_t launch_fft_axis(float2* data, const float2* tw, const FftAxis& A, bool inverse, cudaStream_t st) {
-    const int64_t grid = (A.nlines + A.L - 1) / A.L;
-    const size_t smem = (size_t)A.L * sizeof(float2) << A.log2n;
-    if (inverse) fft_axis_kernel<true><<<(unsigned)grid, 256, smem, st>>>(data, tw, A);
-    else fft_axis_kernel<false><<<(unsigned)grid, 256, smem, st>>>(data, tw, A);
+    const int64_t grid = A.nlines / A.L;
+    if (A.log2n >= 4) {
+        const int n = 1 << A.log2n;
+        const size_t smem = (size_t)A.L * (n + (n >> 4) + 1) * sizeof(float2);
+        const int threads = (A.L * n) >> 4;
+        if (inverse) fft16_axis_kernel<true><<<(unsigned)grid, threads, smem, st>>>(data, tw, A);
+        else fft16_axis_kernel<false><<<(unsigned)grid, threads, smem, st>>>(data, tw, A);
+    } else {
+        const size_t smem = (size_t)A.L * sizeof(float2) << A.log2n;
+        if (inverse) fft_small_axis_kernel<true><<<(unsigned)grid, 256, smem, st>>>(data, tw, A);
+        else fft_small_axis_kernel<false><<<(unsigned)grid, 256, smem, st>>>(data, tw, A);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_spectral_prep(const DomainDev& D, int storage, const void* fin, int gather, double rho_ref,
-                                 double E_ref, double gm1, float2* U, float* mu, double* partials, int grid,
-                                 cudaStream_t st) {
+cudaError_t launch_spectral_prep(const DomainDev& D, int storage, const void* fin, int gather, float2* U, float* mu,
+                                 double* partials, int grid, cudaStream_t st) {
     if (storage == S_F32)
-        spectral_prep_kernel<S_F32><<<grid, 256, 0, st>>>(D, fin, gather, rho_ref, E_ref, gm1, U, mu, partials);
+        spectral_prep_kernel<S_F32><<<grid, 256, 0, st>>>(D, fin, gather, U, mu, partials);
     else if (storage == S_F16)
-        spectral_prep_kernel<S_F16><<<grid, 256, 0, st>>>(D, fin, gather, rho_ref, E_ref, gm1, U, mu, partials);
+        spectral_prep_kernel<S_F16><<<grid, 256, 0, st>>>(D, fin, gather, U, mu, partials);
     else
-        spectral_prep_kernel<S_BF16><<<grid, 256, 0, st>>>(D, fin, gather, rho_ref, E_ref, gm1, U, mu, partials);
+        spectral_prep_kernel<S_BF16><<<grid, 256, 0, st>>>(D, fin, gather, U, mu, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_spectral_modes(float2* U, float2* TH, int nx, int ny, int nz, int nbins, double inv_N2,
-                                  double fx_scale, unsigned long long* bins, int grid, cudaStream_t st) {
+cudaError_t launch_spectral_modes(float2* U, float2* TH, int lgx, int lgy, int lgz, int nbins, float scale,
+                                  unsigned long long* bins, int grid, cudaStream_t st) {
     const size_t smem = (size_t)nbins * sizeof(unsigned long long);
-    spectral_modes_kernel<<<grid, 256, smem, st>>>(U, TH, nx, ny, nz, nbins, inv_N2, fx_scale, bins);
+    spectral_modes_kernel<<<grid, 256, smem, st>>>(U, TH, lgx, lgy, lgz, nbins, scale, bins);
     return cudaGetLastError();
 }
 
