@@ -267,14 +267,15 @@ grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init);
  *   derivatives d/dx_a <-> i k_a, k_a = 2 pi m_a / n (zero for the Nyquist index m_a = -n/2);
  *   sums[0] = eps_s = sum_x mu |curl u|^2, sums[1] = eps_d = sum_x 4/3 mu (div u)^2 (the units
  *   of grlb_diag's cell-local eps_s / eps_d), sums[2] = sum_x 1/2 |u|^2.
- *  d         domain (periodic; every extent above 1 the same power of two, 2..4096: cubes and
- *            squares with nz = 1).
+ *  d         domain: periodic, an n^3 cube (n in [16, 1024]) or an n x n x 1 square (n in
+ *            [32, 1024]), n a power of two.
  *  nbins     entries of spectrum to fill; shells beyond grlb_spectrum_shells(p) - 1 read 0,
  *            shells at or beyond nbins are left out of spectrum (not of sums).
  *  spectrum  host array of nbins doubles (may be NULL when nbins == 0).
  *  sums      host array of 3 doubles.
- * Scratch: 36 bytes per cell plus small tables, taken from the stream-ordered pool on the
- * domain's stream and returned before the call ends.  The call synchronises the domain's stream
+ * Five kernels (cubes; three for squares) move 372 bytes per cell (FP32 populations).  Scratch:
+ * 36 bytes per cell plus small tables, taken from the stream-ordered pool on the domain's
+ * stream and returned before the call ends.  The call synchronises the domain's stream
  * (twice).  Shell sums are accumulated in 64-bit fixed point (resolution 2^-60 of the total),
  * so the result does not depend on the order of the additions and is reproducible run to run.
  * Errors: GRLB_EINVAL for NULL pointers, negative nbins, a non-periodic domain or unsupported

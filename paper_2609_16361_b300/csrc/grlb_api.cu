@@ -928,23 +928,26 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
         return fail(GRLB_EINVAL, "grlb_spectral_diag: NULL or negative argument");
     const grlb_params& P = d->P;
     if (P.bc != GRLB_BC_PERIODIC) return fail(GRLB_EINVAL, "grlb_spectral_diag: periodic domains only");
-    int dims = 0;
-    const int n = spectral_extent(P, &dims);
-    const int lg = n > 1 ? ilog2_exact(n) : 0;
-    if (dims == 0 || n == 0 || lg < 1 || n > 4096)
-        return fail(GRLB_EINVAL, "grlb_spectral_diag: every extent above 1 must be the same power of two "
-                                 "between 2 and 4096");
+    const int n = P.nx;
+    const int lg = n > 1 ? ilog2_exact(n) : -1;
+    if (P.ny != n || (P.nz != 1 && P.nz != n) || lg < (P.nz > 1 ? 4 : 5) || lg > 10)
+        return fail(GRLB_EINVAL, "grlb_spectral_diag: needs an n^3 cube (n in [16, 1024]) or an n x n x 1 square "
+                                 "(n in [32, 1024]), n a power of two");
     const int shells = grlb_spectrum_shells(&P);
     const int nb = std::min<int>(nbins, shells);
     const int64_t N = d->D.plane;
-    const int grid = (int)std::min<int64_t>((N + 255) / 256, 148 * 8);
     cudaStream_t st = d->stream;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grlb::SpectralPlan plan = grlb::spectral_plan(lg, lg, P.nz > 1 ? lg : 0, nb, sms);
+    const int np = std::max(plan.grid1, 2 * plan.grid5);
 
     // scratch: 4 complex planes, mu plane, twiddles, per-CTA partials, shell bins
     const size_t oU = 0, oMu = align256(oU + 4 * (size_t)N * sizeof(float2));
     const size_t oTw = align256(oMu + (size_t)N * sizeof(float));
     const size_t oPart = align256(oTw + (size_t)n * sizeof(float2));
-    const size_t oBins = align256(oPart + 2 * (size_t)grid * sizeof(double));
+    const size_t oBins = align256(oPart + (size_t)np * sizeof(double));
     const size_t bytes = align256(oBins + (size_t)std::max(nb, 1) * sizeof(unsigned long long));
     char* base = nullptr;
     GRLB_CU(cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, st));
@@ -959,62 +962,31 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
         const double a = -2.0 * M_PI * (double)j / (double)n;
         htw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
-    std::vector<double> hpart(2 * (size_t)grid);
+    std::vector<double> hpart(np);
     std::vector<unsigned long long> hbins(std::max(nb, 1));
     const int gather = (P.streaming && (d->steps & 1)) ? 1 : 0;
     double ke_sum = 0.0;
     cudaError_t e = cudaMemcpyAsync(tw, htw.data(), htw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, std::max(nb, 1) * sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = grlb::launch_spectral_prep(d->D, P.storage, d->D.buf[d->D.cur], gather, U, mu, part, grid, st);
+        e = grlb::launch_spectral_k1(d->D, P.storage, d->D.buf[d->D.cur], gather, plan, tw, U, mu, part, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hpart.data(), part, grid * sizeof(double), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(hpart.data(), part, plan.grid1 * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) {
-        for (int i = 0; i < grid; ++i) ke_sum += hpart[i];
+        for (int i = 0; i < plan.grid1; ++i) ke_sum += hpart[i];
         // fixed point for the shell sums: total 1/2|u^|^2/N^2 = ke_sum / N stays below 2^60
         int ex = 0;
         const double mean = ke_sum / (double)N;
         if (mean > 0) std::frexp(mean, &ex);
         // 2^fx / N^2 must stay a normal FP32 number: fx within [-126 + lg N^2, 127 + lg N^2]
-        const int lgN2 = 2 * (lgs_of(P.nx) + lgs_of(P.ny) + lgs_of(P.nz));
+        const int lgN2 = 2 * (plan.lgx + plan.lgy + plan.lgz);
         const int fx = std::max(-126 + lgN2, std::min(127 + lgN2, 60 - ex));
         const double fx_scale = std::ldexp(1.0, fx);
-        const float scale = std::ldexp(1.0f, fx - lgN2);
-        const int64_t dimsz[3] = {P.nx, P.ny, P.nz};
-        const int lgs[3] = {lgs_of(P.nx), lgs_of(P.ny), lgs_of(P.nz)};
-        auto axes = [&](float2* plane, bool inverse) -> cudaError_t {
-            for (int a = 0; a < 3; ++a) {
-                if (dimsz[a] <= 1) continue;
-                grlb::FftAxis A;
-                A.log2n = lg;
-                int lg_in = 0;
-                if (a == 0) {
-                    A.stride = 1; lg_in = 0; A.inner_stride = 0; A.outer_stride = P.nx;
-                    A.nlines = (int64_t)P.ny * P.nz;
-                } else if (a == 1) {
-                    A.stride = P.nx; lg_in = lgs[0]; A.inner_stride = 1; A.outer_stride = (int64_t)P.nx * P.ny;
-                    A.nlines = (int64_t)P.nx * P.nz;
-                } else {
-                    A.stride = (int64_t)P.nx * P.ny; lg_in = lgs[0] + lgs[1]; A.inner_stride = 1;
-                    A.outer_stride = 0; A.nlines = (int64_t)P.nx * P.ny;
-                }
-                A.lg_inner = lg_in;
-                A.inner_mask = ((int64_t)1 << lg_in) - 1;
-                A.L = grlb::fft_lines_per_cta(lg, A.nlines);
-                A.lgL = ilog2_exact(A.L);
-                cudaError_t r = grlb::launch_fft_axis(plane, tw, A, inverse, st);
-                if (r != cudaSuccess) return r;
-            }
-            return cudaSuccess;
-        };
-        for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = axes(U + c * N, false);
+        plan.scale = std::ldexp(1.0f, fx - lgN2);
+        e = grlb::launch_spectral_k2_to_k5(plan, tw, U, mu, bins, part, st);
         if (e == cudaSuccess)
-            e = grlb::launch_spectral_modes(U, U + 3 * N, lgs[0], lgs[1], lgs[2], nb, scale, bins, grid, st);
-        for (int c = 0; c < 4 && e == cudaSuccess; ++c) e = axes(U + c * N, true);
-        if (e == cudaSuccess) e = grlb::launch_spectral_eps(U, mu, N, part, grid, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hpart.data(), part, 2 * grid * sizeof(double), cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(hpart.data(), part, 2 * plan.grid5 * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && nb > 0)
             e = cudaMemcpyAsync(hbins.data(), bins, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
         cudaError_t e2 = cudaFreeAsync(base, st);
@@ -1023,7 +995,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess) {
             double es = 0.0, ed = 0.0;
-            for (int i = 0; i < grid; ++i) {
+            for (int i = 0; i < plan.grid5; ++i) {
                 es += hpart[2 * i];
                 ed += hpart[2 * i + 1];
             }

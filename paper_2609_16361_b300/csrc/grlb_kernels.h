@@ -37,25 +37,26 @@ cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, d
                              double s, double rho_ref, double E_ref, int gather, cudaStream_t st);
 
 // ---- spectral post-processing (grlb_spectral.cu) ------------------------------------------
-// One batched FFT pass: lines of 2^log2n complex values `stride` apart; line l starts at
-// (l & inner_mask) * inner_stride + (l >> lg_inner) * outer_stride (inner_mask = 2^lg_inner - 1);
-// L = 2^lgL lines per CTA, L divides nlines.
-struct FftAxis {
-    int log2n, L, lgL, lg_inner;
-    int64_t stride, inner_mask, inner_stride, outer_stride, nlines;
+// Cubes (lgz > 0, n >= 16) or squares (lgz = 0, n >= 32) of extent n = 2^lg <= 1024.  grid1,
+// grid3, grid5: the persistent grids of K1, K3, K5 (set by the launchers to the resident CTA
+// count; the plan's values are upper bounds for sizing the partial-sum buffers); scale =
+// 2^fx / N^2 for the fixed-point shell sums (set after K1).
+struct SpectralPlan {
+    int lg, lgx, lgy, lgz;
+    int64_t N;
+    int nbins;
+    float scale;
+    int grid1, grid3, grid5;
 };
-constexpr int kFftSmemBytes = 32768;
-int fft_lines_per_cta(int log2n, int64_t nlines);
-cudaError_t launch_fft_axis(float2* data, const float2* tw, const FftAxis& A, bool inverse, cudaStream_t st);
-// Populations -> u (3 complex planes) and mu(T) (float plane), per-CTA sums of 1/2 |u|^2
-// (lattice units).  gather as for launch_conserved.
-cudaError_t launch_spectral_prep(const DomainDev& D, int storage, const void* fin, int gather, float2* U, float* mu,
-                                 double* partials, int grid, cudaStream_t st);
-// scale = 2^fx / N^2 (a power of two): shell sums in fixed point with 2^-fx resolution
-cudaError_t launch_spectral_modes(float2* U, float2* TH, int lgx, int lgy, int lgz, int nbins, float scale,
-                                  unsigned long long* bins, int grid, cudaStream_t st);
-cudaError_t launch_spectral_eps(const float2* W, const float* mu, int64_t N, double* partials, int grid,
-                                cudaStream_t st);
+SpectralPlan spectral_plan(int lgx, int lgy, int lgz, int nbins, int sms);
+// K1: populations -> x-transformed velocity planes U (3 N complex), mu (N), per-CTA sums of
+// 1/2 |u|^2 (grid1 doubles).  gather as for launch_conserved.
+cudaError_t launch_spectral_k1(const DomainDev& D, int storage, const void* fin, int gather, SpectralPlan& P,
+                               const float2* tw, float2* U, float* mu, double* partials, cudaStream_t st);
+// K2..K5: shell sums into bins (nbins, zeroed by the caller), per-CTA dissipation sums
+// (2 grid5 doubles); U needs 4 N complex.
+cudaError_t launch_spectral_k2_to_k5(SpectralPlan& P, const float2* tw, float2* U, const float* mu,
+                                     unsigned long long* bins, double* partials, cudaStream_t st);
 // FP32 FFMA issue-rate probe: ctas x 256 threads x iters x 128 FFMAs.
 cudaError_t launch_ffma_probe(float* sink, int ctas, int iters, cudaStream_t st);
 }  // namespace grlb

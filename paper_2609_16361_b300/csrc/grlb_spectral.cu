@@ -2,97 +2,33 @@
 // shell-averaged velocity spectrum and the solenoidal / dilatational dissipation computed with
 // spectral derivatives; plus the FFMA issue-rate probe used to place the instruction ceiling.
 //
-// Pipeline (one stream, scratch from the stream-ordered pool, see grlb_api.cu):
-//   prep     populations -> u (3 complex planes, imaginary part 0) and mu(T) (one float
-//            plane); per-CTA FP64 sums of 1/2 |u|^2
-//   forward  FFT of each velocity plane along x, y and z: self-sorting (Stockham) passes of
-//            radix 16 / 8 / 4 / 2 on lines held in padded shared memory, 16 values per thread
-//            in registers; L lines per CTA with consecutive bases, so that the strided axes
-//            still read 16 consecutive x per row (128-byte segments)
-//   modes    shell binning of 1/2 |u^(m)|^2 into fixed-point integer sums (order independent,
-//            hence deterministic), then u^ -> (i k x u^, i k . u^) in place plus one plane
-//   inverse  FFT of the four derivative planes along x, y and z
-//   eps      per-CTA FP64 sums of mu |omega|^2 and 4/3 mu theta^2 (fixed-order tree)
+// Five kernels on one stream (scratch from the stream-ordered pool, see grlb_api.cu); every
+// FFT runs on lines held in padded shared memory as self-sorting (Stockham) passes of radix
+// 16 / 8 / 4 / 2 with 16 values per thread in registers, so a line of n = 2^lg points needs
+// n / 16 threads.  For a cube (x, y, z) or a square (x, y):
+//   K1  prep + forward x: moments of the stored state -> u, mu(T) for a group of x-rows, FFT of
+//       the three velocity rows, store 3 complex planes and the mu plane; per-CTA FP64 sums
+//       of 1/2 |u|^2                                                    (168 B per cell)
+//   K2  forward y (cubes only): the 3 planes along y                    (48 B per cell)
+//   K3  forward along the last axis + modes + inverse along it: shell sums of 1/2 |u^|^2 in
+//       fixed point (order independent), i k x u^ and i k . u^, inverse FFT of the 4 planes
+//                                                                       (56 B per cell)
+//   K4  inverse y (cubes only): the 4 planes along y                    (64 B per cell)
+//   K5  inverse x + dissipation: per-CTA FP64 sums of mu |omega|^2 and 4/3 mu theta^2
+//                                                                       (36 B per cell)
+// 372 B per cell for a cube (FP32 populations), 260 for a square.  Extents are powers of two,
+// so all index arithmetic is shifts and masks; K1, K3 and K5 loop over line groups
+// (persistent grids, fixed assignment, hence reproducible sums).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "grlb_device.cuh"
 #include "grlb_kernels.h"
 
 namespace grlb {
 
-// ---- prep: velocity and viscosity planes ---------------------------------------------------
-// Lattice-unit moments of the stored state in FP32 deviation form (as the sweep takes them),
-// then rho_f = max(rho, rho_min), u = m / rho_f, p = max((gamma-1)(E - |m|^2 / (2 rho_f)),
-// p_min), T = p / rho_f and mu(T) (constant or Sutherland, the closure of the collision,
-// Sec. 2.4).  U receives u_x, u_y, u_z as complex planes (imaginary part 0), mu the viscosity;
-// each CTA writes its FP64 sum of 1/2 |u|^2 (fixed-order tree).  Periodic domains only.
-// gather = 1: one-buffer state after an odd step, where f*_i(x) sits in slot i of x + c_i.
-template <int S>
-__global__ void __launch_bounds__(256) spectral_prep_kernel(const DomainDev D, const void* __restrict__ fin_v,
-                                                            int gather, float2* __restrict__ U,
-                                                            float* __restrict__ mu_out, double* __restrict__ partials) {
-    using T = typename Store<S>::T;
-    __shared__ double red[256];
-    const T* fin = static_cast<const T*>(fin_v);
-    const int64_t N = D.plane;
-    const int nx = D.nx, ny = D.ny, nz = D.nz;
-    double ke = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t at[NQ] = {c, c, c, c, c, c, c};
-        if (gather) {
-            const int x = (int)(c % nx);
-            const int64_t r = c / nx;
-            const int y = (int)(r % ny), z = (int)(r / ny);
-            const int64_t row = c - x, pl = (int64_t)nx * ny;
-            at[1] = row + (x == nx - 1 ? 0 : x + 1);
-            at[2] = row + (x == 0 ? nx - 1 : x - 1);
-            at[3] = c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
-            at[4] = c + (int64_t)((y == 0) ? (ny - 1) : -1) * nx;
-            at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
-            at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
-        }
-        float dQ[NF];
-#pragma unroll
-        for (int k = 0; k < NF; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
-            dQ[k] = acc * D.dec[k];
-        }
-        const float rho = D.rho_ref + dQ[0];
-        const float rf = fmaxf(rho, D.rho_min);
-        const float u0 = dQ[1] / rf, u1 = dQ[2] / rf, u2 = dQ[3] / rf;
-        const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
-        // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
-        const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
-        float mu = D.mu_ref;
-        if (D.sutherland) {
-            const float t = (p / rf) * D.inv_T_ref;
-            mu *= (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
-        }
-        U[c] = make_float2(u0, 0.0f);
-        U[N + c] = make_float2(u1, 0.0f);
-        U[2 * N + c] = make_float2(u2, 0.0f);
-        mu_out[c] = mu;
-        ke += (double)(0.5f * (u0 * u0 + u1 * u1 + u2 * u2));
-    }
-    red[threadIdx.x] = ke;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
-}
-
-// ---- batched FFTs along one axis ----------------------------------------------------------
-// Line `line` (0 <= line < nlines) starts at (line & (inner - 1)) * inner_stride +
-// (line >> lg_inner) * outer_stride and has n = 2^log2n elements `stride` apart (extents are
-// powers of two, so no integer division).  A CTA transforms L lines held in shared memory.
-// Global loads and stores of a strided axis run across the L lines (consecutive x), so a warp
-// touches 16-element (128-byte) row segments.  tw[m] = exp(-2 pi i m / n), m < n, host-computed
-// in FP64 and rounded to FP32; INV uses the conjugate (unnormalised inverse).
-
+// ---- FFT core --------------------------------------------------------------------------------
 // element (l, j) of the CTA's lines in shared memory: one pad slot per 16 elements and one per
 // line, so that stride-16 and line-to-line accesses fall in distinct banks
 __device__ __forceinline__ int sm_index(int l, int j, int LS) { return l * LS + j + (j >> 4); }
@@ -113,6 +49,25 @@ __device__ __forceinline__ float2 root16(int k, bool inv) {
     return make_float2(c, inv ? sn : -sn);
 }
 
+// Radix-2 butterfly stages of span LEN, 2 LEN, ..., R over v (compile-time recursion, so no
+// stage loop is left for the compiler to keep rolled and index dynamically).
+template <int R, int LEN, bool INV>
+__device__ __forceinline__ void dft_stages(float2* v) {
+    if constexpr (LEN <= R) {
+#pragma unroll
+        for (int g = 0; g < R; g += LEN) {
+#pragma unroll
+            for (int p = 0; p < LEN / 2; ++p) {
+                const float2 a = v[g + p];
+                const float2 b = p == 0 ? v[g + p + LEN / 2] : cmul(v[g + p + LEN / 2], root16(p * (16 / LEN), INV));
+                v[g + p] = make_float2(a.x + b.x, a.y + b.y);
+                v[g + p + LEN / 2] = make_float2(a.x - b.x, a.y - b.y);
+            }
+        }
+        dft_stages<R, 2 * LEN, INV>(v);
+    }
+}
+
 // In-register DFT of R = 2, 4, 8 or 16 points: bit-reversal permutation, then radix-2
 // butterflies with the 16th roots of unity (all indices resolve at compile time).
 template <int R, bool INV>
@@ -129,32 +84,22 @@ __device__ __forceinline__ void dft_reg(float2* v) {
             v[r] = t;
         }
     }
-#pragma unroll
-    for (int len = 2; len <= R; len <<= 1) {
-#pragma unroll
-        for (int g = 0; g < R; g += len) {
-#pragma unroll
-            for (int p = 0; p < len / 2; ++p) {
-                const float2 a = v[g + p];
-                const float2 b = p == 0 ? v[g + p + len / 2] : cmul(v[g + p + len / 2], root16(p * (16 / len), INV));
-                v[g + p] = make_float2(a.x + b.x, a.y + b.y);
-                v[g + p + len / 2] = make_float2(a.x - b.x, a.y - b.y);
-            }
-        }
-    }
+    dft_stages<R, 2, INV>(v);
 }
 
-// One Stockham (self-sorting) pass of radix R = 2^rb over a line of n = 2^lg points held in
-// shared memory, after passes whose radices multiply to Ns = 2^lgNs.  Thread q of the line
-// owns the items j = q + it n/16 (it < 16/R): it reads x[j + r n/R], multiplies by the twiddle
-// exp(-2 pi i r (j mod Ns) / (Ns R)), takes the R-point DFT and writes
+// One Stockham (self-sorting) pass of radix R = 2^RB over a line of n = 2^LG points held in
+// shared memory, after passes whose radices multiply to Ns = 2^LGNS (all compile-time, so the
+// padded shared-memory offsets are immediates).  Thread q of the line owns the items
+// j = q + it n/16 (it < 16/R): it reads x[j + r n/R], multiplies by the twiddle
+// exp(-2 pi i r (j mod Ns) / (Ns R)) (1 in the first pass), takes the R-point DFT and writes
 // y[(j div Ns) Ns R + (j mod Ns) + r Ns].  Reads complete (barrier) before writes.
-template <int R, bool INV>
-__device__ __forceinline__ void stockham_pass(float2* line, int lg, int lgNs, int q, const float2* __restrict__ tw) {
-    constexpr int rb = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+template <int LG, int LGNS, int RB, bool INV>
+__device__ __forceinline__ void stockham_pass(float2* line, int q, const float2* __restrict__ tw) {
+    constexpr int R = 1 << RB;
     constexpr int IT = 16 / R;
-    const int n16 = 1 << (lg - 4);
-    const int nR = 1 << (lg - rb);
+    constexpr int n16 = 1 << (LG - 4);
+    constexpr int nR = 1 << (LG - RB);
+    constexpr int Ns = 1 << LGNS;
     float2 v[16];
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
@@ -166,20 +111,21 @@ __device__ __forceinline__ void stockham_pass(float2* line, int lg, int lgNs, in
         }
     }
     __syncthreads();
-    const int Ns = 1 << lgNs;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         const int j = q + it * n16;
         const int k = j & (Ns - 1);
-        const int step = k << (lg - lgNs - rb);
+        if (LGNS > 0) {
+            const int step = k << (LG - LGNS - RB);
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-            float2 w = tw[r * step];
-            if (INV) w.y = -w.y;
-            v[it * R + r] = cmul(v[it * R + r], w);
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * step];
+                if (INV) w.y = -w.y;
+                v[it * R + r] = cmul(v[it * R + r], w);
+            }
         }
         dft_reg<R, INV>(v + it * R);
-        const int idx = ((j >> lgNs) << (lgNs + rb)) + k;
+        const int idx = ((j >> LGNS) << (LGNS + RB)) + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int a = idx + r * Ns;
@@ -189,101 +135,55 @@ __device__ __forceinline__ void stockham_pass(float2* line, int lg, int lgNs, in
     __syncthreads();
 }
 
-__device__ __forceinline__ int64_t line_base(const FftAxis& A, int64_t line) {
-    return (line & A.inner_mask) * A.inner_stride + (line >> A.lg_inner) * A.outer_stride;
-}
-
-// n >= 16: L lines of n points per CTA, L n / 16 threads, each holding 16 values.
-template <bool INV>
-__global__ void __launch_bounds__(256, 3) fft16_axis_kernel(float2* __restrict__ data, const float2* __restrict__ tw,
-                                                         FftAxis A) {
-    extern __shared__ float2 sm[];
-    const int lg = A.log2n;
-    const int n = 1 << lg;
-    const int L = A.L;
-    const int LS = n + (n >> 4) + 1;
-    const int tot = L * n;
-    const int64_t l0 = (int64_t)blockIdx.x * L;
-    // every thread moves exactly 16 elements (L n = 16 blockDim): all 16 global loads are in
-    // flight before the first shared-memory store
-    float2 tmp[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int t = threadIdx.x + e * blockDim.x;
-        int l, j;
-        if (A.stride == 1) { l = t >> lg; j = t & (n - 1); }
-        else { j = t >> A.lgL; l = t & (L - 1); }
-        tmp[e] = data[line_base(A, l0 + l) + (int64_t)j * A.stride];
-    }
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int t = threadIdx.x + e * blockDim.x;
-        int l, j;
-        if (A.stride == 1) { l = t >> lg; j = t & (n - 1); }
-        else { j = t >> A.lgL; l = t & (L - 1); }
-        sm[sm_index(l, j, LS)] = tmp[e];
-    }
-    __syncthreads();
-    (void)tot;
-    const int l = threadIdx.x >> (lg - 4);
-    const int q = threadIdx.x & ((1 << (lg - 4)) - 1);
-    float2* line = sm + l * LS;
-    int lgNs = 0;
-    while (lgNs < lg) {
-        const int rem = lg - lgNs;
-        if (rem >= 4) { stockham_pass<16, INV>(line, lg, lgNs, q, tw); lgNs += 4; }
-        else if (rem == 3) { stockham_pass<8, INV>(line, lg, lgNs, q, tw); lgNs += 3; }
-        else if (rem == 2) { stockham_pass<4, INV>(line, lg, lgNs, q, tw); lgNs += 2; }
-        else { stockham_pass<2, INV>(line, lg, lgNs, q, tw); lgNs += 1; }
-    }
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int t = threadIdx.x + e * blockDim.x;
-        int ll, j;
-        if (A.stride == 1) { ll = t >> lg; j = t & (n - 1); }
-        else { j = t >> A.lgL; ll = t & (L - 1); }
-        data[line_base(A, l0 + ll) + (int64_t)j * A.stride] = sm[sm_index(ll, j, LS)];
+template <int LG, int LGNS, bool INV>
+__device__ __forceinline__ void fft_passes(float2* line, int q, const float2* __restrict__ tw) {
+    if constexpr (LGNS < LG) {
+        constexpr int RB = (LG - LGNS) >= 4 ? 4 : (LG - LGNS);
+        stockham_pass<LG, LGNS, RB, INV>(line, q, tw);
+        fft_passes<LG, LGNS + RB, INV>(line, q, tw);
     }
 }
 
-// n < 16 (tiny domains): radix-2 decimation in time, bit-reversed load, one line per thread
-// group of n/2 butterflies per stage.
-template <bool INV>
-__global__ void __launch_bounds__(256) fft_small_axis_kernel(float2* __restrict__ data, const float2* __restrict__ tw,
-                                                             FftAxis A) {
-    extern __shared__ float2 sm[];
-    const int lg = A.log2n;
-    const int n = 1 << lg;
-    const int L = A.L;
-    const int tot = L * n;
-    const int64_t l0 = (int64_t)blockIdx.x * L;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int l = t >> lg, j = t & (n - 1);
-        const int r = (int)(__brev((unsigned)j) >> (32 - lg));
-        sm[l * n + r] = data[line_base(A, l0 + l) + (int64_t)j * A.stride];
-    }
+// padded line length: one pad slot per 16 points and one per line
+template <int LG>
+struct Line {
+    static constexpr int n = 1 << LG;
+    static constexpr int LS = n + (n >> 4) + 1;
+};
+
+// FFT of the blockDim / (n / 16) lines of n = 2^LG >= 16 points held at sm + l LS: thread t
+// works on line t >> (LG - 4); all threads of the CTA call it (barriers inside).
+template <int LG, bool INV>
+__device__ __forceinline__ void cta_fft(float2* sm, const float2* __restrict__ tw) {
+    const int l = threadIdx.x >> (LG - 4);
+    const int q = threadIdx.x & ((1 << (LG - 4)) - 1);
+    fft_passes<LG, 0, INV>(sm + l * Line<LG>::LS, q, tw);
+}
+
+// Sum over the CTA (blockDim <= 256, any size) in a fixed order: fold onto the largest power
+// of two p2 <= blockDim, then a tree.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    red[threadIdx.x] = v;
     __syncthreads();
-    for (int s = 1; s <= lg; ++s) {
-        const int half = 1 << (s - 1);
-        for (int t = threadIdx.x; t < (tot >> 1); t += blockDim.x) {
-            const int l = t >> (lg - 1);
-            const int b = t & ((n >> 1) - 1);
-            const int pos = b & (half - 1);
-            const int i0 = ((b >> (s - 1)) << s) + pos;
-            float2 w = tw[pos << (lg - s)];
-            if (INV) w.y = -w.y;
-            float2* row = sm + l * n;
-            const float2 a = row[i0], c = cmul(row[i0 + half], w);
-            row[i0] = make_float2(a.x + c.x, a.y + c.y);
-            row[i0 + half] = make_float2(a.x - c.x, a.y - c.y);
-        }
+    int p2 = 1;
+    while (2 * p2 <= (int)blockDim.x) p2 *= 2;
+    if ((int)threadIdx.x >= p2) red[threadIdx.x - p2] += red[threadIdx.x];
+    __syncthreads();
+    for (int h = p2 >> 1; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int l = t >> lg, j = t & (n - 1);
-        data[line_base(A, l0 + l) + (int64_t)j * A.stride] = sm[l * n + j];
-    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
 }
+
+// lines per CTA of K1, K3, K5 (1024 points per line group) and of K2/K4 (4096 points)
+template <int LG>
+struct Groups {
+    static constexpr int L1 = (1024 >> LG) > 0 ? (1024 >> LG) : 1;
+    static constexpr int L2 = 4096 >> LG;
+};
 
 // ---- wavevector helpers -------------------------------------------------------------------
 // Signed integer wavenumber of FFT index j on an axis of n points: j for j < n/2, else j - n.
@@ -298,109 +198,262 @@ __device__ __forceinline__ int shell_of(int64_t M) {
     return b;
 }
 
-// ---- mode kernel: shell energies and spectral derivatives ---------------------------------
-// U: three planes of u^ (FP32 complex) for the nx x ny x nz index box; TH: one more plane.
-// The shell energy 1/2 |u^|^2 / N^2 goes to bins[shell] in fixed point: value * scale with
-// scale = 2^fx / N^2 a power of two (exact in FP32), rounded to the nearest integer; integer
-// sums do not depend on the order of the additions.  The 32 lanes of a warp hold consecutive
-// cells; within one row and one sign half of m_x the shell index is monotone in x, so lanes of
-// equal (row, half, shell) are contiguous and a segmented shuffle scan leaves each group's sum
-// in its last lane, which adds it to the CTA's shared bins (distinct groups, distinct bins).
-// Then the planes are overwritten with i k x u^ (U) and i k . u^ (TH), k_a = 2 pi m_a / n_a,
-// zero for the Nyquist index m_a = -n_a/2.  Grid-stride over whole warps, 4 cells per lane per
-// trip (loads first); the loop bound is uniform across the CTA.
-__global__ void __launch_bounds__(256) spectral_modes_kernel(float2* __restrict__ U, float2* __restrict__ TH,
-                                                             int lgx, int lgy, int lgz, int nbins, float scale,
-                                                             unsigned long long* __restrict__ bins) {
-    extern __shared__ unsigned long long sbins[];
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sbins[b] = 0ull;
-    __syncthreads();
-    const int nx = 1 << lgx, ny = 1 << lgy, nz = 1 << lgz;
-    const int64_t N = (int64_t)1 << (lgx + lgy + lgz);
-    const float tpx = 6.283185307179586f / (float)nx;
-    const float tpy = 6.283185307179586f / (float)ny;
-    const float tpz = 6.283185307179586f / (float)nz;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 - threadIdx.x < N; c0 += 4 * stride) {
-        float2 A[4], B[4], D[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int64_t c = c0 + e * stride;
-            if (c < N) { A[e] = U[c]; B[e] = U[N + c]; D[e] = U[2 * N + c]; }
-            else { A[e] = B[e] = D[e] = make_float2(0.0f, 0.0f); }
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int64_t c = c0 + e * stride;
-            const bool in = c < N;
-            const float2 a = A[e], b = B[e], d = D[e];
-            const int jx = (int)(c & (nx - 1));
-            const int jy = (int)((c >> lgx) & (ny - 1));
-            const int jz = (int)(c >> (lgx + lgy));
-            const int mx = signed_mode(jx, nx), my = signed_mode(jy, ny), mz = signed_mode(jz, nz);
-            const float en = 0.5f * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + d.x * d.x + d.y * d.y);
-            const int sh = shell_of((int64_t)mx * mx + (int64_t)my * my + (int64_t)mz * mz);
-            const bool valid = in && sh < nbins;
-            // group key: (row, sign half of m_x, shell); lanes outside the domain get unique keys
-            const long long key = valid ? ((((c >> lgx) << 1) | (mx < 0 ? 1 : 0)) << 24) | sh : -1 - lane;
-            unsigned long long v = valid ? __float2ull_rn(en * scale) : 0ull;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned long long t = __shfl_up_sync(0xffffffffu, v, off);
-                const long long k = __shfl_up_sync(0xffffffffu, key, off);
-                if (lane >= off && k == key) v += t;
+// ---- K1: prep + forward x ---------------------------------------------------------------------
+// Lattice-unit moments of the stored state in FP32 deviation form (as the sweep takes them),
+// then rho_f = max(rho, rho_min), u = m / rho_f, p = max((gamma-1)(E - |m|^2 / (2 rho_f)),
+// p_min), T = p / rho_f and mu(T) (constant or Sutherland, the closure of the collision,
+// Sec. 2.4).  A group is L consecutive x-rows (L n = 1024 consecutive cells); the three
+// velocity rows of each are transformed along x in shared memory and stored as complex planes
+// U[k N + c].  gather = 1: one-buffer state after an odd step, where f*_i(x) sits in slot i of
+// x + c_i.  3 L n / 16 = 192 threads.
+template <int S, int LG>
+__global__ void __launch_bounds__(192, 3) spectral_k1_kernel(const DomainDev D, const void* __restrict__ fin_v,
+                                                             int gather, SpectralPlan P, const float2* __restrict__ tw,
+                                                             float2* __restrict__ U, float* __restrict__ mu_out,
+                                                             double* __restrict__ partials) {
+    using T = typename Store<S>::T;
+    constexpr int n = 1 << LG, LS = Line<LG>::LS, L = Groups<LG>::L1;
+    extern __shared__ float2 sm[];
+    __shared__ double red[256];
+    const T* fin = static_cast<const T*>(fin_v);
+    const int64_t N = P.N;
+    const int nx = 1 << P.lgx, ny = 1 << P.lgy, nz = 1 << P.lgz;
+    const int64_t groups = (N >> LG) / L;
+    double ke = 0.0;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int64_t c0 = g * L * n;
+        for (int w = threadIdx.x; w < L * n; w += blockDim.x) {
+            const int64_t c = c0 + w;
+            int64_t at[NQ] = {c, c, c, c, c, c, c};
+            if (gather) {
+                const int x = (int)(c & (nx - 1));
+                const int y = (int)((c >> P.lgx) & (ny - 1));
+                const int z = (int)(c >> (P.lgx + P.lgy));
+                const int64_t row = c - x, pl = (int64_t)nx * ny;
+                at[1] = row + (x == nx - 1 ? 0 : x + 1);
+                at[2] = row + (x == 0 ? nx - 1 : x - 1);
+                at[3] = c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
+                at[4] = c + (int64_t)((y == 0) ? (ny - 1) : -1) * nx;
+                at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
+                at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
             }
-            const long long knext = __shfl_down_sync(0xffffffffu, key, 1);
-            if (valid && (lane == 31 || knext != key) && v) atomicAdd(&sbins[sh], v);
-            if (in) {
-                const float kx = (nx > 1 && jx == (nx >> 1)) ? 0.0f : tpx * (float)mx;
-                const float ky = (ny > 1 && jy == (ny >> 1)) ? 0.0f : tpy * (float)my;
-                const float kz = (nz > 1 && jz == (nz >> 1)) ? 0.0f : tpz * (float)mz;
-                // i (k x u^): i (p + i q) = -q + i p with p + i q = (k x u^)_a
-                const float2 cx = make_float2(ky * d.x - kz * b.x, ky * d.y - kz * b.y);
-                const float2 cy = make_float2(kz * a.x - kx * d.x, kz * a.y - kx * d.y);
-                const float2 cz = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
-                const float2 dv = make_float2(kx * a.x + ky * b.x + kz * d.x, kx * a.y + ky * b.y + kz * d.y);
-                U[c] = make_float2(-cx.y, cx.x);
-                U[N + c] = make_float2(-cy.y, cy.x);
-                U[2 * N + c] = make_float2(-cz.y, cz.x);
-                TH[c] = make_float2(-dv.y, dv.x);
+            float dQ[NF];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
+                dQ[k] = acc * D.dec[k];
             }
+            const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);
+            const float u0 = dQ[1] / rf, u1 = dQ[2] / rf, u2 = dQ[3] / rf;
+            const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
+            // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
+            const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
+            float mu = D.mu_ref;
+            if (D.sutherland) {
+                const float t = (p / rf) * D.inv_T_ref;
+                mu *= (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
+            }
+            mu_out[c] = mu;
+            ke += (double)(0.5f * (u0 * u0 + u1 * u1 + u2 * u2));
+            const int l = w >> LG, j = w & (n - 1);
+            sm[sm_index(l, j, LS)] = make_float2(u0, 0.0f);
+            sm[sm_index(L + l, j, LS)] = make_float2(u1, 0.0f);
+            sm[sm_index(2 * L + l, j, LS)] = make_float2(u2, 0.0f);
         }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
-        if (sbins[b]) atomicAdd(&bins[b], sbins[b]);
-}
-
-// ---- dissipation sums ---------------------------------------------------------------------
-// W: planes omega_x, omega_y, omega_z, theta (unnormalised inverse transforms, real parts).
-// Per CTA: sum of mu |omega|^2 and of 4/3 mu theta^2 (the 1/N^2 of the inverse transform is
-// applied by the host), reduced in a fixed order.
-__global__ void __launch_bounds__(256) spectral_eps_kernel(const float2* __restrict__ W, const float* __restrict__ mu,
-                                                           int64_t N, double* __restrict__ partials) {
-    __shared__ double red[2][256];
-    double es = 0.0, ed = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
-        const float wx = W[c].x, wy = W[N + c].x, wz = W[2 * N + c].x, th = W[3 * N + c].x;
-        const float m = mu[c];
-        es += (double)(m * (wx * wx + wy * wy + wz * wz));
-        ed += (double)((4.0f / 3.0f) * m * th * th);
-    }
-    red[0][threadIdx.x] = es;
-    red[1][threadIdx.x] = ed;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + h];
-            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        __syncthreads();
+        cta_fft<LG, false>(sm, tw);
+        for (int w = threadIdx.x; w < L * n; w += blockDim.x) {
+            const int l = w >> LG, j = w & (n - 1);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) U[k * N + c0 + w] = sm[sm_index(k * L + l, j, LS)];
         }
         __syncthreads();
     }
+    const double tot = block_sum(ke, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// ---- K2 / K4: FFT of several planes along y (cubes) -------------------------------------------
+// Lines along y: line id = x + nx z starts at x + nx ny z, stride nx.  A CTA takes L = 4096 / n
+// lines of consecutive x (16 for n = 256: 128-byte row segments) of plane blockIdx.y; every
+// thread moves 16 elements with one base address and a fixed increment.  256 threads.
+template <int LG, bool INV>
+__global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_fft_y_kernel(float2* __restrict__ U, SpectralPlan P,
+                                                                const float2* __restrict__ tw) {
+    constexpr int LS = Line<LG>::LS, L = Groups<LG>::L2;
+    constexpr int lgL = 12 - LG;
+    constexpr int jstep = 256 >> lgL;
+    extern __shared__ float2 sm[];
+    const int nx = 1 << P.lgx;
+    float2* plane = U + (int64_t)blockIdx.y * P.N;
+    const int l = threadIdx.x & (L - 1);
+    const int j0 = threadIdx.x >> lgL;
+    const int64_t id = (int64_t)blockIdx.x * L + l;
+    const int64_t base = (id & (nx - 1)) + ((id >> P.lgx) << (P.lgx + P.lgy));
+    float2* src = plane + base + (int64_t)j0 * nx;
+    const int64_t inc = (int64_t)jstep * nx;
+    float2 tmp[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tmp[e] = src[e * inc];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[sm_index(l, j0 + e * jstep, LS)] = tmp[e];
+    __syncthreads();
+    cta_fft<LG, INV>(sm, tw);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) src[e * inc] = sm[sm_index(l, j0 + e * jstep, LS)];
+}
+
+// ---- K3: forward + modes + inverse along the last axis -----------------------------------------
+// Lines along the last axis a (z for a cube, y for a square): line id < N / n starts at id,
+// stride N / n.  A group is L = 1024 / n lines of consecutive id.  After the forward FFT of the
+// three velocity lines, each point (line, j) of the group gives the shell energy
+// 1/2 |u^|^2 / N^2 in fixed point (value * scale, scale = 2^fx / N^2 a power of two: exact in
+// FP32; integer sums are order independent) and the derivatives i k x u^ and i k . u^
+// (k_a = 2 pi m_a / n, zero at the Nyquist index), written in place; then the four lines are
+// transformed back.  Lanes of a warp hold consecutive j of one line, where the shell index is
+// monotone within each sign half of m_a, so a segmented shuffle scan leaves each (line, half,
+// shell) sum in its last lane, which adds it to the CTA's shared bins.  4 L n / 16 = 256
+// threads, 4 points per thread and plane.
+template <int LG>
+__global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k3_kernel(float2* __restrict__ U, SpectralPlan P,
+                                                             const float2* __restrict__ tw,
+                                                             unsigned long long* __restrict__ bins) {
+    constexpr int n = 1 << LG, LS = Line<LG>::LS, L = Groups<LG>::L1;
+    constexpr int lgL = 10 - LG > 0 ? 10 - LG : 0;
+    constexpr int jstep = 256 >> lgL;
+    extern __shared__ float2 sm[];
+    unsigned long long* sbins = reinterpret_cast<unsigned long long*>(sm + 4 * L * LS);
+    for (int b = threadIdx.x; b < P.nbins; b += blockDim.x) sbins[b] = 0ull;
+    const int64_t N = P.N;
+    const int64_t S3 = N >> LG;             // stride of the last axis
+    const int64_t groups = S3 / L;
+    const bool cube = P.lgz > 0;
+    const int nx = 1 << P.lgx;
+    const float tp = 6.283185307179586f / (float)n;
+    const int lane = threadIdx.x & 31;
+    const int l_ld = threadIdx.x & (L - 1);
+    const int j0 = threadIdx.x >> lgL;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        float2* col = U + g * L + l_ld + (int64_t)j0 * S3;
+        const int64_t inc = (int64_t)jstep * S3;
+        float2 tmp[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) tmp[k * 4 + e] = col[k * N + e * inc];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sm[sm_index(k * L + l_ld, j0 + e * jstep, LS)] = tmp[k * 4 + e];
+        __syncthreads();
+        // all 4 L lines are transformed (one thread group per line); the fourth plane's lines
+        // hold stale values here and are overwritten by the mode pass below
+        cta_fft<LG, false>(sm, tw);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int w = threadIdx.x + e * 256;
+            const int l = w >> LG, j = w & (n - 1);
+            const int64_t id = g * L + l;
+            // wavevector: cube (x, y from the line id; z = j), square (x from the id; y = j)
+            const int ja = (int)(id & (nx - 1));
+            const int jb = cube ? (int)(id >> P.lgx) : j;
+            const int jc = cube ? j : 0;
+            const int ma = signed_mode(ja, n), mb = signed_mode(jb, n), mc = cube ? signed_mode(jc, n) : 0;
+            const float2 a = sm[sm_index(l, j, LS)];
+            const float2 b = sm[sm_index(L + l, j, LS)];
+            const float2 d = sm[sm_index(2 * L + l, j, LS)];
+            const float en = 0.5f * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + d.x * d.x + d.y * d.y);
+            const int sh = shell_of((int64_t)ma * ma + (int64_t)mb * mb + (int64_t)mc * mc);
+            const bool valid = sh < P.nbins;
+            const int mj = cube ? mc : mb;  // the component along the line
+            // a warp spans at most two lines (n >= 16): line parity, sign half and shell
+            // identify a group; invalid points get keys no other lane has
+            const int key = valid ? ((l & 1) << 16) | ((mj < 0 ? 1 : 0) << 15) | sh : -1 - lane;
+            unsigned long long v = valid ? __float2ull_rn(en * P.scale) : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long t = __shfl_up_sync(0xffffffffu, v, off);
+                const int kk = __shfl_up_sync(0xffffffffu, key, off);
+                if (lane >= off && kk == key) v += t;
+            }
+            const int knext = __shfl_down_sync(0xffffffffu, key, 1);
+            if (valid && (lane == 31 || knext != key) && v) atomicAdd(&sbins[sh], v);
+            const float kx = (ja == (n >> 1)) ? 0.0f : tp * (float)ma;
+            const float ky = (jb == (n >> 1)) ? 0.0f : tp * (float)mb;
+            const float kz = (!cube || jc == (n >> 1)) ? 0.0f : tp * (float)mc;
+            // i (k x u^): i (p + i q) = -q + i p with p + i q = (k x u^)_a
+            const float2 cx = make_float2(ky * d.x - kz * b.x, ky * d.y - kz * b.y);
+            const float2 cy = make_float2(kz * a.x - kx * d.x, kz * a.y - kx * d.y);
+            const float2 cz = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
+            const float2 dv = make_float2(kx * a.x + ky * b.x + kz * d.x, kx * a.y + ky * b.y + kz * d.y);
+            sm[sm_index(l, j, LS)] = make_float2(-cx.y, cx.x);
+            sm[sm_index(L + l, j, LS)] = make_float2(-cy.y, cy.x);
+            sm[sm_index(2 * L + l, j, LS)] = make_float2(-cz.y, cz.x);
+            sm[sm_index(3 * L + l, j, LS)] = make_float2(-dv.y, dv.x);
+        }
+        __syncthreads();
+        cta_fft<LG, true>(sm, tw);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) col[k * N + e * inc] = sm[sm_index(k * L + l_ld, j0 + e * jstep, LS)];
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < P.nbins; b += blockDim.x)
+        if (sbins[b]) atomicAdd(&bins[b], sbins[b]);
+}
+
+// ---- K5: inverse x + dissipation -------------------------------------------------------------
+// A group is L = 1024 / n consecutive x-rows of the four derivative planes; after the inverse
+// FFT along x the real parts are omega_x, omega_y, omega_z, theta (times N: the 1/N^2 of the
+// squares is applied by the host).  Per CTA: FP64 sums of mu |omega|^2 and 4/3 mu theta^2,
+// fixed order.  256 threads, 16 points per thread.
+template <int LG>
+__global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k5_kernel(const float2* __restrict__ U, const float* __restrict__ mu,
+                                                             SpectralPlan P, const float2* __restrict__ tw,
+                                                             double* __restrict__ partials) {
+    constexpr int n = 1 << LG, LS = Line<LG>::LS, L = Groups<LG>::L1;
+    extern __shared__ float2 sm[];
+    __shared__ double red[256];
+    const int64_t N = P.N;
+    const int64_t groups = (N >> LG) / L;
+    double es = 0.0, ed = 0.0;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int64_t c0 = g * L * n;
+        float2 tmp[16];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tmp[4 * e + k] = U[k * N + c0 + threadIdx.x + e * 256];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int w = threadIdx.x + e * 256;
+            const int l = w >> LG, j = w & (n - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sm[sm_index(k * L + l, j, LS)] = tmp[4 * e + k];
+        }
+        __syncthreads();
+        cta_fft<LG, true>(sm, tw);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int w = threadIdx.x + e * 256;
+            const int l = w >> LG, j = w & (n - 1);
+            const float wx = sm[sm_index(l, j, LS)].x, wy = sm[sm_index(L + l, j, LS)].x;
+            const float wz = sm[sm_index(2 * L + l, j, LS)].x, th = sm[sm_index(3 * L + l, j, LS)].x;
+            const float m = mu[c0 + w];
+            es += (double)(m * (wx * wx + wy * wy + wz * wz));
+            ed += (double)((4.0f / 3.0f) * m * th * th);
+        }
+        __syncthreads();
+    }
+    const double s1 = block_sum(es, red);
+    const double s2 = block_sum(ed, red);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = red[0][0];
-        partials[2 * blockIdx.x + 1] = red[1][0];
+        partials[2 * blockIdx.x] = s1;
+        partials[2 * blockIdx.x + 1] = s2;
     }
 }
 
@@ -423,53 +476,111 @@ __global__ void __launch_bounds__(256) ffma_probe_kernel(float* __restrict__ sin
 }
 
 // ---- launchers ----------------------------------------------------------------------------
-int fft_lines_per_cta(int log2n, int64_t nlines) {
-    // n >= 16: L n = 4096 points per CTA (256 threads); smaller n: 32 KB of lines
-    int64_t L = log2n >= 4 ? (int64_t)4096 >> log2n : (int64_t)(kFftSmemBytes / (int)(sizeof(float2) << log2n));
-    if (L < 1) L = 1;
-    if (log2n < 4 && L > 16) L = 16;
-    while (L > 1 && L > nlines) L >>= 1;
-    return (int)L;
+namespace {
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t launch_fft_axis(float2* data, const float2* tw, const FftAxis& A, bool inverse, cudaStream_t st) {
-    const int64_t grid = A.nlines / A.L;
-    if (A.log2n >= 4) {
-        const int n = 1 << A.log2n;
-        const size_t smem = (size_t)A.L * (n + (n >> 4) + 1) * sizeof(float2);
-        const int threads = (A.L * n) >> 4;
-        if (inverse) fft16_axis_kernel<true><<<(unsigned)grid, threads, smem, st>>>(data, tw, A);
-        else fft16_axis_kernel<false><<<(unsigned)grid, threads, smem, st>>>(data, tw, A);
-    } else {
-        const size_t smem = (size_t)A.L * sizeof(float2) << A.log2n;
-        if (inverse) fft_small_axis_kernel<true><<<(unsigned)grid, 256, smem, st>>>(data, tw, A);
-        else fft_small_axis_kernel<false><<<(unsigned)grid, 256, smem, st>>>(data, tw, A);
+// persistent grid: every CTA resident at once (no tail wave), at most `groups`
+template <typename K>
+int resident_grid(K kernel, int threads, size_t smem, int64_t groups) {
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return (int)std::min<int64_t>(groups, (int64_t)per * sms);
+}
+
+template <int LG>
+size_t line_bytes() { return (size_t)Line<LG>::LS * sizeof(float2); }
+
+template <int S, int LG>
+cudaError_t k1_t(const DomainDev& D, const void* fin, int gather, SpectralPlan& P, const float2* tw, float2* U,
+                 float* mu, double* partials, cudaStream_t st) {
+    constexpr int L = Groups<LG>::L1;
+    const size_t smem = 3 * L * line_bytes<LG>();
+    const int threads = (3 * L) << (LG - 4);
+    auto kern = spectral_k1_kernel<S, LG>;
+    cudaError_t e = allow_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    P.grid1 = resident_grid(kern, threads, smem, (P.N >> LG) / L);
+    kern<<<P.grid1, threads, smem, st>>>(D, fin, gather, P, tw, U, mu, partials);
+    return cudaGetLastError();
+}
+
+template <int LG>
+cudaError_t rest_t(SpectralPlan& P, const float2* tw, float2* U, const float* mu, unsigned long long* bins,
+                   double* partials, cudaStream_t st) {
+    cudaError_t e;
+    const bool cube = P.lgz > 0;
+    const size_t smem2 = Groups<LG>::L2 * line_bytes<LG>();
+    const unsigned grid2 = (unsigned)((P.N >> LG) / Groups<LG>::L2);
+    if (cube) {
+        if ((e = allow_smem(spectral_fft_y_kernel<LG, false>, smem2)) != cudaSuccess) return e;
+        spectral_fft_y_kernel<LG, false><<<dim3(grid2, 3), 256, smem2, st>>>(U, P, tw);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    constexpr int L = Groups<LG>::L1;
+    const size_t smem3 = 4 * L * line_bytes<LG>() + (size_t)P.nbins * sizeof(unsigned long long);
+    if ((e = allow_smem(spectral_k3_kernel<LG>, smem3)) != cudaSuccess) return e;
+    P.grid3 = resident_grid(spectral_k3_kernel<LG>, 256, smem3, (P.N >> LG) / L);
+    spectral_k3_kernel<LG><<<P.grid3, 256, smem3, st>>>(U, P, tw, bins);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (cube) {
+        if ((e = allow_smem(spectral_fft_y_kernel<LG, true>, smem2)) != cudaSuccess) return e;
+        spectral_fft_y_kernel<LG, true><<<dim3(grid2, 4), 256, smem2, st>>>(U, P, tw);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t smem5 = 4 * L * line_bytes<LG>();
+    if ((e = allow_smem(spectral_k5_kernel<LG>, smem5)) != cudaSuccess) return e;
+    P.grid5 = resident_grid(spectral_k5_kernel<LG>, 256, smem5, (P.N >> LG) / L);
+    spectral_k5_kernel<LG><<<P.grid5, 256, smem5, st>>>(U, mu, P, tw, partials);
     return cudaGetLastError();
 }
+}  // namespace
 
-cudaError_t launch_spectral_prep(const DomainDev& D, int storage, const void* fin, int gather, float2* U, float* mu,
-                                 double* partials, int grid, cudaStream_t st) {
-    if (storage == S_F32)
-        spectral_prep_kernel<S_F32><<<grid, 256, 0, st>>>(D, fin, gather, U, mu, partials);
-    else if (storage == S_F16)
-        spectral_prep_kernel<S_F16><<<grid, 256, 0, st>>>(D, fin, gather, U, mu, partials);
-    else
-        spectral_prep_kernel<S_BF16><<<grid, 256, 0, st>>>(D, fin, gather, U, mu, partials);
-    return cudaGetLastError();
+SpectralPlan spectral_plan(int lgx, int lgy, int lgz, int nbins, int sms) {
+    SpectralPlan P{};
+    P.lgx = lgx;
+    P.lgy = lgy;
+    P.lgz = lgz;
+    P.lg = lgx;
+    P.N = (int64_t)1 << (lgx + lgy + lgz);
+    P.nbins = nbins;
+    // upper bounds of the persistent grids (the launchers set the resident counts)
+    const int64_t g = (P.N >> P.lg) / std::max(1, 1024 >> P.lg);
+    P.grid1 = P.grid3 = P.grid5 = (int)std::min<int64_t>(g, (int64_t)sms * 8);
+    return P;
 }
 
-cudaError_t launch_spectral_modes(float2* U, float2* TH, int lgx, int lgy, int lgz, int nbins, float scale,
-                                  unsigned long long* bins, int grid, cudaStream_t st) {
-    const size_t smem = (size_t)nbins * sizeof(unsigned long long);
-    spectral_modes_kernel<<<grid, 256, smem, st>>>(U, TH, lgx, lgy, lgz, nbins, scale, bins);
-    return cudaGetLastError();
+cudaError_t launch_spectral_k1(const DomainDev& D, int storage, const void* fin, int gather, SpectralPlan& P,
+                               const float2* tw, float2* U, float* mu, double* partials, cudaStream_t st) {
+#define GRLB_K1(LGV)                                                                                   \
+    case LGV:                                                                                          \
+        if (storage == S_F32) return k1_t<S_F32, LGV>(D, fin, gather, P, tw, U, mu, partials, st);     \
+        if (storage == S_F16) return k1_t<S_F16, LGV>(D, fin, gather, P, tw, U, mu, partials, st);     \
+        return k1_t<S_BF16, LGV>(D, fin, gather, P, tw, U, mu, partials, st);
+    switch (P.lg) {
+        GRLB_K1(4) GRLB_K1(5) GRLB_K1(6) GRLB_K1(7) GRLB_K1(8) GRLB_K1(9) GRLB_K1(10)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GRLB_K1
 }
 
-cudaError_t launch_spectral_eps(const float2* W, const float* mu, int64_t N, double* partials, int grid,
-                                cudaStream_t st) {
-    spectral_eps_kernel<<<grid, 256, 0, st>>>(W, mu, N, partials);
-    return cudaGetLastError();
+cudaError_t launch_spectral_k2_to_k5(SpectralPlan& P, const float2* tw, float2* U, const float* mu,
+                                     unsigned long long* bins, double* partials, cudaStream_t st) {
+    switch (P.lg) {
+        case 4: return rest_t<4>(P, tw, U, mu, bins, partials, st);
+        case 5: return rest_t<5>(P, tw, U, mu, bins, partials, st);
+        case 6: return rest_t<6>(P, tw, U, mu, bins, partials, st);
+        case 7: return rest_t<7>(P, tw, U, mu, bins, partials, st);
+        case 8: return rest_t<8>(P, tw, U, mu, bins, partials, st);
+        case 9: return rest_t<9>(P, tw, U, mu, bins, partials, st);
+        case 10: return rest_t<10>(P, tw, U, mu, bins, partials, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_ffma_probe(float* sink, int ctas, int iters, cudaStream_t st) {
