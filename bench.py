@@ -672,6 +672,53 @@ def run_spectral(args):
     return 0
 
 
+def run_slabs(args):
+    """z-slab decomposition on one device: the n^3 Taylor-Green domain (FP32, RLB + sensor) as
+    2 and 4 z-slabs with one ghost plane on each side, the ghost exchange (grlb_halo_exchange_z)
+    before every step, against the undivided domain; MLUP/s of interior cells over --steps x 50
+    sweeps (CUDA events, 3 warm-up steps)."""
+    import torch
+    from paper_2609_16361_b300 import capi, decomp, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n = args.n
+    c = inputs.tgv3d(n)
+    N = c.params.ncells
+    sweeps = SWEEPS_PER_STEP * args.steps
+
+    def timed(step):
+        for _ in range(3):
+            step(SWEEPS_PER_STEP)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    out = {}
+    d = capi.Domain(c.params, stream=stream.cuda_stream)
+    d.init(c.rho, c.u, c.p)
+    out["undivided"] = N * sweeps / timed(d.step) / 1e6
+    d.close()
+    for S in (2, 4):
+        s = decomp.SlabSet(c, decomp.slab_sizes(n, S), stream=stream.cuda_stream)
+        s.init()
+        out[f"slabs{S}"] = N * sweeps / timed(s.step) / 1e6
+        s.close()
+    line = {"metric": "MLUP/s (interior cells) of the z-slab decomposition on one device",
+            "value": out["slabs2"], "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"tgv{n}_f32_rlb_sensor as z-slabs", "steps": args.steps,
+                       "sweeps_per_step": SWEEPS_PER_STEP},
+            "variants": out, "slabs2_vs_undivided": out["slabs2"] / out["undivided"],
+            "slabs4_vs_undivided": out["slabs4"] / out["undivided"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_capacity(args):
     """Largest grids on one device: the Taylor-Green workload with one population buffer (AA
     pattern) at 1024^3 in FP16 (75 GB of populations) and 768^3 in FP32 (63 GB) -- the paper runs
@@ -740,7 +787,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
-                             "capacity", "spectral"])
+                             "capacity", "spectral", "slabs"])
     ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=40)
@@ -760,6 +807,8 @@ def main():
         return run_tgv_series(args)
     if args.workload == "spectral":
         return run_spectral(args)
+    if args.workload == "slabs":
+        return run_slabs(args)
     if args.workload == "capacity":
         return run_capacity(args)
     return run_ours(args)

@@ -254,6 +254,23 @@ grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* f_in, void*
  * value other than 0 / 1. */
 grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init);
 
+/* ---- z-slab decomposition (one periodic domain split along z) -----------------------------
+ * The scheme's streaming moves one population per field across a z-face per step, so a domain
+ * splits into z-slabs that exchange two planes of 5 populations per step (the decomposition a
+ * multi-device run uses, here with both slabs on one device).  A slab of nz_s interior planes
+ * is an ordinary periodic domain of nz_s + 2 planes (ghost plane 0 below, nz_s + 1 above),
+ * initialised with the fields of the whole domain's planes z0 - 1 .. z0 + nz_s (periodic
+ * wrap).  Before every step call grlb_halo_exchange_z for every adjacent pair (lower, upper),
+ * including (last, first) of a periodic ring: it copies, for the five fields, the +z population
+ * of lower's top interior plane into upper's ghost plane 0 and the -z population of upper's
+ * bottom interior plane into lower's top ghost plane -- the only ghost values an interior cell
+ * pulls.  The interior cells then evolve bitwise as in the undivided domain (same kernel, same
+ * inputs); ghost-plane cells carry no meaning and enter the slab's own diagnostics, so interior
+ * totals are taken from the readback.  Enqueued on the slabs' common stream.
+ * Errors: GRLB_EINVAL for NULL domains, slabs that differ in nx, ny or storage, one-buffer
+ * streaming, non-periodic slabs, nz < 3, or different streams; GRLB_ECUDA on launch failure. */
+grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upper);
+
 /* ---- spectral post-processing (Sec. 3.4) ------------------------------------------------
  * The paper evaluates the Taylor-Green dissipation spectrally and shows the shell-averaged
  * velocity spectrum.  grlb_spectral_diag computes both from the domain's current state (the

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgrlb.so")
-SOURCES = ["grlb_kernels.cu", "grlb_spectral.cu", "grlb_init_ce.cu", "grlb_api.cu"]
+SOURCES = ["grlb_kernels.cu", "grlb_spectral.cu", "grlb_init_ce.cu", "grlb_halo.cu", "grlb_api.cu"]
 HEADERS = ["grlb_device.cuh", "grlb_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -108,6 +108,7 @@ def lib():
             "grlb_spectral_diag": ([vp, C.c_int32, dp, dp], i32),
             "grlb_ffma_probe": ([C.c_int32, C.c_int32, vp, vp, dp], i32),
             "grlb_set_init_mode": ([vp, C.c_int32], i32),
+            "grlb_halo_exchange_z": ([vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -127,7 +128,7 @@ def exported_symbols():
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
             "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe",
-            "grlb_set_init_mode"]
+            "grlb_set_init_mode", "grlb_halo_exchange_z"]
 
 
 def check(status):
@@ -297,6 +298,10 @@ def grlb_step_diag_noalloc(prm, f_in_ptr, f_out_ptr, diag_out_ptr, stream=None):
 
 def grlb_set_init_mode(h, ce_init):
     check(lib().grlb_set_init_mode(h, int(ce_init)))
+
+
+def grlb_halo_exchange_z(lower, upper):
+    check(lib().grlb_halo_exchange_z(lower, upper))
 
 
 def grlb_spectrum_shells(prm) -> int:

@@ -1011,6 +1011,23 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     return GRLB_OK;
 }
 
+extern "C" grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upper) {
+    if (!lower || !upper) return fail(GRLB_EINVAL, "grlb_halo_exchange_z: NULL domain");
+    const grlb_params& a = lower->P;
+    const grlb_params& b = upper->P;
+    if (a.nx != b.nx || a.ny != b.ny || a.storage != b.storage)
+        return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs differ in nx, ny or storage");
+    if (a.streaming || b.streaming) return fail(GRLB_EINVAL, "grlb_halo_exchange_z: two-buffer streaming only");
+    if (a.bc != GRLB_BC_PERIODIC || b.bc != GRLB_BC_PERIODIC)
+        return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs are periodic domains");
+    if (a.nz < 3 || b.nz < 3) return fail(GRLB_EINVAL, "grlb_halo_exchange_z: a slab needs nz >= 3 (2 ghost planes)");
+    if (lower->stream != upper->stream)
+        return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs must share one stream");
+    GRLB_CU(grlb::launch_halo_z(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], lower->D.plane,
+                                upper->D.plane, a.nz, (int64_t)a.nx * a.ny, elem_bytes(a.storage), lower->stream));
+    return GRLB_OK;
+}
+
 extern "C" grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     if (ce_init != 0 && ce_init != 1) return fail(GRLB_EINVAL, "grlb_set_init_mode: ce_init must be 0 or 1");

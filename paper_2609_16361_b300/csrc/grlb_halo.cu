@@ -1,0 +1,50 @@
+// grlb_halo.cu -- ghost-plane exchange of z-slabs (one domain split along z).
+//
+// A slab of nz interior planes lives in an ordinary periodic domain of nz + 2 planes: ghost
+// plane 0 below, nz + 1 above.  In a pull sweep an interior cell reads from a ghost plane only
+// the population travelling into the slab: f_{k,+z} from plane 0 (into plane 1) and f_{k,-z}
+// from plane nz + 1 (into plane nz).  So the exchange copies, for the five fields k, the +z
+// population of the lower slab's top interior plane into the upper slab's plane 0, and the -z
+// population of the upper slab's bottom interior plane into the lower slab's top ghost plane;
+// the interior cells then compute exactly what the undivided domain computes.  One launch per
+// pair: 10 slices of nx ny elements (2 x 5 fields).
+#include <cuda_runtime.h>
+
+#include "grlb_device.cuh"
+#include "grlb_kernels.h"
+
+namespace grlb {
+
+template <typename T>
+__global__ void __launch_bounds__(256) halo_z_kernel(T* __restrict__ lower, T* __restrict__ upper, int64_t plane_lo,
+                                                     int64_t plane_up, int nzl, int64_t nxy) {
+    // slices: s < 5: +z of field s, lower top interior (z = nzl - 2) -> upper ghost (z = 0);
+    //         s >= 5: -z of field s - 5, upper bottom interior (z = 1) -> lower ghost (z = nzl - 1)
+    const int s = blockIdx.y;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
+        if (s < 5) {
+            const int q = 7 * s + 5;
+            upper[q * plane_up + c] = lower[q * plane_lo + (int64_t)(nzl - 2) * nxy + c];
+        } else {
+            const int q = 7 * (s - 5) + 6;
+            lower[q * plane_lo + (int64_t)(nzl - 1) * nxy + c] = upper[q * plane_up + nxy + c];
+        }
+    }
+}
+
+cudaError_t launch_halo_z(void* lower, void* upper, int64_t plane_lo, int64_t plane_up, int nzl, int64_t nxy,
+                          size_t elem, cudaStream_t st) {
+    int64_t blocks = (nxy + 255) / 256;
+    if (blocks > 148 * 4) blocks = 148 * 4;
+    const dim3 grid((unsigned)blocks, 10);
+    if (elem == 4)
+        halo_z_kernel<float><<<grid, 256, 0, st>>>(static_cast<float*>(lower), static_cast<float*>(upper), plane_lo,
+                                                   plane_up, nzl, nxy);
+    else
+        halo_z_kernel<unsigned short><<<grid, 256, 0, st>>>(static_cast<unsigned short*>(lower),
+                                                            static_cast<unsigned short*>(upper), plane_lo, plane_up,
+                                                            nzl, nxy);
+    return cudaGetLastError();
+}
+
+}  // namespace grlb

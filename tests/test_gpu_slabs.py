@@ -1,0 +1,59 @@
+"""z-slab decomposition on one GPU (grlb_halo_exchange_z): the interior of the slabs evolves
+bitwise as the undivided domain, for uneven slabs, ragged CTA tiles, FP16 storage and the
+Chapman-Enskog start; interior totals add up to the whole domain's."""
+import numpy as np
+import pytest
+
+from paper_2609_16361_b300 import capi, decomp, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def whole_run(case, steps, ce=None):
+    d = capi.Domain(case.params.replace(streaming=0))
+    d.init(case.rho, case.u, case.p, ce_init=ce)
+    d.step(steps)
+    Q = d.conserved()
+    d.close()
+    return Q
+
+
+def slab_run(case, sizes, steps, ce=None):
+    s = decomp.SlabSet(case, sizes)
+    s.init(ce_init=ce)
+    s.step(steps)
+    Q = s.conserved()
+    tot = s.interior_totals()
+    s.close()
+    return Q, tot
+
+
+@pytest.mark.parametrize("case,sizes,steps", [
+    (lambda: inputs.tgv3d(32), [16, 16], 40),
+    (lambda: inputs.random_smooth(40, 21, 24, seed=5), [5, 9, 10], 30),
+    (lambda: inputs.tgv3d(32, storage=inputs.STORE_F16), [12, 20], 30),
+    (lambda: inputs.random_smooth(32, 32, 32, seed=8, collision=inputs.COLL_BGK), [8, 8, 8, 8], 25),
+])
+def test_slabs_bitwise_equal_the_undivided_run(case, sizes, steps):
+    c = case()
+    Qw = whole_run(c, steps)
+    Qs, tot = slab_run(c, sizes, steps)
+    assert np.array_equal(Qs, Qw)
+    np.testing.assert_allclose(np.sum(tot, axis=0), Qw.sum(axis=1), rtol=1e-12)
+
+
+def test_slabs_with_chapman_enskog_start():
+    c = inputs.tgv3d(32, mach=0.5, re=100.0, fmu=0.001)
+    assert np.array_equal(slab_run(c, [10, 22], 20, ce=True)[0], whole_run(c, 20, ce=True))
+
+
+def test_exchange_rejects_unsuitable_slabs():
+    c = inputs.random_smooth(16, 16, 16, seed=1)
+    a = capi.Domain(c.params)
+    b = capi.Domain(c.params.replace(streaming=1))
+    e = capi.Domain(c.params.replace(nx=8))
+    for x, y in ((a, b), (a, e)):
+        with pytest.raises(capi.GrlbError):
+            capi.grlb_halo_exchange_z(x.h, y.h)
+    for d in (a, b, e):
+        d.close()
