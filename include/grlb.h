@@ -60,8 +60,10 @@ typedef struct {
     double T_ref;               /* Sutherland reference temperature (T = p/rho, > 0)        */
     int32_t sutherland;         /* 1: mu(T) by the Sutherland law of Listing 1; 0: constant */
     int32_t streaming;          /* 0: two population buffers (pull); 1: one buffer updated in
-                                   place by the AA pattern (half the memory, same traffic,
-                                   bitwise the same results); sources and batches need 0     */
+                                   place by the AA pattern (half the memory, same traffic, the
+                                   same collisions: results agree with 0 to FP32 rounding);
+                                   sources need 0, batches 0 for domains they run in the
+                                   batched kernel (below solo_min_cells)                     */
     double T_S;                 /* Sutherland constant relative to T_ref (0.4042)           */
     double omega_rho, omega_mom, omega_E; /* per-field relaxation 1/tau_LB, in (0, 2]       */
     double omega_min;           /* sensor floor rate (Listing 2)                            */
@@ -172,7 +174,7 @@ int64_t grlb_steps_done(const grlb_domain* d);
  * the tiles of every active small domain (one launch per storage/collision group), plus one
  * single-domain sweep per active large domain (at least solo_min_cells cells; it saturates
  * the GPU on its own and runs the kernel grlb_step runs, so its result is bitwise that of
- * grlb_step).  A 128-thread CTA covers tile_x cells along x times 128/tile_x rows.  A small
+ * grlb_step; a large domain may use one-buffer streaming, a small one may not).  A 128-thread CTA covers tile_x cells along x times 128/tile_x rows.  A small
  * domain's result does not depend on the other domains of the batch and matches grlb_step
  * within FP32 rounding.  All domains must live on the same device; the batch runs on the
  * stream of domains[0] (or the one set with grlb_batch_set_stream). */

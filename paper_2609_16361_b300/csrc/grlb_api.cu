@@ -693,15 +693,19 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
             delete b;
             return fail(GRLB_EINVAL, "NULL domain in batch");
         }
-        if (domains[i]->D.src || domains[i]->P.streaming) {
+        const int64_t thr = b->cfg.solo_min_cells == 0 ? 262144 : b->cfg.solo_min_cells;
+        const int solo = thr > 0 && domains[i]->D.plane >= thr ? 1 : 0;
+        // the batched kernel runs two-buffer domains without a source; a domain advanced on its
+        // own (solo) may use one-buffer streaming
+        if (domains[i]->D.src || (domains[i]->P.streaming && !solo)) {
             delete b;
-            return fail(GRLB_EINVAL, "batched domains need two-buffer streaming and no source term");
+            return fail(GRLB_EINVAL, "batched domains need two-buffer streaming (unless at least solo_min_cells "
+                                     "cells) and no source term");
         }
         b->doms.push_back(domains[i]);
         b->active.push_back(1);
         b->tile_x.push_back(0);
-        const int64_t thr = b->cfg.solo_min_cells == 0 ? 262144 : b->cfg.solo_min_cells;
-        b->solo.push_back(thr > 0 && domains[i]->D.plane >= thr ? 1 : 0);
+        b->solo.push_back(solo);
     }
     b->stream = domains[0]->stream;
     retain_pool();

@@ -12,6 +12,9 @@ ones (each fills the GPU on its own) only the one with the least remaining work
 behind long ones.  A finished request's conserved fields are read back and its memory is
 released, which may admit waiting requests.
 
+With one_buffer_large, large requests keep one population buffer (AA pattern: half their
+memory, the same traffic and collisions); small ones stay two-buffer for the batched kernel.
+
 A domain's result does not depend on which other domains share its launches, so every
 request's result is bitwise the same alone and in the mix.  `serial_plain` is the baseline:
 the same trace first-in first-out, one domain at a time, one single-domain launch per step.
@@ -58,7 +61,8 @@ def _finish(res: Result, dom: capi.Domain, t0: float, keep: bool):
 class Server:
     def __init__(self, hbm_budget: float = 150e9, max_resident: int = 512, chunk: int = 200,
                  use_graph: bool = True, tile_table: dict | None = None, stream=None,
-                 keep_fields: bool = False, large_cells: int = 262144, srpt: bool = True):
+                 keep_fields: bool = False, large_cells: int = 262144, srpt: bool = True,
+                 one_buffer_large: bool = False):
         import torch
         self.budget = float(hbm_budget)
         self.max_resident = max_resident
@@ -72,6 +76,9 @@ class Server:
         self.keep_fields = keep_fields
         self.large_cells = large_cells  # same threshold as the batch's solo_min_cells
         self.srpt = srpt
+        # large requests with one population buffer (AA pattern): half their memory, same
+        # traffic; small ones run in the batched kernel, which needs two buffers
+        self.one_buffer_large = one_buffer_large
 
     def run(self, trace, realtime: bool = True, lookahead: int = 12):
         """Serve `trace` (list of inputs.Request sorted by arrival).  Returns Results in
@@ -139,7 +146,8 @@ class Server:
                 # admission: FIFO while the head fits in the budget and a slot is free
                 while waiting and len(resident) < self.max_resident:
                     r = waiting[0]
-                    need = capi.grlb_bytes_for(r.case.params)
+                    prm = request_params(r, self.large_cells, self.one_buffer_large)
+                    need = capi.grlb_bytes_for(prm)
                     if need == 0:
                         raise capi.GrlbError(-1, f"request {r.rid}: invalid parameters")
                     with lock:
@@ -150,7 +158,7 @@ class Server:
                             raise capi.GrlbError(-2, f"request {r.rid} needs {need} B > budget")
                         break
                     waiting.popleft()
-                    dom = capi.Domain(r.case.params, stream=st)
+                    dom = capi.Domain(prm, stream=st)
                     capi.grlb_stage_primitive(dom.h, host(r.case.rho), host(r.case.u), host(r.case.p))
                     capi.grlb_init_from_stage(dom.h)
                     res = Result(r.rid, r.kind, r.steps, r.case.params.ncells,
@@ -217,9 +225,17 @@ class Server:
         return [results[r.rid] for r in sorted(trace, key=lambda r: r.rid)]
 
 
-def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = False):
+def request_params(r, large_cells: int, one_buffer_large: bool):
+    """Domain parameters of a request: one population buffer for large requests if asked."""
+    if one_buffer_large and r.case.params.ncells >= large_cells:
+        return r.case.params.replace(streaming=1)
+    return r.case.params
+
+
+def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = False,
+                 one_buffer_large: bool = False, large_cells: int = 262144):
     """Baseline: first-in first-out, one domain at a time, one single-domain launch per step
-    (no batching, no graphs)."""
+    (no batching, no graphs); the same buffer choice per request as the server's."""
     import torch
     stream = stream or torch.cuda.Stream()
     st = stream.cuda_stream
@@ -232,7 +248,7 @@ def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = 
                 time.sleep(wait)
         res = Result(r.rid, r.kind, r.steps, r.case.params.ncells, r.arrival if realtime else 0.0,
                      admitted=time.perf_counter() - t0)
-        dom = capi.Domain(r.case.params, stream=st)
+        dom = capi.Domain(request_params(r, large_cells, one_buffer_large), stream=st)
         dom.init(r.case.rho, r.case.u, r.case.p)
         dom.step(r.steps)
         _finish(res, dom, t0, keep_fields)

@@ -55,3 +55,28 @@ def test_request_larger_than_budget_is_refused():
     trace = small_trace(n=1, seed=5)
     with pytest.raises(capi.GrlbError):
         serve.Server(hbm_budget=1000).run(trace, realtime=False)
+
+
+def test_one_buffer_large_requests():
+    """Large requests with one population buffer: half their device memory, results within
+    FP32 rounding of the two-buffer ones (the same collisions), small requests unchanged
+    bitwise, and still independent of the mix."""
+    trace = small_trace(n=8, seed=11)
+    large = 3000
+    big = [r for r in trace if r.case.params.ncells >= large]
+    assert big and len(big) < len(trace)
+    for r in big:
+        one = capi.grlb_bytes_for(serve.request_params(r, large, True))
+        two = capi.grlb_bytes_for(r.case.params)
+        assert one < 0.6 * two
+    a = serve.Server(chunk=12, large_cells=large, one_buffer_large=True, keep_fields=True).run(trace, realtime=False)
+    b = serve.Server(chunk=12, large_cells=large, keep_fields=True).run(trace, realtime=False)
+    for r, x, y in zip(trace, a, b):
+        if r.case.params.ncells < large:
+            assert x.digest == y.digest
+        else:
+            tol = 1e-6 if r.storage == inputs.STORE_F32 else 1e-2
+            assert np.all(rel_linf(x.fields, y.fields) <= tol), r.rid
+    r0 = big[0]
+    alone = serve.Server(chunk=12, large_cells=large, one_buffer_large=True).run([r0], realtime=False)[0]
+    assert alone.digest == a[trace.index(r0)].digest
