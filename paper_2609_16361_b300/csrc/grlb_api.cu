@@ -585,6 +585,11 @@ struct grlb_batch {
     int group_off[7] = {0};
     cudaGraphExec_t graph = nullptr;
     bool dirty = true;
+    // large domains step on streams of their own, forked from and joined back into `stream`,
+    // so that their launches overlap one another's tails and the table launches
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_done;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -740,6 +745,10 @@ void grlb_batch_destroy(grlb_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_doms) cudaFreeAsync(b->d_doms, b->stream);
     if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
+    // pending work on the side streams completes before their resources are released
+    for (cudaStream_t s : b->aux) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->aux_done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaGetLastError();
     delete b;
 }
@@ -775,22 +784,51 @@ grlb_status grlb_batch_set_tile_x(grlb_batch* b, const int* tile_x) {
     return rebuild_tiles(b);
 }
 
+static grlb_status batch_table_steps(grlb_batch* b, int nsteps);
+
 grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
     if (!b) return fail(GRLB_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return GRLB_OK;
-    // large domains: the single-domain sweep, one launch per step (bitwise = grlb_step)
-    for (size_t i = 0; i < b->doms.size(); ++i) {
-        if (!b->active[i] || !b->solo[i]) continue;
-        grlb_domain* d = b->doms[i];
-        cudaStream_t keep = d->stream;
-        d->stream = b->stream;
-        grlb_status st = GRLB_OK;
-        for (int n = 0; n < nsteps && st == GRLB_OK; ++n) st = sweep_once(d, false);
-        d->stream = keep;
-        if (st != GRLB_OK) return st;
+    // large domains: the single-domain sweep, one launch per step (bitwise = grlb_step), each
+    // domain on its own stream forked from the batch stream
+    int nsolo = 0;
+    for (size_t i = 0; i < b->doms.size(); ++i) nsolo += (b->active[i] && b->solo[i]) ? 1 : 0;
+    if (nsolo > 0) {
+        if (!b->fork) GRLB_CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        while ((int)b->aux.size() < nsolo) {
+            cudaStream_t s;
+            cudaEvent_t ev;
+            GRLB_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            b->aux.push_back(s);
+            GRLB_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            b->aux_done.push_back(ev);
+        }
+        GRLB_CU(cudaEventRecord(b->fork, b->stream));
+        int k = 0;
+        for (size_t i = 0; i < b->doms.size(); ++i) {
+            if (!b->active[i] || !b->solo[i]) continue;
+            grlb_domain* d = b->doms[i];
+            GRLB_CU(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+            cudaStream_t keep = d->stream;
+            d->stream = b->aux[k];
+            grlb_status st = GRLB_OK;
+            for (int n = 0; n < nsteps && st == GRLB_OK; ++n) st = sweep_once(d, false);
+            d->stream = keep;
+            if (st != GRLB_OK) return st;
+            GRLB_CU(cudaEventRecord(b->aux_done[k], b->aux[k]));
+            ++k;
+        }
     }
-    if (b->ntiles == 0) return GRLB_OK;
+    grlb_status tst = GRLB_OK;
+    if (b->ntiles > 0) tst = batch_table_steps(b, nsteps);
+    for (int k = 0; k < nsolo; ++k) GRLB_CU(cudaStreamWaitEvent(b->stream, b->aux_done[k], 0));
+    return tst;
+}
+
+// The small domains' part of grlb_batch_step: nsteps launches of the batched sweep over the
+// tile table (pairs of steps replayed from a CUDA graph).
+static grlb_status batch_table_steps(grlb_batch* b, int nsteps) {
     for (size_t i = 0; i < b->doms.size(); ++i) {
         b->h_doms[i] = b->doms[i]->D;
         b->h_doms[i].tile_x = tile_width(b, i);
@@ -912,8 +950,6 @@ int64_t shell_of_host(int64_t M) {
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-int lgs_of(int e) { return e > 1 ? ilog2_exact(e) : 0; }
 
 }  // namespace
 
