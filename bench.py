@@ -744,6 +744,65 @@ def run_slabs(args):
     return 0
 
 
+def run_cases(args):
+    """Sweep throughput per input kind (FP32, one GPU, CUDA events after warm-up): the Sod tube
+    (400 x 1 x 1, 1000 steps) and a Becker tube (2048 x 4 x 4, 1000 steps) of the paper's
+    sizes, which are too small to fill the device and are reported per step as well; the same
+    tube physics at the Taylor-Green cell count (Sod 262144 x 8 x 8 with the transverse fields
+    replicated, Becker 262144 x 8 x 8, M 3; 200 sweeps each); and the supersonic Taylor-Green
+    vortex at 256^3 (200 sweeps)."""
+    import numpy as np
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    peak, src = measured_peaks()
+
+    def widen(case, ny, nz):
+        prm = case.params.replace(ny=ny, nz=nz)
+        rep = ny * nz
+        return inputs.Case(prm, np.tile(case.rho, rep), np.stack([np.tile(case.u[k], rep) for k in range(3)]),
+                           np.tile(case.p, rep), case.meta)
+
+    big_sod_steps = 200
+    om = inputs.becker_tied_omega(8.0)  # the dt-tied relaxation at 8 cells per front
+    cases = {
+        "sod_400x1x1": (inputs.sod(400), 1000),
+        "becker_2048x4x4_M3": (inputs.becker(2048, mach=3.0, ny=4, nz=4, cfl_max=0.1, omega=om), 1000),
+        "sod_262144x8x8": (widen(inputs.sod(262144, steps=big_sod_steps, t_end=0.08 * big_sod_steps / 262144), 8, 8),
+                           big_sod_steps),
+        "becker_262144x8x8_M3": (inputs.becker(262144, mach=3.0, ny=8, nz=8, cfl_max=0.1, omega=om), 200),
+        "tgv_256^3": (inputs.tgv3d(args.n), 200),
+    }
+    out = {}
+    for name, (c, sweeps) in cases.items():
+        d = capi.Domain(c.params, stream=stream.cuda_stream)
+        d.init(c.rho, c.u, c.p)
+        d.step(10)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / sweeps
+        N = c.params.ncells
+        gbs = BYTES_PER_LUP[0] * N / (ms / 1e3) / 1e9
+        d.step_diag()
+        g = d.diag()
+        out[name] = {"cells": N, "sweeps": sweeps, "us_per_sweep": 1e3 * ms, "mlups": N / (ms / 1e3) / 1e6,
+                     "achieved_gbs": gbs, "roofline_frac": gbs / peak, "n_nan": g["n_nan"]}
+        d.close()
+    line = {"metric": "sweep MLUP/s per input kind (FP32)", "value": out["becker_262144x8x8_M3"]["mlups"],
+            "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Sod / Becker tubes at the paper's sizes and at 16.8 M cells; Taylor-Green "
+                                   f"{args.n}^3", "peak_gbs": peak, "peak_source": src},
+            "cases": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_capacity(args):
     """Largest grids on one device: the Taylor-Green workload with one population buffer (AA
     pattern) at 1024^3 in FP16 (75 GB of populations) and 768^3 in FP32 (63 GB) -- the paper runs
@@ -812,7 +871,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
-                             "capacity", "spectral", "slabs"])
+                             "capacity", "spectral", "slabs", "cases"])
     ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=40)
@@ -835,6 +894,8 @@ def main():
         return run_spectral(args)
     if args.workload == "slabs":
         return run_slabs(args)
+    if args.workload == "cases":
+        return run_cases(args)
     if args.workload == "capacity":
         return run_capacity(args)
     return run_ours(args)
