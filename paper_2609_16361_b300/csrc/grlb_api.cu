@@ -92,6 +92,10 @@ struct grlb_domain {
     cudaEvent_t staged[2] = {nullptr, nullptr};
     int stage_head = 0, stage_count = 0;
     int ce_init = 0;  // grlb_set_init_mode
+    // grlb_step replays kStepGraphSweeps plain sweeps from a CUDA graph on small domains; the
+    // graph starts from buffer graph_cur at step parity graph_parity
+    cudaGraphExec_t step_graph = nullptr;
+    int graph_cur = 0, graph_parity = 0;
 };
 
 extern "C" {
@@ -296,6 +300,7 @@ void grlb_destroy(grlb_domain* d) {
         if (d->staged[i]) cudaEventDestroy(d->staged[i]);
     }
     if (d->copy_stream) cudaStreamDestroy(d->copy_stream);
+    if (d->step_graph) cudaGraphExecDestroy(d->step_graph);
     cudaGetLastError();
     delete d;
 }
@@ -427,13 +432,75 @@ grlb_status grlb_set_source_device(grlb_domain* d, const float* S) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     if (S && d->P.streaming) return fail(GRLB_EINVAL, "a source needs two-buffer streaming (streaming = 0)");
     d->D.src = S;
+    if (d->step_graph) {  // the captured sweeps carry the old source pointer
+        cudaGraphExecDestroy(d->step_graph);
+        d->step_graph = nullptr;
+    }
+    return GRLB_OK;
+}
+
+// A small domain's sweep is shorter than a kernel launch (a 400-cell tube: ~4 us per sweep,
+// all of it launch latency), so grlb_step replays its sweeps from a CUDA graph of
+// kStepGraphSweeps launches.  The count is even, so a replay returns to the buffer (and step
+// parity) it started from; the graph is captured once, on the domain's stream, and used
+// whenever the domain is at that buffer and parity.  Not used on the legacy default stream,
+// while the caller is capturing the stream, for domains above kStepGraphMaxCells cells (there
+// the launch latency is negligible), or for fewer than 2 kStepGraphSweeps steps.
+constexpr int kStepGraphSweeps = 8;
+constexpr int64_t kStepGraphMaxCells = (int64_t)1 << 22;
+
+static grlb_status capture_step_graph(grlb_domain* d) {
+    const int cur = d->D.cur;
+    const int64_t steps = d->steps;
+    cudaGraph_t g = nullptr;
+    GRLB_CU(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+    grlb_status st = GRLB_OK;
+    for (int n = 0; n < kStepGraphSweeps && st == GRLB_OK; ++n) st = sweep_once(d, false);
+    cudaError_t e = cudaStreamEndCapture(d->stream, &g);
+    d->D.cur = cur;  // nothing ran yet: the captured sweeps run at each replay
+    d->steps = steps;
+    if (st != GRLB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (step graph)");
+    e = cudaGraphInstantiate(&d->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        d->step_graph = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate (step graph)");
+    }
+    d->graph_cur = cur;
+    d->graph_parity = (int)(steps & 1);
     return GRLB_OK;
 }
 
 grlb_status grlb_step(grlb_domain* d, int nsteps) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
-    for (int n = 0; n < nsteps; ++n) {
+    int n = 0;
+    if (d->stream && nsteps >= 2 * kStepGraphSweeps && d->D.plane <= kStepGraphMaxCells) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(d->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            if (!d->step_graph) {
+                grlb_status st = capture_step_graph(d);
+                if (st != GRLB_OK) return st;
+            }
+            // one plain sweep aligns the buffer and parity with the graph's start
+            if (d->D.cur != d->graph_cur || (int)(d->steps & 1) != d->graph_parity) {
+                grlb_status st = sweep_once(d, false);
+                if (st != GRLB_OK) return st;
+                ++n;
+            }
+            if (d->D.cur == d->graph_cur && (int)(d->steps & 1) == d->graph_parity) {
+                for (; n + kStepGraphSweeps <= nsteps; n += kStepGraphSweeps) {
+                    GRLB_CU(cudaGraphLaunch(d->step_graph, d->stream));
+                    d->steps += kStepGraphSweeps;
+                }
+            }
+        }
+    }
+    for (; n < nsteps; ++n) {
         grlb_status st = sweep_once(d, false);
         if (st != GRLB_OK) return st;
     }
