@@ -505,7 +505,8 @@ cudaError_t k1_t(const DomainDev& D, const void* fin, int gather, SpectralPlan& 
     auto kern = spectral_k1_kernel<S, LG>;
     cudaError_t e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    P.grid1 = resident_grid(kern, threads, smem, (P.N >> LG) / L);
+    // never above the plan's bound, which sized the caller's partial-sum buffer
+    P.grid1 = std::min(P.grid1, resident_grid(kern, threads, smem, (P.N >> LG) / L));
     kern<<<P.grid1, threads, smem, st>>>(D, fin, gather, P, tw, U, mu, partials);
     return cudaGetLastError();
 }
@@ -525,7 +526,7 @@ cudaError_t rest_t(SpectralPlan& P, const float2* tw, float2* U, const float* mu
     constexpr int L = Groups<LG>::L1;
     const size_t smem3 = 4 * L * line_bytes<LG>() + (size_t)P.nbins * sizeof(unsigned long long);
     if ((e = allow_smem(spectral_k3_kernel<LG>, smem3)) != cudaSuccess) return e;
-    P.grid3 = resident_grid(spectral_k3_kernel<LG>, 256, smem3, (P.N >> LG) / L);
+    P.grid3 = std::min(P.grid3, resident_grid(spectral_k3_kernel<LG>, 256, smem3, (P.N >> LG) / L));
     spectral_k3_kernel<LG><<<P.grid3, 256, smem3, st>>>(U, P, tw, bins);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (cube) {
@@ -535,7 +536,7 @@ cudaError_t rest_t(SpectralPlan& P, const float2* tw, float2* U, const float* mu
     }
     const size_t smem5 = 4 * L * line_bytes<LG>();
     if ((e = allow_smem(spectral_k5_kernel<LG>, smem5)) != cudaSuccess) return e;
-    P.grid5 = resident_grid(spectral_k5_kernel<LG>, 256, smem5, (P.N >> LG) / L);
+    P.grid5 = std::min(P.grid5, resident_grid(spectral_k5_kernel<LG>, 256, smem5, (P.N >> LG) / L));
     spectral_k5_kernel<LG><<<P.grid5, 256, smem5, st>>>(U, mu, P, tw, partials);
     return cudaGetLastError();
 }
