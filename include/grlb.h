@@ -35,8 +35,9 @@ typedef enum {
     GRLB_EINVAL = -1,   /* bad argument (null pointer, size, enum, parameter range)      */
     GRLB_ENOMEM = -2,   /* device or host allocation failed                              */
     GRLB_ECUDA = -3,    /* a CUDA runtime call failed; message carries cudaGetErrorString */
-    GRLB_ENUMERIC = -4, /* non-finite or non-positive state detected                     */
-    GRLB_ETIMEOUT = -5, /* a bounded device wait ran out                                 */
+    GRLB_ENUMERIC = -4, /* reserved: no call returns it; a non-finite state shows as
+                           grlb_diag.n_nan > 0 after a diagnostic sweep                  */
+    GRLB_ETIMEOUT = -5, /* reserved: no kernel of the library waits on another           */
     GRLB_ESTATE = -6    /* call not valid in the object's current state                  */
 } grlb_status;
 
