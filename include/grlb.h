@@ -100,8 +100,9 @@ const char* grlb_last_error(void);
 /* Library version string. */
 const char* grlb_version(void);
 
-/* Create a domain: validates p, allocates two population buffers (35 planes each, storage
- * type per p->storage) and the diagnostic scratch on the current CUDA device.  stream is a
+/* Create a domain: validates p, allocates two population buffers (storage type per
+ * p->storage, in the cell-brick layout below) and the diagnostic scratch on the current CUDA
+ * device.  stream is a
  * cudaStream_t (may be NULL).  On success *out owns the memory; free with grlb_destroy. */
 grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out);
 void grlb_destroy(grlb_domain* d);
@@ -164,7 +165,15 @@ grlb_status grlb_read_primitive(grlb_domain* d, double* rho, double* u, double* 
 
 /* Raw checkpoint: stored populations + step counter.  grlb_save with buf == NULL sets
  * *bytes to the size needed; otherwise *bytes must be at least that size.  grlb_load
- * requires a buffer written by grlb_save of a domain with the same params. */
+ * requires a buffer written by grlb_save of a domain with the same params.
+ * Format: a 32-byte header, then the population buffer as the library keeps it in device
+ * memory -- the cell-brick layout: cells in storage order (x fastest) are grouped into
+ * ceil(N / 128) bricks of 128 cells; a brick holds its 35 population rows q = 7k + i (field k
+ * = rho, m_x, m_y, m_z, E; link i = 0, +x, -x, +y, -y, +z, -z) one after the other, 128
+ * elements each, so population q of cell c is element (c / 128) 4480 + 128 q + c % 128 (the
+ * cells past N in the last brick hold zeros).  Elements are the storage type's deviations
+ * from the reference equilibrium (FP16: times a per-field power of two), followed, for a
+ * one-buffer X_DIRICHLET_EQ domain, by its outflow record. */
 grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes);
 grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes);
 int64_t grlb_steps_done(const grlb_domain* d);
@@ -216,9 +225,9 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
  * allocating routine.
  *
  *  p        domain description (as for grlb_create); validated on the host.
- *  f_in     device pointer, current populations: 35 planes of N elements of the storage
- *           type, the layout and equilibrium-shift format of the library's own buffers (the
- *           bytes grlb_save writes after its 32-byte header).
+ *  f_in     device pointer, current populations: 4480 ceil(N / 128) elements of the storage
+ *           type in the cell-brick layout and equilibrium-shift format of the library's own
+ *           buffers (the bytes grlb_save writes after its 32-byte header).
  *  f_out    device pointer, same size, receives the populations one step later; must not
  *           overlap f_in.
  *  diag_out device pointer to GRLB_NDIAG doubles: sums over cells of (Q_k - Q_ref,k) for

@@ -37,6 +37,8 @@ grlb_status cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 size_t elem_bytes(int storage) { return storage == GRLB_STORE_F32 ? 4 : 2; }
+// one population buffer: N cells in cell bricks (whole bricks of 35 x 128 elements)
+size_t pop_bytes(size_t N, int storage) { return (size_t)grlb::brick_elems((int64_t)N) * elem_bytes(storage); }
 
 // One-buffer Dirichlet domains keep the populations that leave through the ends in an odd step.
 size_t outflow_bytes(const grlb_params& p) {
@@ -196,6 +198,11 @@ static void fill_domain_dev(grlb_domain* d) {
     for (int k = 0; k < 5; ++k) {
         D.enc[k] = storage_scale(p.storage, M[k]);
         D.dec[k] = 1.0f / D.enc[k];
+        D.enc_q0[k] = 0.25f * D.enc[k];
+        D.enc_q1[k] = 0.125f * D.enc[k];
+        D.enc_j[k] = 0.5f * D.enc[k];
+        D.ghostL_st[k] = D.ghostL[k] * D.enc[k];
+        D.ghostR_st[k] = D.ghostR[k] * D.enc[k];
     }
     D.src = nullptr;
     D.outflow = nullptr;
@@ -242,7 +249,7 @@ size_t grlb_bytes_for(const grlb_params* p) {
     choose_launch(&tmp);
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     const size_t nbuf = p->streaming ? 1 : 2;
-    return nbuf * 35 * N * elem_bytes(p->storage) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+    return nbuf * pop_bytes(N, p->storage) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
            NDIAG * 8 + outflow_bytes(*p);
 }
 
@@ -259,16 +266,21 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     fill_domain_dev(d);
     choose_launch(d);
     const size_t N = (size_t)d->D.plane;
-    const size_t pop_bytes = 35 * N * elem_bytes(p->storage);
+    const size_t pb = pop_bytes(N, p->storage);
     retain_pool();
     cudaStream_t s = d->stream;
     cudaError_t e = cudaSuccess;
     d->D.buf[0] = d->D.buf[1] = nullptr;
-    e = cudaMallocAsync(&d->D.buf[0], pop_bytes, s);
+    e = cudaMallocAsync(&d->D.buf[0], pb, s);
     if (e == cudaSuccess) {
         if (p->streaming) d->D.buf[1] = d->D.buf[0];  // one buffer, updated in place
-        else e = cudaMallocAsync(&d->D.buf[1], pop_bytes, s);
+        else e = cudaMallocAsync(&d->D.buf[1], pb, s);
     }
+    // the last brick's cells past N are never written by a kernel: zero them once so that
+    // checkpoints of equal states are equal bytes
+    const size_t tail = grlb::NP * grlb::kBrick * elem_bytes(p->storage);
+    for (int b = 0; b < (p->streaming ? 1 : 2) && e == cudaSuccess; ++b)
+        e = cudaMemsetAsync(static_cast<char*>(d->D.buf[b]) + pb - tail, 0, tail, s);
     if (e == cudaSuccess && p->streaming && p->bc == GRLB_BC_X_DIRICHLET_EQ)
         e = cudaMallocAsync(&d->D.outflow, outflow_bytes(*p), s);
     if (e == cudaSuccess)
@@ -280,7 +292,7 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
         return fail(e == cudaErrorMemoryAllocation ? GRLB_ENOMEM : GRLB_ECUDA,
                     std::string("grlb_create: ") + cudaGetErrorString(e));
     }
-    d->bytes = (p->streaming ? 1 : 2) * pop_bytes + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+    d->bytes = (p->streaming ? 1 : 2) * pb + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
                NDIAG * 8 + outflow_bytes(*p);
     *out = d;
     return GRLB_OK;
@@ -586,12 +598,12 @@ struct SaveHeader {
     int64_t N;
     int32_t storage, pad;
 };
-const uint64_t kMagic = 0x3142524c47ULL;  // "GLRB1"
+const uint64_t kMagic = 0x3242524c47ULL;  // "GLRB2": cell-brick population layout
 }  // namespace
 
 grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
     if (!d || !bytes) return fail(GRLB_EINVAL, "grlb_save: NULL argument");
-    const size_t pop = 35 * (size_t)d->D.plane * elem_bytes(d->P.storage);
+    const size_t pop = pop_bytes((size_t)d->D.plane, d->P.storage);
     const size_t ob = outflow_bytes(d->P);
     const size_t need = sizeof(SaveHeader) + pop + ob;
     if (!buf) {
@@ -613,7 +625,7 @@ grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
 
 grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
     if (!d || !buf) return fail(GRLB_EINVAL, "grlb_load: NULL argument");
-    const size_t pop = 35 * (size_t)d->D.plane * elem_bytes(d->P.storage);
+    const size_t pop = pop_bytes((size_t)d->D.plane, d->P.storage);
     const size_t ob = outflow_bytes(d->P);
     if (bytes < sizeof(SaveHeader) + pop + ob) return fail(GRLB_EINVAL, "grlb_load: buffer too small");
     SaveHeader h;
@@ -1130,8 +1142,8 @@ extern "C" grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upp
     if (a.nz < 3 || b.nz < 3) return fail(GRLB_EINVAL, "grlb_halo_exchange_z: a slab needs nz >= 3 (2 ghost planes)");
     if (lower->stream != upper->stream)
         return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs must share one stream");
-    GRLB_CU(grlb::launch_halo_z(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], lower->D.plane,
-                                upper->D.plane, a.nz, (int64_t)a.nx * a.ny, elem_bytes(a.storage), lower->stream));
+    GRLB_CU(grlb::launch_halo_z(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], a.nz, (int64_t)a.nx * a.ny,
+                                elem_bytes(a.storage), lower->stream));
     return GRLB_OK;
 }
 

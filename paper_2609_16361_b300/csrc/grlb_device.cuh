@@ -29,14 +29,37 @@ constexpr int NDIAG = 13;  // per-block partial record of the diagnostic sweep
 // the first finalize stage.
 constexpr int kDiagStageRecords = 256;
 
+// Population layout in HBM: cell bricks.  Cells are grouped in storage order (x fastest) into
+// bricks of kBrick consecutive cells; a brick holds its 35 population rows q = 7k + i one after
+// the other, kBrick elements each, so population q of cell c is element
+//     brick_at(c) + q * kBrick,   brick_at(c) = (c / kBrick) * 35 kBrick + c % kBrick.
+// A warp of consecutive cells reads and writes whole contiguous row segments (as in 35 separate
+// planes), while the 35 populations of one cell lie within 35 kBrick elements of one base
+// address: a sweep forms 7 addresses per cell (its own and the 6 pull sources) and reaches
+// the 35 populations by constant offsets, instead of forming 35 + 35 64-bit addresses.  A
+// buffer holds ceil(N / kBrick) bricks; the cells past N in the last brick are never updated.
+constexpr int kBrick = 128;
+__host__ __device__ __forceinline__ int64_t brick_at(int64_t c) {  // c >= 0
+    const uint64_t u = (uint64_t)c;
+    return (int64_t)((u / kBrick) * (uint64_t)(NP * kBrick) + (u % kBrick));
+}
+__device__ __forceinline__ int64_t brick_at_u32(uint32_t c) {
+    return (int64_t)(c >> 7) * (NP * kBrick) + (c & (kBrick - 1));
+}
+// elements of one population buffer for N cells
+__host__ __device__ __forceinline__ int64_t brick_elems(int64_t N) {
+    return (N + kBrick - 1) / kBrick * (int64_t)(NP * kBrick);
+}
+static_assert(kBrick == 128, "brick_at_u32 shifts by log2(kBrick)");
+
 enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
 enum Collision { C_BGK = 0, C_RLB = 1 };
 
 // Per-domain lattice-unit constants.  Plain old data: passed by value as a kernel
 // parameter for single-domain launches, read from a device array by the batched sweep.
 struct DomainDev {
-    void* buf[2];          // population buffers A, B (35 planes each)
-    int64_t plane;         // elements per population plane = nx*ny*nz
+    void* buf[2];          // population buffers A, B (cell bricks, brick_elems(N) elements each)
+    int64_t plane;         // cells N = nx*ny*nz
     int32_t nx, ny, nz, bc;
     int32_t cur;           // index of the buffer holding the current state (batched sweep)
     int32_t tile_x;        // cells along x per CTA in the batched sweep (divides blockDim.x);
@@ -52,7 +75,11 @@ struct DomainDev {
     float ghostL[5];       // deviation of f_{k,+x} in the x = -1 ghost (X_DIRICHLET_EQ)
     float ghostR[5];       // deviation of f_{k,-x} in the x = nx ghost
     float dec[5];          // per-field storage scale: value = stored * dec[k]
-    float enc[5];          // stored = value * enc[k]
+    float enc[5];          // stored = value * enc[k] (a power of two)
+    float enc_q0[5], enc_q1[5], enc_j[5];  // w_0 enc[k], w_1 enc[k], enc[k] / 2: the scale
+                                           // folded into the constants of the outgoing set
+    float ghostL_st[5];    // ghostL[k] enc[k], ghostR[k] enc[k]: the ghost values in stored units
+    float ghostR_st[5];
     void* outflow;         // one-buffer X_DIRICHLET_EQ: populations leaving through x = -1 / nx in
                            // an odd step, [side][k][y + ny z] (side 0: -x at x = 0, 1: +x at nx-1)
     const float* src;      // optional source S_k (5 planes, physical rates), or null
@@ -313,19 +340,22 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
             const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
             const float omh = D.omega[r] - chi * D.omega_red[r];
             const float onem = 1.0f - omh;
-            const float sc = SC ? D.enc[k] : 1.0f;
+            // storage scale (a power of two) folded into w_i and 1/2: every product is exact,
+            // so the stored values equal those of scaling the outgoing set afterwards
+            const float cq0 = SC ? D.enc_q0[k] : 0.25f;
+            const float cq1 = SC ? D.enc_q1[k] : 0.125f;
+            const float cj = SC ? D.enc_j[k] : 0.5f;
             float js[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) js[c] = (Pd[k][c] + onem * (nA[k][c] - Fd[k][c])) * sc;
-            const float q0 = 0.25f * dQ[k] * sc;
-            const float q1 = 0.125f * dQ[k] * sc;
-            o[k][0] = q0;
-            o[k][1] = q1 + 0.5f * js[0];
-            o[k][2] = q1 - 0.5f * js[0];
-            o[k][3] = q1 + 0.5f * js[1];
-            o[k][4] = q1 - 0.5f * js[1];
-            o[k][5] = q1 + 0.5f * js[2];
-            o[k][6] = q1 - 0.5f * js[2];
+            for (int c = 0; c < 3; ++c) js[c] = Pd[k][c] + onem * (nA[k][c] - Fd[k][c]);
+            const float q1 = dQ[k] * cq1;
+            o[k][0] = dQ[k] * cq0;
+            o[k][1] = fmaf(cj, js[0], q1);
+            o[k][2] = fmaf(-cj, js[0], q1);
+            o[k][3] = fmaf(cj, js[1], q1);
+            o[k][4] = fmaf(-cj, js[1], q1);
+            o[k][5] = fmaf(cj, js[2], q1);
+            o[k][6] = fmaf(-cj, js[2], q1);
         }
     } else {
         // BGK (Sec. 2.2): f* = f + omega (f^eq - f)

@@ -16,34 +16,32 @@
 namespace grlb {
 
 template <typename T>
-__global__ void __launch_bounds__(256) halo_z_kernel(T* __restrict__ lower, T* __restrict__ upper, int64_t plane_lo,
-                                                     int64_t plane_up, int nzl, int64_t nxy) {
+__global__ void __launch_bounds__(256) halo_z_kernel(T* __restrict__ lower, T* __restrict__ upper, int nzl,
+                                                     int64_t nxy) {
     // slices: s < 5: +z of field s, lower top interior (z = nzl - 2) -> upper ghost (z = 0);
     //         s >= 5: -z of field s - 5, upper bottom interior (z = 1) -> lower ghost (z = nzl - 1)
+    // (cell bricks: population q of cell c at brick_at(c) + q kBrick)
     const int s = blockIdx.y;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
         if (s < 5) {
-            const int q = 7 * s + 5;
-            upper[q * plane_up + c] = lower[q * plane_lo + (int64_t)(nzl - 2) * nxy + c];
+            const int64_t q = (7 * s + 5) * kBrick;
+            upper[brick_at(c) + q] = lower[brick_at((int64_t)(nzl - 2) * nxy + c) + q];
         } else {
-            const int q = 7 * (s - 5) + 6;
-            lower[q * plane_lo + (int64_t)(nzl - 1) * nxy + c] = upper[q * plane_up + nxy + c];
+            const int64_t q = (7 * (s - 5) + 6) * kBrick;
+            lower[brick_at((int64_t)(nzl - 1) * nxy + c) + q] = upper[brick_at(nxy + c) + q];
         }
     }
 }
 
-cudaError_t launch_halo_z(void* lower, void* upper, int64_t plane_lo, int64_t plane_up, int nzl, int64_t nxy,
-                          size_t elem, cudaStream_t st) {
+cudaError_t launch_halo_z(void* lower, void* upper, int nzl, int64_t nxy, size_t elem, cudaStream_t st) {
     int64_t blocks = (nxy + 255) / 256;
     if (blocks > 148 * 4) blocks = 148 * 4;
     const dim3 grid((unsigned)blocks, 10);
     if (elem == 4)
-        halo_z_kernel<float><<<grid, 256, 0, st>>>(static_cast<float*>(lower), static_cast<float*>(upper), plane_lo,
-                                                   plane_up, nzl, nxy);
+        halo_z_kernel<float><<<grid, 256, 0, st>>>(static_cast<float*>(lower), static_cast<float*>(upper), nzl, nxy);
     else
         halo_z_kernel<unsigned short><<<grid, 256, 0, st>>>(static_cast<unsigned short*>(lower),
-                                                            static_cast<unsigned short*>(upper), plane_lo, plane_up,
-                                                            nzl, nxy);
+                                                            static_cast<unsigned short*>(upper), nzl, nxy);
     return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
 #pragma unroll
             for (int i = 0; i < NQ; ++i) {
                 const int slot = swap ? (i == 0 ? 0 : (i & 1 ? i + 1 : i - 1)) : i;
-                Store<S>::st(fout + (int64_t)(7 * k + slot) * N + c, v[i] * sc);
+                Store<S>::st(fout + brick_at(c) + (7 * k + slot) * kBrick, v[i] * sc);
             }
         }
     }

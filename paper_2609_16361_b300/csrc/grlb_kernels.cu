@@ -1,12 +1,14 @@
 // grlb_kernels.cu -- sweep, initialisation, readback and diagnostic-reduction kernels.
 //
-// Layout in HBM (per domain, per buffer): 35 planes of N = nx*ny*nz elements, plane index
-// q = 7k + i (field k, link i), x fastest inside a plane.  One CTA covers a tile of
-// blockDim.x consecutive cells of blockDim.y rows at one z; consecutive lanes touch
-// consecutive addresses of every plane, so each of the 35 loads and 35 stores of a warp is a
-// fully used 128-byte line (FP32).  The +-y / +-z pulls read whole neighbouring rows; the +-x
-// pulls are the same row shifted by one element, served from L1/L2 lines already fetched for
-// the row (no extra DRAM traffic).
+// Layout in HBM (per domain, per buffer): cell bricks (grlb_device.cuh) -- 128 consecutive
+// cells in storage order (x fastest) keep their 35 population rows q = 7k + i (field k, link i)
+// together, 128 elements each.  One CTA covers a tile of blockDim.x consecutive cells of
+// blockDim.y rows at one z (or 128 consecutive cells); consecutive lanes touch consecutive
+// elements of every population row, so each of the 35 loads and 35 stores of a warp is a fully
+// used 128-byte line (FP32).  The +-y / +-z pulls read whole neighbouring rows; the +-x pulls
+// are the same row shifted by one element, served from L1/L2 lines already fetched for the row
+// (no extra DRAM traffic).  A thread forms one 64-bit address per pull source and reaches the
+// five fields' populations of that source by constant offsets q * 128.
 #include <cuda_runtime.h>
 
 #include "grlb_device.cuh"
@@ -62,75 +64,98 @@ __device__ __forceinline__ float ld_pop(const typename Store<S>::T* p) {
     return Store<S>::ld_plain(p);             // in place: plain (coherent) load
 }
 
+// Element offsets (cell bricks) of population row 0 of the cell and of its 6 pull sources.
+struct PullAt {
+    int64_t c, xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ PullAt pull_at(const PullIdx& P) {
+    PullAt A;
+    A.c = brick_at_u32((uint32_t)P.c);
+    A.xm = brick_at_u32((uint32_t)P.xm);
+    A.xp = brick_at_u32((uint32_t)P.xp);
+    A.ym = brick_at_u32((uint32_t)P.ym);
+    A.yp = brick_at_u32((uint32_t)P.yp);
+    A.zm = brick_at_u32((uint32_t)P.zm);
+    A.zp = brick_at_u32((uint32_t)P.zp);
+    return A;
+}
+
 template <int S, int PAT>
 __device__ __forceinline__ void load_cell(const DomainDev& D, const typename Store<S>::T* fin,
-                                          const PullIdx& P, float (&d)[NF][NQ]) {
+                                          const PullIdx& P, const PullAt& A, float (&d)[NF][NQ]) {
     using St = Store<S>;
-    const int64_t pl = D.plane;
+    using T = typename St::T;
+    const T* bc = fin + A.c;
+    const T* bxm = fin + A.xm;
+    const T* bxp = fin + A.xp;
+    const T* bym = fin + A.ym;
+    const T* byp = fin + A.yp;
+    const T* bzm = fin + A.zm;
+    const T* bzp = fin + A.zp;
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        const typename St::T* b = fin + (int64_t)(7 * k) * pl;
-        // stored units: ghosts (physical deviations) take the storage scale
-        const float gl = St::scaled ? D.ghostL[k] * D.enc[k] : D.ghostL[k];
-        const float gr = St::scaled ? D.ghostR[k] * D.enc[k] : D.ghostR[k];
+        const int q = 7 * k * kBrick;
+        const float gl = D.ghostL_st[k], gr = D.ghostR_st[k];  // stored units
         if (PAT == AA_EVEN) {
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) d[k][i] = ld_pop<S, PAT>(b + i * pl + P.c);
+            for (int i = 0; i < NQ; ++i) d[k][i] = ld_pop<S, PAT>(bc + q + i * kBrick);
         } else {
-            // PULL reads plane i of the neighbour; AA_ODD reads plane opp(i) of it
+            // PULL reads row i of the neighbour; AA_ODD reads row opp(i) of it
             const int o1 = PAT == PULL ? 1 : 2, o2 = PAT == PULL ? 2 : 1;
             const int o3 = PAT == PULL ? 3 : 4, o4 = PAT == PULL ? 4 : 3;
             const int o5 = PAT == PULL ? 5 : 6, o6 = PAT == PULL ? 6 : 5;
-            d[k][0] = ld_pop<S, PAT>(b + P.c);
-            d[k][1] = P.gl ? gl : ld_pop<S, PAT>(b + o1 * pl + P.xm);
-            d[k][2] = P.gr ? gr : ld_pop<S, PAT>(b + o2 * pl + P.xp);
-            d[k][3] = ld_pop<S, PAT>(b + o3 * pl + P.ym);
-            d[k][4] = ld_pop<S, PAT>(b + o4 * pl + P.yp);
-            d[k][5] = ld_pop<S, PAT>(b + o5 * pl + P.zm);
-            d[k][6] = ld_pop<S, PAT>(b + o6 * pl + P.zp);
+            d[k][0] = ld_pop<S, PAT>(bc + q);
+            d[k][1] = P.gl ? gl : ld_pop<S, PAT>(bxm + q + o1 * kBrick);
+            d[k][2] = P.gr ? gr : ld_pop<S, PAT>(bxp + q + o2 * kBrick);
+            d[k][3] = ld_pop<S, PAT>(bym + q + o3 * kBrick);
+            d[k][4] = ld_pop<S, PAT>(byp + q + o4 * kBrick);
+            d[k][5] = ld_pop<S, PAT>(bzm + q + o5 * kBrick);
+            d[k][6] = ld_pop<S, PAT>(bzp + q + o6 * kBrick);
         }
     }
 }
 
 template <int S, int PAT>
 __device__ __forceinline__ void store_cell(const DomainDev& D, typename Store<S>::T* fout,
-                                           const PullIdx& P, const float (&o)[NF][NQ]) {
+                                           const PullIdx& P, const PullAt& A, const float (&o)[NF][NQ]) {
     using St = Store<S>;
-    const int64_t pl = D.plane;
+    using T = typename St::T;
+    T* bc = fout + A.c;
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        typename St::T* b = fout + (int64_t)(7 * k) * pl;
+        const int q = 7 * k * kBrick;
         if (PAT == PULL) {
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) St::st(b + i * pl + P.c, o[k][i]);
+            for (int i = 0; i < NQ; ++i) St::st(bc + q + i * kBrick, o[k][i]);
         } else if (PAT == AA_EVEN) {
-            St::st(b + P.c, o[k][0]);
-            St::st(b + 2 * pl + P.c, o[k][1]);
-            St::st(b + 1 * pl + P.c, o[k][2]);
-            St::st(b + 4 * pl + P.c, o[k][3]);
-            St::st(b + 3 * pl + P.c, o[k][4]);
-            St::st(b + 6 * pl + P.c, o[k][5]);
-            St::st(b + 5 * pl + P.c, o[k][6]);
+            St::st(bc + q, o[k][0]);
+            St::st(bc + q + 2 * kBrick, o[k][1]);
+            St::st(bc + q + 1 * kBrick, o[k][2]);
+            St::st(bc + q + 4 * kBrick, o[k][3]);
+            St::st(bc + q + 3 * kBrick, o[k][4]);
+            St::st(bc + q + 6 * kBrick, o[k][5]);
+            St::st(bc + q + 5 * kBrick, o[k][6]);
         } else {  // AA_ODD: push to the neighbour the population streams to
-            St::st(b + P.c, o[k][0]);
+            St::st(bc + q, o[k][0]);
             const int64_t nyz = (int64_t)D.ny * D.nz;
-            typename St::T* out = static_cast<typename St::T*>(D.outflow);
+            T* out = static_cast<T*>(D.outflow);
             if (P.gr) {
-                St::st(b + 2 * pl + P.c, St::scaled ? D.ghostR[k] * D.enc[k] : D.ghostR[k]);
+                St::st(bc + q + 2 * kBrick, D.ghostR_st[k]);
                 St::st(out + (5 + k) * nyz + P.yz, o[k][1]);
             } else {
-                St::st(b + 1 * pl + P.xp, o[k][1]);
+                St::st(fout + A.xp + q + 1 * kBrick, o[k][1]);
             }
             if (P.gl) {
-                St::st(b + 1 * pl + P.c, St::scaled ? D.ghostL[k] * D.enc[k] : D.ghostL[k]);
+                St::st(bc + q + 1 * kBrick, D.ghostL_st[k]);
                 St::st(out + k * nyz + P.yz, o[k][2]);
             } else {
-                St::st(b + 2 * pl + P.xm, o[k][2]);
+                St::st(fout + A.xm + q + 2 * kBrick, o[k][2]);
             }
-            St::st(b + 3 * pl + P.yp, o[k][3]);
-            St::st(b + 4 * pl + P.ym, o[k][4]);
-            St::st(b + 5 * pl + P.zp, o[k][5]);
-            St::st(b + 6 * pl + P.zm, o[k][6]);
+            St::st(fout + A.yp + q + 3 * kBrick, o[k][3]);
+            St::st(fout + A.ym + q + 4 * kBrick, o[k][4]);
+            St::st(fout + A.zp + q + 5 * kBrick, o[k][5]);
+            St::st(fout + A.zm + q + 6 * kBrick, o[k][6]);
         }
     }
 }
@@ -215,11 +240,12 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
     CellDiag cd;
     if (active) {
         const PullIdx P = pull_index(D, x, y, z);
+        const PullAt A = pull_at(P);
         float d[NF][NQ], o[NF][NQ];
-        load_cell<S, PAT>(D, fin, P, d);
+        load_cell<S, PAT>(D, fin, P, A, d);
         collide<S, COLL, DIAG>(D, d, o, &cd);
         if (SRC) add_source<S>(D, P.c, o);
-        store_cell<S, PAT>(D, fout, P, o);
+        store_cell<S, PAT>(D, fout, P, A, o);
     }
     if (DIAG) {
         const int64_t blk = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
@@ -276,10 +302,11 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __res
             const T* __restrict__ fin = static_cast<const T*>(D.buf[c]);
             T* __restrict__ fout = static_cast<T*>(D.buf[c ^ 1]);
             const PullIdx P = pull_index(D, x, y, z);
+            const PullAt A = pull_at(P);
             float d[NF][NQ], o[NF][NQ];
-            load_cell<S, PULL>(D, fin, P, d);
+            load_cell<S, PULL>(D, fin, P, A, d);
             collide<S, COLL, false>(D, d, o, nullptr);
-            store_cell<S, PULL>(D, fout, P, o);
+            store_cell<S, PULL>(D, fout, P, A, o);
         }
     }
 }
@@ -375,7 +402,7 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
 #pragma unroll
             for (int i = 0; i < NQ; ++i) {
                 const int slot = swap ? (i == 0 ? 0 : (i & 1 ? i + 1 : i - 1)) : i;
-                Store<S>::st(fout + (int64_t)(7 * k + slot) * N + c, v[i] * sc);
+                Store<S>::st(fout + brick_at(c) + (7 * k + slot) * kBrick, v[i] * sc);
             }
         }
     }
@@ -409,7 +436,7 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
                 double v;
                 if (gather && i == 1 && P.gr) v = (double)Store<S>::ld(outflow + (5 + k) * nyz + P.yz);
                 else if (gather && i == 2 && P.gl) v = (double)Store<S>::ld(outflow + k * nyz + P.yz);
-                else v = (double)Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
+                else v = (double)Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
                 acc += v * sc;
             }
             double q = acc;

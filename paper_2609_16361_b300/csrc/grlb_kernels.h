@@ -59,8 +59,7 @@ cudaError_t launch_spectral_k2_to_k5(SpectralPlan& P, const float2* tw, float2* 
                                      unsigned long long* bins, double* partials, cudaStream_t st);
 // z-slab ghost exchange (grlb_halo.cu): lower's top interior +z slices -> upper's ghost plane
 // 0; upper's bottom interior -z slices -> lower's top ghost plane (nzl = lower's planes).
-cudaError_t launch_halo_z(void* lower, void* upper, int64_t plane_lo, int64_t plane_up, int nzl, int64_t nxy,
-                          size_t elem, cudaStream_t st);
+cudaError_t launch_halo_z(void* lower, void* upper, int nzl, int64_t nxy, size_t elem, cudaStream_t st);
 // FP32 FFMA issue-rate probe: ctas x 256 threads x iters x 128 FFMAs.
 cudaError_t launch_ffma_probe(float* sink, int ctas, int iters, cudaStream_t st);
 }  // namespace grlb

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(192, 3) spectral_k1_kernel(const DomainDev D, 
             for (int k = 0; k < NF; ++k) {
                 float acc = 0.0f;
 #pragma unroll
-                for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + (int64_t)(7 * k + i) * N + at[i]);
+                for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
                 dQ[k] = acc * D.dec[k];
             }
             const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);

@@ -2,6 +2,7 @@
 import numpy as np
 
 WI = np.array([0.25] + [0.125] * 6)
+BRICK = 128  # cells per brick of the population layout
 CI = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
 
 
@@ -32,18 +33,25 @@ def run_oracle(case, steps, keep_cells=False):
 
 
 def decode_populations(raw, prm, nplanes=35, cells=None):
-    """FP64 populations (lattice units) from a grlb_save checkpoint, all cells or `cells`.
+    """FP64 populations (lattice units) from a grlb_save checkpoint, all cells or `cells`,
+    as 35 rows q = 7k + i of one value per cell.
 
-    The documented storage format: a 32-byte header, then 35 planes of deviations
-    d = f - w_i (Q_ref + c_i . J_ref / cs^2) with Q_ref = (rho_ref, 0, 0, 0, p_ref/(g-1)),
-    J_ref of m_j = p_ref e_j (lattice units), scaled by a per-field factor for FP16."""
+    The documented storage format: a 32-byte header, then the populations in cell bricks --
+    bricks of 128 consecutive cells (storage order), each holding its 35 rows of 128 values,
+    ceil(N / 128) bricks -- of deviations d = f - w_i (Q_ref + c_i . J_ref / cs^2) with
+    Q_ref = (rho_ref, 0, 0, 0, p_ref/(g-1)), J_ref of m_j = p_ref e_j (lattice units), scaled by
+    a per-field factor for FP16."""
     N = prm.nx * prm.ny * prm.nz
     s = prm.dt / prm.dx
     dtype = {0: np.float32, 1: np.float16, 2: np.uint16}[prm.storage]
     raw = np.frombuffer(raw, np.uint8) if isinstance(raw, bytes) else raw
-    body = raw[32:].view(dtype).reshape(nplanes, N)
+    nb = (N + BRICK - 1) // BRICK
+    bricks = raw[32:32 + nb * nplanes * BRICK * np.dtype(dtype).itemsize].view(dtype).reshape(nb, nplanes, BRICK)
     if cells is not None:
-        body = body[:, cells]
+        cells = np.asarray(cells)
+        body = bricks[cells // BRICK, :, cells % BRICK].T
+    else:
+        body = bricks.transpose(1, 0, 2).reshape(nplanes, nb * BRICK)[:, :N]
     if prm.storage == 2:
         d = (body.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     else:
