@@ -46,7 +46,7 @@ __device__ __forceinline__ PullIdx pull_index(const DomainDev& D, int x, int y, 
 }
 
 // ---- population access patterns ----------------------------------------------------------
-// PULL: two buffers; read f_i(x - c_i) from the input, write f*_i(x) to the output (plane i).
+// PULL: two buffers; read f_i(x - c_i) from the input, write f*_i(x) to the output (row i).
 // AA (one buffer, in place, alternating):
 //   AA_ODD : read f*_i(x - c_i) from slot opp(i) of the neighbour x - c_i, collide, write
 //            f*_i(x) to slot i of the neighbour x + c_i (the streamed population arrives there);
