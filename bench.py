@@ -66,11 +66,16 @@ def job_mlups(ws, cells_per_rank, sweeps, seconds):
     return ws * cells_per_rank * sweeps / seconds / 1e6
 
 
-def kernel_source_sha():
+def kernel_source_sha(sources=None):
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES if sources is None else sources:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
+
+
+# the spectral post-processing's five kernels and the sweep header they include
+SPECTRAL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh",
+                    "paper_2609_16361_b300/csrc/grlb_spectral.cu"]
 
 
 def measured_peaks():
@@ -678,13 +683,19 @@ def run_spectral(args):
     peak, src = measured_peaks()
     bpc = 372
     ach = bpc * N / (ms / 1e3) / 1e9
+    # DRAM bytes of the five kernels of one call (ncu), while the kernel source is unchanged
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        rec = json.load(open(TRAFFIC_FILE)).get(f"spectral_tgv{n}_f32")
+        if rec and rec.get("source_sha") == kernel_source_sha(SPECTRAL_SOURCES):
+            traffic = rec.get("dram_bytes_per_call")
     line = {"metric": "spectral diagnostics time per call", "value": ms, "unit": "ms",
             "n_gpus": 1, "higher_is_better": False, "dtype": "f32 (FFT), f64 (sums)",
             "data": "synthetic",
             "config": {"workload": f"tgv{n}_f32 state after 50 steps", "grid": [n, n, n],
                        "shells": len(spec)},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "traffic": None, "bytes_per_call": bpc * N,
+                         "frac": ach / peak, "traffic": traffic, "bytes_per_call": bpc * N,
                          "peak_source": f"{src} hbm_gbs",
                          "note": "whole call, including its two host synchronisations"},
             "share_of_50_step_step": ms / step_ms,
