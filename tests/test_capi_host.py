@@ -69,6 +69,20 @@ def test_parameter_validation_without_device():
     assert st == -1 and b"nx" in capi.lib().grlb_last_error()
 
 
+@pytest.mark.parametrize("shape", [(32, 32, 32), (10, 7, 3), (129, 1, 1), (40, 21, 7)])
+def test_population_buffers_are_whole_cell_bricks(shape):
+    """Populations live in bricks of 128 cells x 35 rows: a buffer holds ceil(N / 128) bricks
+    whatever N is (ragged last brick included), two buffers per two-buffer domain, one for the
+    one-buffer (AA) pattern; FP32 and FP16 differ only in the element size."""
+    nx, ny, nz = shape
+    p32 = inputs.uniform(nx, ny, nz).params
+    p16 = p32.replace(storage=inputs.STORE_F16)
+    bricks = -(-(nx * ny * nz) // 128)
+    one_buffer_f16 = 35 * 128 * bricks * 2
+    assert capi.grlb_bytes_for(p32) - capi.grlb_bytes_for(p16) == 2 * one_buffer_f16
+    assert capi.grlb_bytes_for(p16) - capi.grlb_bytes_for(p16.replace(streaming=1)) == one_buffer_f16
+
+
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
 def test_create_fails_cleanly_without_device():
     h = C.c_void_p()
