@@ -2,10 +2,12 @@
 // shell-averaged velocity spectrum and the solenoidal / dilatational dissipation computed with
 // spectral derivatives; plus the FFMA issue-rate probe used to place the instruction ceiling.
 //
-// Five kernels on one stream (scratch from the stream-ordered pool, see grlb_api.cu); every
-// FFT runs on lines held in padded shared memory as self-sorting (Stockham) passes of radix
-// 16 / 8 / 4 / 2 with 16 values per thread in registers, so a line of n = 2^lg points needs
-// n / 16 threads.  For a cube (x, y, z) or a square (x, y):
+// Five kernels on one stream (scratch from the stream-ordered pool, see grlb_api.cu).  A line
+// of n = 2^lg points is transformed by n / 16 threads with 16 values each in registers: along
+// x and z, for n <= 256, as a four-step transform (16-point DFTs of points loaded from global
+// memory, one shared-memory transpose, n/16-point DFTs); along y, and for longer lines, as
+// self-sorting (Stockham) passes of radix 16 / 8 / 4 / 2 on lines held in padded shared
+// memory.  For a cube (x, y, z) or a square (x, y):
 //   K1  prep + forward x: moments of the stored state -> u, mu(T) for a group of x-rows, FFT of
 //       the three velocity rows, store 3 complex planes and the mu plane; per-CTA FP64 sums
 //       of 1/2 |u|^2                                                    (168 B per cell)
@@ -144,6 +146,14 @@ __device__ __forceinline__ void fft_passes(float2* line, int q, const float2* __
     }
 }
 
+// twiddle read at each use (L1-resident table): a plain load would be kept in registers across
+// the transforms of a line group (four-step kernels)
+__device__ __forceinline__ float2 tw_load(const float2* p) {
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 // padded line length: one pad slot per 16 points and one per line
 template <int LG>
 struct Line {
@@ -270,6 +280,107 @@ __global__ void __launch_bounds__(192, 3) spectral_k1_kernel(const DomainDev D, 
             for (int k = 0; k < 3; ++k) U[k * N + c0 + w] = sm[sm_index(k * L + l, j, LS)];
         }
         __syncthreads();
+    }
+    const double tot = block_sum(ke, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// ---- K1 for n <= 256: prep + four-step forward along x ----------------------------------------
+// Thread q of an x-row (thread = l n2 + q, L = 128 / n2 rows per CTA of 128 threads) prepares
+// the 16 cells x = q + n2 r of its row as spectral_k1_kernel does (moments of the stored
+// state, u, mu(T); 16 consecutive cells per half-warp), keeps the three velocity components in
+// registers and, per component, takes the 16-point DFT over r, the twiddle W_n^{q s}, one
+// shared-memory transpose and the n2-point DFTs, then stores X[s + 16 t] for its values of s.
+// Per thread the kinetic energy of a group is summed in FP32, the groups in FP64.
+template <int S, int LG>
+__global__ void __launch_bounds__(128) spectral_k1_row_kernel(const DomainDev D, const void* __restrict__ fin_v,
+                                                              int gather, SpectralPlan P, const float2* __restrict__ tw,
+                                                              float2* __restrict__ U, float* __restrict__ mu_out,
+                                                              double* __restrict__ partials) {
+    using T = typename Store<S>::T;
+    constexpr int n = 1 << LG, n2 = n >> 4, L = 128 / n2, SP = 16 / n2;
+    constexpr int RL = n2 + 1, RF = L * RL + 1;  // element (s, l, q) at s RF + l RL + q
+    static_assert(LG >= 4 && LG <= 8, "four-step K1 needs 16 <= n <= 256");
+    extern __shared__ float2 sm[];
+    __shared__ double red[256];
+    const T* fin = static_cast<const T*>(fin_v);
+    const int64_t N = P.N;
+    const int nx = 1 << P.lgx, ny = 1 << P.lgy, nz = 1 << P.lgz;
+    const int64_t groups = (N >> LG) / L;
+    const int l = threadIdx.x / n2;
+    const int q = threadIdx.x % n2;  // also p, the role after the transpose
+    double ke = 0.0;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int64_t row = (g * L + l) << LG;
+        float ur[3][16];
+        float fke = 0.0f;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int64_t c = row + q + n2 * r;
+            int64_t at[NQ] = {c, c, c, c, c, c, c};
+            if (gather) {
+                const int x = (int)(c & (nx - 1));
+                const int y = (int)((c >> P.lgx) & (ny - 1));
+                const int z = (int)(c >> (P.lgx + P.lgy));
+                const int64_t rw = c - x, pl = (int64_t)nx * ny;
+                at[1] = rw + (x == nx - 1 ? 0 : x + 1);
+                at[2] = rw + (x == 0 ? nx - 1 : x - 1);
+                at[3] = c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
+                at[4] = c + (int64_t)((y == 0) ? (ny - 1) : -1) * nx;
+                at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
+                at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
+            }
+            float dQ[NF];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
+                dQ[k] = acc * D.dec[k];
+            }
+            const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);
+            const float u0 = dQ[1] / rf, u1 = dQ[2] / rf, u2 = dQ[3] / rf;
+            const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
+            const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
+            float mu = D.mu_ref;
+            if (D.sutherland) {
+                const float t = (p / rf) * D.inv_T_ref;
+                mu *= (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
+            }
+            mu_out[c] = mu;
+            fke += 0.5f * (u0 * u0 + u1 * u1 + u2 * u2);
+            ur[0][r] = u0;
+            ur[1][r] = u1;
+            ur[2][r] = u2;
+        }
+        ke += (double)fke;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = make_float2(ur[k][r], 0.0f);
+            dft_reg<16, false>(v);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                if (q > 0 && s > 0) v[s] = cmul(v[s], tw_load(tw + q * s));
+                sm[s * RF + l * RL + q] = v[s];
+            }
+            __syncthreads();
+            float2 w[16];
+#pragma unroll
+            for (int si = 0; si < SP; ++si)
+#pragma unroll
+                for (int qq = 0; qq < n2; ++qq) w[si * n2 + qq] = sm[(q * SP + si) * RF + l * RL + qq];
+            if constexpr (n2 > 1) {
+#pragma unroll
+                for (int si = 0; si < SP; ++si) dft_reg<n2, false>(w + si * n2);
+            }
+#pragma unroll
+            for (int si = 0; si < SP; ++si)
+#pragma unroll
+                for (int t = 0; t < n2; ++t) U[k * N + row + (q * SP + si) + 16 * t] = w[si * n2 + t];
+            __syncthreads();
+        }
     }
     const double tot = block_sum(ke, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
@@ -406,6 +517,144 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k3_kernel(float
         if (sbins[b]) atomicAdd(&bins[b], sbins[b]);
 }
 
+// ---- K3 for cubes of n <= 256: four-step transforms along z ------------------------------------
+// A line of n = 16 n2 points (n2 = n / 16 <= 16) is transformed as 16 x n2: thread q < n2 of a
+// line loads its 16 points z = q + n2 r straight from global memory, takes their 16-point DFT in
+// registers (Y_q[s]), multiplies by W_n^{q s} and writes them to shared memory; after one
+// transpose, thread p holds Y_q[s] of all q for its 16 / n2 values of s and takes the n2-point
+// DFTs over q, which leaves it X[s + 16 t], t < n2, of the line in registers -- the same
+// frequencies for each of the three velocity planes.  The modes (shell sums, i k x u^ and
+// i k . u^) are formed there, and each of the four outputs goes back the same way in reverse
+// (n2-point inverse DFTs over t, twiddle W_n^{-u s}, transpose, 16-point inverse DFT) and is
+// stored at z = q + n2 w: one shared-memory write and read per value and direction, against
+// two Stockham passes plus staging in spectral_k3_kernel.  L = 128 / n2 consecutive lines per
+// CTA of 128 threads (thread = q L + l, so a warp reads L or 32 consecutive lines of one z
+// row).  Shell sums: a warp's lanes at one register index share the frequency along z and
+// differ in x (and y for n = 16), so with the row parity and the sign half of the x mode in
+// the key, equal shells are contiguous lanes (|m_x| is monotone within a sign half) and the
+// segmented scan of spectral_k3_kernel applies.
+template <int LG>
+__global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restrict__ U, SpectralPlan P,
+                                                               const float2* __restrict__ tw,
+                                                               unsigned long long* __restrict__ bins) {
+    constexpr int n = 1 << LG, n2 = n >> 4, L = 128 / n2, SP = 16 / n2;
+    constexpr int RF = n2 * L + 4;   // forward transpose: element (s, q, l) at s RF + q L + l
+    constexpr int RI = 16 * L + 4;   // inverse transpose: element (u, s, l) at u RI + s L + l
+    static_assert(LG >= 4 && LG <= 8, "four-step K3 needs 16 <= n <= 256");
+    extern __shared__ float2 sm[];
+    constexpr int TB = (16 * RF > n2 * RI) ? 16 * RF : n2 * RI;
+    unsigned long long* sbins = reinterpret_cast<unsigned long long*>(sm + TB);
+    for (int b = threadIdx.x; b < P.nbins; b += blockDim.x) sbins[b] = 0ull;
+    __syncthreads();
+    const int64_t N = P.N;
+    const int64_t S3 = N >> LG;  // stride of z
+    const int64_t groups = S3 / L;
+    const int lgx = P.lgx;
+    const int nx = 1 << lgx;
+    const float tp = 6.283185307179586f / (float)n;
+    const int lane = threadIdx.x & 31;
+    const int l = threadIdx.x % L;
+    const int q = threadIdx.x / L;  // 0 .. n2-1 (also p, the transposed role)
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int64_t id = g * L + l;
+        float2* col = U + id;
+        float2 A[3][16];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = col[k * N + (int64_t)(q + n2 * r) * S3];
+            dft_reg<16, false>(v);
+#pragma unroll
+            for (int s = 1; s < 16; ++s)
+                if (q > 0) v[s] = cmul(v[s], tw_load(tw + q * s));
+#pragma unroll
+            for (int s = 0; s < 16; ++s) sm[s * RF + q * L + l] = v[s];
+            __syncthreads();
+#pragma unroll
+            for (int si = 0; si < SP; ++si)
+#pragma unroll
+                for (int qq = 0; qq < n2; ++qq) A[k][si * n2 + qq] = sm[(q * SP + si) * RF + qq * L + l];
+            if constexpr (n2 > 1) {
+#pragma unroll
+                for (int si = 0; si < SP; ++si) dft_reg<n2, false>(A[k] + si * n2);
+            }
+            __syncthreads();
+        }
+        // A[k][si n2 + t] = component k at frequency index kz = s + 16 t, s = q SP + si
+        const int ja = (int)(id & (nx - 1));
+        const int jb = (int)(id >> lgx);
+        const int ma = signed_mode(ja, n), mb = signed_mode(jb, n);
+        const float kx = (ja == (n >> 1)) ? 0.0f : tp * (float)ma;
+        const float ky = (jb == (n >> 1)) ? 0.0f : tp * (float)mb;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int jc = (q * SP + e / n2) + 16 * (e % n2);
+            const int mc = signed_mode(jc, n);
+            const float2 a = A[0][e], b = A[1][e], d = A[2][e];
+            const float en = 0.5f * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + d.x * d.x + d.y * d.y);
+            const int sh = shell_of((int64_t)ma * ma + (int64_t)mb * mb + (int64_t)mc * mc);
+            const bool valid = sh < P.nbins;
+            const int key = valid ? ((q & 3) << 18) | ((jb & 1) << 17) | ((ma < 0 ? 1 : 0) << 16) | sh : -1 - lane;
+            unsigned long long v = valid ? __float2ull_rn(en * P.scale) : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long t = __shfl_up_sync(0xffffffffu, v, off);
+                const int kk = __shfl_up_sync(0xffffffffu, key, off);
+                if (lane >= off && kk == key) v += t;
+            }
+            const int knext = __shfl_down_sync(0xffffffffu, key, 1);
+            if (valid && (lane == 31 || knext != key) && v) atomicAdd(&sbins[sh], v);
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            float2 w[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int jc = (q * SP + e / n2) + 16 * (e % n2);
+                const float kz = (jc == (n >> 1)) ? 0.0f : tp * (float)signed_mode(jc, n);
+                const float2 a = A[0][e], b = A[1][e], d = A[2][e];
+                float2 c;  // (k x u^)_o or k . u^, then times i: i (p + i q) = -q + i p
+                if (o == 0) c = make_float2(ky * d.x - kz * b.x, ky * d.y - kz * b.y);
+                else if (o == 1) c = make_float2(kz * a.x - kx * d.x, kz * a.y - kx * d.y);
+                else if (o == 2) c = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
+                else c = make_float2(kx * a.x + ky * b.x + kz * d.x, kx * a.y + ky * b.y + kz * d.y);
+                w[e] = make_float2(-c.y, c.x);
+            }
+            if constexpr (n2 > 1) {
+#pragma unroll
+                for (int si = 0; si < SP; ++si) dft_reg<n2, true>(w + si * n2);
+            }
+            // w[si n2 + u] = Z_s[u]; twiddle W_n^{-u s} and transpose to (u, s)
+#pragma unroll
+            for (int si = 0; si < SP; ++si) {
+                const int s = q * SP + si;
+#pragma unroll
+                for (int u = 0; u < n2; ++u) {
+                    float2 z = w[si * n2 + u];
+                    if (u > 0 && s > 0) {
+                        float2 t = tw_load(tw + u * s);
+                        t.y = -t.y;
+                        z = cmul(z, t);
+                    }
+                    sm[u * RI + s * L + l] = z;
+                }
+            }
+            __syncthreads();
+            float2 x[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) x[s] = sm[q * RI + s * L + l];
+            dft_reg<16, true>(x);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) col[o * N + (int64_t)(q + n2 * r) * S3] = x[r];
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < P.nbins; b += blockDim.x)
+        if (sbins[b]) atomicAdd(&bins[b], sbins[b]);
+}
+
 // ---- K5: inverse x + dissipation -------------------------------------------------------------
 // A group is L = 1024 / n consecutive x-rows of the four derivative planes; after the inverse
 // FFT along x the real parts are omega_x, omega_y, omega_z, theta (times N: the 1/N^2 of the
@@ -457,6 +706,88 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k5_kernel(const
     }
 }
 
+// ---- K5 for n <= 256: four-step inverse along x ------------------------------------------------
+// The inverse of the four-step transform of spectral_k3_cube_kernel along contiguous x-rows:
+// thread p of a row loads X[s + 16 t] (its 16 / n2 values of s, all t < n2) straight from
+// global memory, takes the n2-point inverse DFTs over t and the twiddle W_n^{-u s}; after one
+// shared-memory transpose thread q takes the 16-point inverse DFT over s and holds the points
+// x = q + n2 w, w < 16, of the row -- the same points for the four planes, so omega and theta
+// are squared in registers with no staging.  Per thread the 16 products of a group are summed
+// in FP32, the groups in FP64, the CTA in a fixed order.  L = 128 / n2 rows per CTA of 128
+// threads (thread = l n2 + q: 16 consecutive points per half-warp).
+template <int LG>
+__global__ void __launch_bounds__(128) spectral_k5_row_kernel(const float2* __restrict__ U, const float* __restrict__ mu,
+                                                              SpectralPlan P, const float2* __restrict__ tw,
+                                                              double* __restrict__ partials) {
+    constexpr int n = 1 << LG, n2 = n >> 4, L = 128 / n2, SP = 16 / n2;
+    constexpr int RL = 17, RI = L * RL + 1;  // element (u, s, l) at u RI + l RL + s
+    static_assert(LG >= 4 && LG <= 8, "four-step K5 needs 16 <= n <= 256");
+    extern __shared__ float2 sm[];
+    __shared__ double red[256];
+    const int64_t N = P.N;
+    const int64_t groups = (N >> LG) / L;
+    const int l = threadIdx.x / n2;
+    const int q = threadIdx.x % n2;  // also p, the role before the transpose
+    double es = 0.0, ed = 0.0;
+    for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        const int64_t row = (g * L + l) << LG;  // first cell of the row
+        float wsq[16], th[16];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            float2 w[16];
+#pragma unroll
+            for (int si = 0; si < SP; ++si)
+#pragma unroll
+                for (int t = 0; t < n2; ++t) w[si * n2 + t] = U[o * N + row + (q * SP + si) + 16 * t];
+            if constexpr (n2 > 1) {
+#pragma unroll
+                for (int si = 0; si < SP; ++si) dft_reg<n2, true>(w + si * n2);
+            }
+#pragma unroll
+            for (int si = 0; si < SP; ++si) {
+                const int s = q * SP + si;
+#pragma unroll
+                for (int u = 0; u < n2; ++u) {
+                    float2 z = w[si * n2 + u];
+                    if (u > 0 && s > 0) {
+                        float2 t = tw_load(tw + u * s);
+                        t.y = -t.y;
+                        z = cmul(z, t);
+                    }
+                    sm[u * RI + l * RL + s] = z;
+                }
+            }
+            __syncthreads();
+            float2 x[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) x[s] = sm[q * RI + l * RL + s];
+            dft_reg<16, true>(x);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                if (o == 0) wsq[e] = x[e].x * x[e].x;
+                else if (o < 3) wsq[e] += x[e].x * x[e].x;
+                else th[e] = x[e].x;
+            }
+            __syncthreads();
+        }
+        float fs = 0.0f, fd = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const float m = mu[row + q + n2 * e];
+            fs += m * wsq[e];
+            fd += (4.0f / 3.0f) * m * th[e] * th[e];
+        }
+        es += (double)fs;
+        ed += (double)fd;
+    }
+    const double s1 = block_sum(es, red);
+    const double s2 = block_sum(ed, red);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = s1;
+        partials[2 * blockIdx.x + 1] = s2;
+    }
+}
+
 // ---- FFMA issue-rate probe ----------------------------------------------------------------
 // 8 independent FFMA chains per thread, 16 x 8 FFMAs per loop trip; x -> a x + b converges to
 // b / (1 - a), so the chain sum is never 0 and the guarded store (in bounds either way) never
@@ -499,6 +830,18 @@ size_t line_bytes() { return (size_t)Line<LG>::LS * sizeof(float2); }
 template <int S, int LG>
 cudaError_t k1_t(const DomainDev& D, const void* fin, int gather, SpectralPlan& P, const float2* tw, float2* U,
                  float* mu, double* partials, cudaStream_t st) {
+    if constexpr (LG <= 8) {
+        constexpr int n2 = (1 << LG) >> 4, Lr = 128 / n2;
+        if ((P.N >> LG) >= Lr) {  // four-step forward along x (every cube; squares of n >= 64)
+            const size_t smem = (size_t)16 * (Lr * (n2 + 1) + 1) * sizeof(float2);
+            auto kr = spectral_k1_row_kernel<S, LG>;
+            cudaError_t e = allow_smem(kr, smem);
+            if (e != cudaSuccess) return e;
+            P.grid1 = std::min(P.grid1, resident_grid(kr, 128, smem, (P.N >> LG) / Lr));
+            kr<<<P.grid1, 128, smem, st>>>(D, fin, gather, P, tw, U, mu, partials);
+            return cudaGetLastError();
+        }
+    }
     constexpr int L = Groups<LG>::L1;
     const size_t smem = 3 * L * line_bytes<LG>();
     const int threads = (3 * L) << (LG - 4);
@@ -524,15 +867,37 @@ cudaError_t rest_t(SpectralPlan& P, const float2* tw, float2* U, const float* mu
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     constexpr int L = Groups<LG>::L1;
-    const size_t smem3 = 4 * L * line_bytes<LG>() + (size_t)P.nbins * sizeof(unsigned long long);
-    if ((e = allow_smem(spectral_k3_kernel<LG>, smem3)) != cudaSuccess) return e;
-    P.grid3 = std::min(P.grid3, resident_grid(spectral_k3_kernel<LG>, 256, smem3, (P.N >> LG) / L));
-    spectral_k3_kernel<LG><<<P.grid3, 256, smem3, st>>>(U, P, tw, bins);
+    if constexpr (LG <= 8) {
+        if (cube) {  // four-step transforms along z
+            constexpr int n2 = (1 << LG) >> 4, Lc = 128 / n2;
+            constexpr int TB = (16 * (n2 * Lc + 4) > n2 * (16 * Lc + 4)) ? 16 * (n2 * Lc + 4) : n2 * (16 * Lc + 4);
+            const size_t smem3 = TB * sizeof(float2) + (size_t)P.nbins * sizeof(unsigned long long);
+            if ((e = allow_smem(spectral_k3_cube_kernel<LG>, smem3)) != cudaSuccess) return e;
+            P.grid3 = resident_grid(spectral_k3_cube_kernel<LG>, 128, smem3, (P.N >> LG) / Lc);
+            spectral_k3_cube_kernel<LG><<<P.grid3, 128, smem3, st>>>(U, P, tw, bins);
+        }
+    }
+    if (LG > 8 || !cube) {
+        const size_t smem3 = 4 * L * line_bytes<LG>() + (size_t)P.nbins * sizeof(unsigned long long);
+        if ((e = allow_smem(spectral_k3_kernel<LG>, smem3)) != cudaSuccess) return e;
+        P.grid3 = std::min(P.grid3, resident_grid(spectral_k3_kernel<LG>, 256, smem3, (P.N >> LG) / L));
+        spectral_k3_kernel<LG><<<P.grid3, 256, smem3, st>>>(U, P, tw, bins);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (cube) {
         if ((e = allow_smem(spectral_fft_y_kernel<LG, true>, smem2)) != cudaSuccess) return e;
         spectral_fft_y_kernel<LG, true><<<dim3(grid2, 4), 256, smem2, st>>>(U, P, tw);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if constexpr (LG <= 8) {
+        constexpr int n2 = (1 << LG) >> 4, Lr = 128 / n2;
+        if ((P.N >> LG) >= Lr) {  // four-step inverse along x (every cube; squares of n >= 64)
+            const size_t smem5 = (size_t)n2 * (Lr * 17 + 1) * sizeof(float2);
+            if ((e = allow_smem(spectral_k5_row_kernel<LG>, smem5)) != cudaSuccess) return e;
+            P.grid5 = std::min(P.grid5, resident_grid(spectral_k5_row_kernel<LG>, 128, smem5, (P.N >> LG) / Lr));
+            spectral_k5_row_kernel<LG><<<P.grid5, 128, smem5, st>>>(U, mu, P, tw, partials);
+            return cudaGetLastError();
+        }
     }
     const size_t smem5 = 4 * L * line_bytes<LG>();
     if ((e = allow_smem(spectral_k5_kernel<LG>, smem5)) != cudaSuccess) return e;

@@ -41,10 +41,12 @@ def assert_sums_close(sg, so, rel):
     assert sg["ke_u"] == pytest.approx(so["ke_u"], rel=rel)
 
 
-@pytest.mark.parametrize("n", [32, 256])
+@pytest.mark.parametrize("n", [16, 32, 256, 512])
 def test_taylor_green_initial_closed_form(n):
     """All energy at |m| = sqrt 3 (shell 2): s^2/8 per cell; sum mu |curl u|^2 =
-    N mu_L (s dx)^2 3/4; no divergence.  256^3 is the full benchmark size."""
+    N mu_L (s dx)^2 3/4; no divergence.  256^3 is the full benchmark size; lines of n <= 256
+    points take the four-step kernels (n = 16: one thread per line), n = 512 the Stockham
+    kernels."""
     c = inputs.tgv3d(n)
     d = gpu_domain(c)
     E, s = d.spectral()
@@ -58,9 +60,9 @@ def test_taylor_green_initial_closed_form(n):
     d.close()
 
 
-@pytest.mark.parametrize("steps", [0, 30])
-def test_random_smooth_parity(steps):
-    c = inputs.random_smooth(32, 32, 32, seed=11)
+@pytest.mark.parametrize("n,steps", [(32, 0), (32, 30), (16, 12)])
+def test_random_smooth_parity(n, steps):
+    c = inputs.random_smooth(n, n, n, seed=11)
     d = gpu_domain(c, steps)
     Eg, sg = d.spectral()
     o = run_oracle(c, steps)
@@ -81,12 +83,15 @@ def test_taylor_green_64_after_steps():
     d.close()
 
 
-def test_square_2d_box():
-    c = inputs.tgv2d(64)
+@pytest.mark.parametrize("n", [64, 32])
+def test_square_2d_box(n):
+    """n = 64: four-step x transforms; n = 32 (fewer rows than a four-step CTA takes): the
+    Stockham kernels."""
+    c = inputs.tgv2d(n)
     d = gpu_domain(c, 20)
     Eg, sg = d.spectral()
     Eo, so = spectral.from_oracle(run_oracle(c, 20))
-    assert len(Eg) == spectral.shells(64, 64, 1)
+    assert len(Eg) == spectral.shells(n, n, 1)
     assert_spectra_close(Eg, Eo, 1e-4, 1e-6)
     assert_sums_close(sg, so, 1e-4)
     d.close()
