@@ -3,11 +3,11 @@
 // spectral derivatives; plus the FFMA issue-rate probe used to place the instruction ceiling.
 //
 // Five kernels on one stream (scratch from the stream-ordered pool, see grlb_api.cu).  A line
-// of n = 2^lg points is transformed by n / 16 threads with 16 values each in registers: along
-// x and z, for n <= 256, as a four-step transform (16-point DFTs of points loaded from global
-// memory, one shared-memory transpose, n/16-point DFTs); along y, and for longer lines, as
-// self-sorting (Stockham) passes of radix 16 / 8 / 4 / 2 on lines held in padded shared
-// memory.  For a cube (x, y, z) or a square (x, y):
+// of n = 2^lg points is transformed by n / 16 threads with 16 values each in registers: for
+// n <= 256 as a four-step transform (16-point DFTs of points loaded from global memory, one
+// shared-memory transpose, n/16-point DFTs); for longer lines (and the few rows of small
+// squares) as self-sorting (Stockham) passes of radix 16 / 8 / 4 / 2 on lines held in padded
+// shared memory.  For a cube (x, y, z) or a square (x, y):
 //   K1  prep + forward x: moments of the stored state -> u, mu(T) for a group of x-rows, FFT of
 //       the three velocity rows, store 3 complex planes and the mu plane; per-CTA FP64 sums
 //       of 1/2 |u|^2                                                    (168 B per cell)
@@ -148,6 +148,12 @@ __device__ __forceinline__ void fft_passes(float2* line, int q, const float2* __
 
 // twiddle read at each use (L1-resident table): a plain load would be kept in registers across
 // the transforms of a line group (four-step kernels)
+// an int the compiler cannot see through: values derived from it are recomputed where they are
+// used instead of being hoisted out of a kernel's persistent loop and held in registers
+__device__ __forceinline__ int opaque(int v) {
+    asm volatile("" : "+r"(v));
+    return v;
+}
 __device__ __forceinline__ float2 tw_load(const float2* p) {
     float2 v;
     asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
@@ -416,6 +422,86 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_fft_y_kernel(fl
     for (int e = 0; e < 16; ++e) src[e * inc] = sm[sm_index(l, j0 + e * jstep, LS)];
 }
 
+// ---- K2 / K4 for cubes of n <= 256: four-step transforms along y -------------------------------
+// The transforms of spectral_k3_cube_kernel on one plane (blockIdx.y), lines along y (points
+// at stride nx): forward, thread q loads y = q + n2 r, 16-point DFT, twiddle W_n^{q s},
+// transpose, n2-point DFTs, store X[s + 16 t]; inverse, thread p loads X[s + 16 t] of its
+// values of s, n2-point inverse DFTs, twiddle W_n^{-u s}, transpose, 16-point inverse DFT,
+// store y = q + n2 w.  Every point of a CTA's lines is loaded before the barrier that precedes
+// the first store, so the transform is in place.  L = 128 / n2 lines of consecutive x per CTA
+// of 128 threads (thread = q L + l).
+template <int LG, bool INV>
+__global__ void __launch_bounds__(128) spectral_fft_y4_kernel(float2* __restrict__ U, SpectralPlan P,
+                                                              const float2* __restrict__ tw) {
+    constexpr int n = 1 << LG, n2 = n >> 4, L = 128 / n2, SP = 16 / n2;
+    constexpr int RF = n2 * L + 4;  // forward transpose: (s, q, l) at s RF + q L + l
+    constexpr int RI = 16 * L + 4;  // inverse transpose: (u, s, l) at u RI + s L + l
+    static_assert(LG >= 4 && LG <= 8, "four-step y pass needs 16 <= n <= 256");
+    extern __shared__ float2 sm[];
+    const int nx = 1 << P.lgx;
+    float2* plane = U + (int64_t)blockIdx.y * P.N;
+    const int l = threadIdx.x % L;
+    const int q = threadIdx.x / L;
+    const int64_t id = (int64_t)blockIdx.x * L + l;
+    float2* line = plane + (id & (nx - 1)) + ((id >> P.lgx) << (P.lgx + P.lgy));
+    if (!INV) {
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = line[(int64_t)(q + n2 * r) * nx];
+        dft_reg<16, false>(v);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            if (q > 0 && s > 0) v[s] = cmul(v[s], tw_load(tw + q * s));
+            sm[s * RF + q * L + l] = v[s];
+        }
+        __syncthreads();
+        float2 w[16];
+#pragma unroll
+        for (int si = 0; si < SP; ++si)
+#pragma unroll
+            for (int qq = 0; qq < n2; ++qq) w[si * n2 + qq] = sm[(q * SP + si) * RF + qq * L + l];
+        if constexpr (n2 > 1) {
+#pragma unroll
+            for (int si = 0; si < SP; ++si) dft_reg<n2, false>(w + si * n2);
+        }
+#pragma unroll
+        for (int si = 0; si < SP; ++si)
+#pragma unroll
+            for (int t = 0; t < n2; ++t) line[(int64_t)(q * SP + si + 16 * t) * nx] = w[si * n2 + t];
+    } else {
+        float2 w[16];
+#pragma unroll
+        for (int si = 0; si < SP; ++si)
+#pragma unroll
+            for (int t = 0; t < n2; ++t) w[si * n2 + t] = line[(int64_t)(q * SP + si + 16 * t) * nx];
+        if constexpr (n2 > 1) {
+#pragma unroll
+            for (int si = 0; si < SP; ++si) dft_reg<n2, true>(w + si * n2);
+        }
+#pragma unroll
+        for (int si = 0; si < SP; ++si) {
+            const int s = q * SP + si;
+#pragma unroll
+            for (int u = 0; u < n2; ++u) {
+                float2 z = w[si * n2 + u];
+                if (u > 0 && s > 0) {
+                    float2 t = tw_load(tw + u * s);
+                    t.y = -t.y;
+                    z = cmul(z, t);
+                }
+                sm[u * RI + s * L + l] = z;
+            }
+        }
+        __syncthreads();
+        float2 x[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) x[s] = sm[q * RI + s * L + l];
+        dft_reg<16, true>(x);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) line[(int64_t)(q + n2 * r) * nx] = x[r];
+    }
+}
+
 // ---- K3: forward + modes + inverse along the last axis -----------------------------------------
 // Lines along the last axis a (z for a cube, y for a square): line id < N / n starts at id,
 // stride N / n.  A group is L = 1024 / n lines of consecutive id.  After the forward FFT of the
@@ -561,9 +647,10 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
         float2 A[3][16];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
+            const int qk = opaque(q);
             float2 v[16];
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = col[k * N + (int64_t)(q + n2 * r) * S3];
+            for (int r = 0; r < 16; ++r) v[r] = col[k * N + (int64_t)(qk + n2 * r) * S3];
             dft_reg<16, false>(v);
 #pragma unroll
             for (int s = 1; s < 16; ++s)
@@ -587,9 +674,10 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
         const int ma = signed_mode(ja, n), mb = signed_mode(jb, n);
         const float kx = (ja == (n >> 1)) ? 0.0f : tp * (float)ma;
         const float ky = (jb == (n >> 1)) ? 0.0f : tp * (float)mb;
+        const int qs = opaque(q);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-            const int jc = (q * SP + e / n2) + 16 * (e % n2);
+            const int jc = (qs * SP + e / n2) + 16 * (e % n2);
             const int mc = signed_mode(jc, n);
             const float2 a = A[0][e], b = A[1][e], d = A[2][e];
             const float en = 0.5f * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + d.x * d.x + d.y * d.y);
@@ -606,20 +694,25 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
             const int knext = __shfl_down_sync(0xffffffffu, key, 1);
             if (valid && (lane == 31 || knext != key) && v) atomicAdd(&sbins[sh], v);
         }
-#pragma unroll
+        // one output plane at a time, in a rolled loop (unrolled, the kernel needs 194-255
+        // registers instead of 168-173)
+#pragma unroll 1
         for (int o = 0; o < 4; ++o) {
+            const int qo = opaque(q);
             float2 w[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const int jc = (q * SP + e / n2) + 16 * (e % n2);
+                const int jc = (qo * SP + e / n2) + 16 * (e % n2);
                 const float kz = (jc == (n >> 1)) ? 0.0f : tp * (float)signed_mode(jc, n);
                 const float2 a = A[0][e], b = A[1][e], d = A[2][e];
-                float2 c;  // (k x u^)_o or k . u^, then times i: i (p + i q) = -q + i p
-                if (o == 0) c = make_float2(ky * d.x - kz * b.x, ky * d.y - kz * b.y);
-                else if (o == 1) c = make_float2(kz * a.x - kx * d.x, kz * a.y - kx * d.y);
-                else if (o == 2) c = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
-                else c = make_float2(kx * a.x + ky * b.x + kz * d.x, kx * a.y + ky * b.y + kz * d.y);
-                w[e] = make_float2(-c.y, c.x);
+                // (k x u^)_o (o < 3) or k . u^ (o = 3) as ca a + cb b + cd d, one form for all
+                // four planes (computing each plane's own expression and selecting costs the
+                // registers of all four)
+                const float ca = o == 1 ? kz : (o == 2 ? -ky : (o == 3 ? kx : 0.0f));
+                const float cb = o == 0 ? -kz : (o == 2 ? kx : (o == 3 ? ky : 0.0f));
+                const float cd = o == 0 ? ky : (o == 1 ? -kx : (o == 3 ? kz : 0.0f));
+                const float2 c = make_float2(ca * a.x + cb * b.x + cd * d.x, ca * a.y + cb * b.y + cd * d.y);
+                w[e] = make_float2(-c.y, c.x);  // times i: i (p + i q) = -q + i p
             }
             if constexpr (n2 > 1) {
 #pragma unroll
@@ -628,7 +721,7 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
             // w[si n2 + u] = Z_s[u]; twiddle W_n^{-u s} and transpose to (u, s)
 #pragma unroll
             for (int si = 0; si < SP; ++si) {
-                const int s = q * SP + si;
+                const int s = qo * SP + si;
 #pragma unroll
                 for (int u = 0; u < n2; ++u) {
                     float2 z = w[si * n2 + u];
@@ -643,10 +736,10 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
             __syncthreads();
             float2 x[16];
 #pragma unroll
-            for (int s = 0; s < 16; ++s) x[s] = sm[q * RI + s * L + l];
+            for (int s = 0; s < 16; ++s) x[s] = sm[qo * RI + s * L + l];
             dft_reg<16, true>(x);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) col[o * N + (int64_t)(q + n2 * r) * S3] = x[r];
+            for (int r = 0; r < 16; ++r) col[o * N + (int64_t)(qo + n2 * r) * S3] = x[r];
             __syncthreads();
         }
     }
@@ -861,9 +954,18 @@ cudaError_t rest_t(SpectralPlan& P, const float2* tw, float2* U, const float* mu
     const bool cube = P.lgz > 0;
     const size_t smem2 = Groups<LG>::L2 * line_bytes<LG>();
     const unsigned grid2 = (unsigned)((P.N >> LG) / Groups<LG>::L2);
+    constexpr int n2y = ((1 << LG) >> 4) > 0 ? ((1 << LG) >> 4) : 1, Ly = 128 / n2y;
+    constexpr size_t smem_y4 = (size_t)(16 * (n2y * Ly + 4) > n2y * (16 * Ly + 4) ? 16 * (n2y * Ly + 4)
+                                                                                  : n2y * (16 * Ly + 4)) * sizeof(float2);
+    const unsigned grid_y4 = (unsigned)((P.N >> LG) / Ly);
     if (cube) {
-        if ((e = allow_smem(spectral_fft_y_kernel<LG, false>, smem2)) != cudaSuccess) return e;
-        spectral_fft_y_kernel<LG, false><<<dim3(grid2, 3), 256, smem2, st>>>(U, P, tw);
+        if constexpr (LG <= 8) {
+            if ((e = allow_smem(spectral_fft_y4_kernel<LG, false>, smem_y4)) != cudaSuccess) return e;
+            spectral_fft_y4_kernel<LG, false><<<dim3(grid_y4, 3), 128, smem_y4, st>>>(U, P, tw);
+        } else {
+            if ((e = allow_smem(spectral_fft_y_kernel<LG, false>, smem2)) != cudaSuccess) return e;
+            spectral_fft_y_kernel<LG, false><<<dim3(grid2, 3), 256, smem2, st>>>(U, P, tw);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     constexpr int L = Groups<LG>::L1;
@@ -885,8 +987,13 @@ cudaError_t rest_t(SpectralPlan& P, const float2* tw, float2* U, const float* mu
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (cube) {
-        if ((e = allow_smem(spectral_fft_y_kernel<LG, true>, smem2)) != cudaSuccess) return e;
-        spectral_fft_y_kernel<LG, true><<<dim3(grid2, 4), 256, smem2, st>>>(U, P, tw);
+        if constexpr (LG <= 8) {
+            if ((e = allow_smem(spectral_fft_y4_kernel<LG, true>, smem_y4)) != cudaSuccess) return e;
+            spectral_fft_y4_kernel<LG, true><<<dim3(grid_y4, 4), 128, smem_y4, st>>>(U, P, tw);
+        } else {
+            if ((e = allow_smem(spectral_fft_y_kernel<LG, true>, smem2)) != cudaSuccess) return e;
+            spectral_fft_y_kernel<LG, true><<<dim3(grid2, 4), 256, smem2, st>>>(U, P, tw);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if constexpr (LG <= 8) {
