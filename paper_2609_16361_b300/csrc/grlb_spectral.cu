@@ -51,20 +51,47 @@ __device__ __forceinline__ float2 root16(int k, bool inv) {
     return make_float2(c, inv ? sn : -sn);
 }
 
+// v times the 16th root of unity root16(K, INV), K compile-time.  K = 4 (-i, or i for the
+// inverse) is a swap with a sign change and K = 2, 6 ((1 - i) / sqrt 2 and (-1 - i) / sqrt 2,
+// conjugated for the inverse) take two additions and two multiplications: a general complex
+// product would multiply by the zero parts, which IEEE arithmetic does not let the compiler drop.
+template <int K, bool INV>
+__device__ __forceinline__ float2 mul_root16(float2 v) {
+    constexpr float c = 0.70710678118654752f;
+    if constexpr (K == 0) {
+        return v;
+    } else if constexpr (K == 4) {
+        return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    } else if constexpr (K == 2) {
+        return INV ? make_float2(c * (v.x - v.y), c * (v.x + v.y)) : make_float2(c * (v.x + v.y), c * (v.y - v.x));
+    } else if constexpr (K == 6) {
+        return INV ? make_float2(-c * (v.x + v.y), c * (v.x - v.y)) : make_float2(c * (v.y - v.x), -c * (v.x + v.y));
+    } else {
+        return cmul(v, root16(K, INV));
+    }
+}
+
 // Radix-2 butterfly stages of span LEN, 2 LEN, ..., R over v (compile-time recursion, so no
 // stage loop is left for the compiler to keep rolled and index dynamically).
+// the LEN / 2 butterflies of one group, p = P, P + 1, ... (recursion: the twiddle index is a
+// template argument)
+template <int LEN, int P, bool INV>
+__device__ __forceinline__ void butterflies(float2* v) {
+    if constexpr (P < LEN / 2) {
+        const float2 a = v[P];
+        const float2 b = mul_root16<P * (16 / LEN), INV>(v[P + LEN / 2]);
+        v[P] = make_float2(a.x + b.x, a.y + b.y);
+        v[P + LEN / 2] = make_float2(a.x - b.x, a.y - b.y);
+        butterflies<LEN, P + 1, INV>(v);
+    }
+}
+
 template <int R, int LEN, bool INV>
 __device__ __forceinline__ void dft_stages(float2* v) {
     if constexpr (LEN <= R) {
 #pragma unroll
         for (int g = 0; g < R; g += LEN) {
-#pragma unroll
-            for (int p = 0; p < LEN / 2; ++p) {
-                const float2 a = v[g + p];
-                const float2 b = p == 0 ? v[g + p + LEN / 2] : cmul(v[g + p + LEN / 2], root16(p * (16 / LEN), INV));
-                v[g + p] = make_float2(a.x + b.x, a.y + b.y);
-                v[g + p + LEN / 2] = make_float2(a.x - b.x, a.y - b.y);
-            }
+            butterflies<LEN, 0, INV>(v + g);
         }
         dft_stages<R, 2 * LEN, INV>(v);
     }
