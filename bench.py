@@ -390,7 +390,10 @@ def run_ours(args):
 def run_batch(args):
     """64 uneven domains (48 Becker tubes + 16 Taylor-Green boxes, seed 0), 1000 steps each:
     persistent batched sweep with autotuned tile widths and a CUDA-graph step loop, against
-    64 sequential single-domain runs (one launch per step, no graphs)."""
+    64 sequential single-domain runs through grlb_step -- one launch per sweep (the domains on
+    the legacy default stream, where grlb_step replays no graph: the baseline `vs_sequential_plain`
+    divides by) and, for reference, on a stream of their own, where grlb_step replays the
+    small domains' sweeps from CUDA graphs."""
     import torch
     from paper_2609_16361_b300 import autotune, capi, inputs
     torch.cuda.set_device(0)
@@ -426,17 +429,20 @@ def run_batch(args):
         t = e0.elapsed_time(e1) / 1e3
         capi.grlb_batch_destroy(b)
         out[label] = {"mlups": cells * steps / t / 1e6, "seconds": t}
-    for d, c in zip(doms, cases):
-        d.init(c.rho, c.u, c.p)
-    stream.synchronize()
-    e0, e1 = ev(), ev()
-    e0.record(stream)
-    for d in doms:
-        d.step(steps)
-    e1.record(stream)
-    e1.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
-    out["sequential_plain"] = {"mlups": cells * steps / t / 1e6, "seconds": t}
+    legacy = torch.cuda.default_stream()
+    for label, s_run in (("sequential_plain", legacy), ("sequential_graph_replay", stream)):
+        for d, c in zip(doms, cases):
+            capi.grlb_set_stream(d.h, s_run.cuda_stream)
+            d.init(c.rho, c.u, c.p)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(s_run)
+        for d in doms:
+            d.step(steps)
+        e1.record(s_run)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        out[label] = {"mlups": cells * steps / t / 1e6, "seconds": t}
     diag_ok = True
     for d in doms:
         d.step_diag()
@@ -447,6 +453,7 @@ def run_batch(args):
     line = {"metric": "batched MLUP/s (64 uneven domains, 1000 steps each)", "value": best,
             "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True,
             "vs_sequential_plain": best / out["sequential_plain"]["mlups"],
+            "vs_sequential_graph_replay": best / out["sequential_graph_replay"]["mlups"],
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "48 Becker tubes (128-2048 x 4 x 4, M 1.5-5) + 16 Taylor-Green "
                                    "boxes (32^3-96^3, M 0.5-1.25, Re 100), seed 0",

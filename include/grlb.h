@@ -147,7 +147,13 @@ grlb_status grlb_stage_primitive(grlb_domain* d, const double* rho, const double
                                  const double* p);
 grlb_status grlb_init_from_stage(grlb_domain* d);
 
-/* Enqueue nsteps >= 0 plain sweeps (Algorithm 1 on every cell + exact streaming). */
+/* Enqueue nsteps >= 0 plain sweeps (Algorithm 1 on every cell + exact streaming).  A domain of
+ * at most 4,194,304 cells on a stream other than the legacy default stream, asked for at least
+ * 16 sweeps while its stream is not being captured, replays them from a CUDA graph of 8 sweeps
+ * (captured on the first such call, re-captured after grlb_set_source_device; at most one
+ * plain sweep first to match the graph's buffer and step parity, plain sweeps for the
+ * remainder): the same kernels in the same order, so the state is bitwise that of one launch
+ * per sweep.  Otherwise every sweep is one launch. */
 grlb_status grlb_step(grlb_domain* d, int nsteps);
 
 /* Enqueue one diagnostic sweep: the same update as grlb_step(d, 1), which also reduces
