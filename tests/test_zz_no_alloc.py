@@ -17,10 +17,14 @@ pytestmark = pytest.mark.gpu
 HDR = 32  # bytes of the grlb_save header before the populations
 
 
-def test_noalloc_diag_sweep_matches_allocating_entry_point_twice():
+@pytest.mark.parametrize("case", ["tgv32", "ragged"])
+def test_noalloc_diag_sweep_matches_allocating_entry_point_twice(case):
+    """tgv32: 256 whole cell bricks; ragged: 40 x 21 x 7 = 5880 cells, 46 bricks, the last one
+    partly used (the caller's buffers hold whole bricks; the unused cells are never written,
+    so the output buffer starts zeroed like the library's own)."""
     torch = pytest.importorskip("torch")
     assert torch.cuda.is_available()
-    c = inputs.tgv3d(32)
+    c = inputs.tgv3d(32) if case == "tgv32" else inputs.random_smooth(40, 21, 7, seed=9)
     prm = c.params
     N = prm.ncells
     d = capi.Domain(prm)
@@ -28,8 +32,9 @@ def test_noalloc_diag_sweep_matches_allocating_entry_point_twice():
     d.step(7)
     torch.cuda.synchronize()
     state = capi.grlb_save(d.h)[HDR:]
+    assert state.size == 35 * 128 * (-(-N // 128)) * 4
     f_a = torch.from_numpy(state.copy()).cuda()
-    f_b = torch.empty_like(f_a)
+    f_b = torch.zeros_like(f_a)
     diag = torch.zeros(13, dtype=torch.float64, device="cuda")
     Qref = np.array([prm.ref_rho, 0, 0, 0, prm.ref_p * (prm.dt / prm.dx) ** 2 / (prm.gamma - 1)])
     src, dst = f_a, f_b
