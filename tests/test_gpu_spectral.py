@@ -60,7 +60,7 @@ def test_taylor_green_initial_closed_form(n):
     d.close()
 
 
-@pytest.mark.parametrize("n,steps", [(32, 0), (32, 30), (16, 12)])
+@pytest.mark.parametrize("n,steps", [(32, 0), (32, 30), (16, 12), (128, 0)])
 def test_random_smooth_parity(n, steps):
     c = inputs.random_smooth(n, n, n, seed=11)
     d = gpu_domain(c, steps)
