@@ -192,7 +192,8 @@ int64_t grlb_steps_done(const grlb_domain* d);
  * the GPU on its own and runs the kernel grlb_step runs, so its result is bitwise that of
  * grlb_step; a large domain may use one-buffer streaming, a small one may not).  A 128-thread CTA covers tile_x cells along x times 128/tile_x rows.  A small
  * domain's result does not depend on the other domains of the batch and matches grlb_step
- * within FP32 rounding.  All domains must live on the same device; the batch runs on the
+ * within FP32 rounding (16-bit storage: up to a few stored values one 16-bit rounding apart).
+ * All domains must live on the same device; the batch runs on the
  * stream of domains[0] (or the one set with grlb_batch_set_stream). */
 typedef struct {
     int32_t block_x;        /* default tile width: 32, 64 or 128 (0 = 128, narrowed for

@@ -68,10 +68,13 @@ def test_batch_equals_solo_runs(use_graph, nsteps, block_x):
         raw = capi.grlb_save(d.h)[32:]
         # alone in a batch == in the mix, bitwise
         assert np.array_equal(raw, batched_alone(c, nsteps, block_x, use_graph)), c.params.name
-        # == the solo sweep within FP32 rounding
+        # == the solo sweep within FP32 rounding; with 16-bit storage an FP32 rounding difference
+        # between the two kernels can round a stored value to the neighbouring 16-bit number
+        # (the tolerance of the other 16-bit path comparisons)
         Q_ref, _ = solo(c, nsteps)
         err = rel_linf(d.conserved(), Q_ref)
-        assert np.all(err <= 1e-6), (c.params.name, err)
+        tol = 1e-6 if c.params.storage == inputs.STORE_F32 else 1e-2
+        assert np.all(err <= tol), (c.params.name, err)
     capi.grlb_batch_destroy(b)
 
 
