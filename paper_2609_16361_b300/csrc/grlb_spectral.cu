@@ -372,13 +372,16 @@ __global__ void __launch_bounds__(128) spectral_k1_row_kernel(const DomainDev D,
                 dQ[k] = acc * D.dec[k];
             }
             const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);
-            const float u0 = dQ[1] / rf, u1 = dQ[2] / rf, u2 = dQ[3] / rf;
+            // approximate division (within 2 ulp): the IEEE slow path costs this kernel time and
+            // registers, and u, mu feed FP32 transforms
+            const float irf = __fdividef(1.0f, rf);
+            const float u0 = dQ[1] * irf, u1 = dQ[2] * irf, u2 = dQ[3] * irf;
             const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
             const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
             float mu = D.mu_ref;
             if (D.sutherland) {
-                const float t = (p / rf) * D.inv_T_ref;
-                mu *= (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
+                const float t = (p * irf) * D.inv_T_ref;
+                mu *= __fdividef((1.0f + D.T_S) * t * sqrtf(t), t + D.T_S);
             }
             mu_out[c] = mu;
             fke += 0.5f * (u0 * u0 + u1 * u1 + u2 * u2);
