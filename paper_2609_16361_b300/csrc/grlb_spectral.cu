@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
             if (valid && (lane == 31 || knext != key) && v) atomicAdd(&sbins[sh], v);
         }
         // one output plane at a time, in a rolled loop (unrolled, the kernel needs 194-255
-        // registers instead of 168-173)
+        // registers instead of 168)
 #pragma unroll 1
         for (int o = 0; o < 4; ++o) {
             const int qo = opaque(q);
