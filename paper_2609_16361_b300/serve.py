@@ -234,8 +234,9 @@ def request_params(r, large_cells: int, one_buffer_large: bool):
 
 def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = False,
                  one_buffer_large: bool = False, large_cells: int = 262144):
-    """Baseline: first-in first-out, one domain at a time, one single-domain launch per step
-    (no batching, no graphs); the same buffer choice per request as the server's."""
+    """Baseline: first-in first-out, one domain at a time through grlb_step on `stream` (no
+    batching; grlb_step replays a small domain's sweeps from a CUDA graph of 8 launches); the
+    same buffer choice per request as the server's."""
     import torch
     stream = stream or torch.cuda.Stream()
     st = stream.cuda_stream
