@@ -241,6 +241,54 @@ __device__ __forceinline__ int shell_of(int64_t M) {
     return b;
 }
 
+// ---- per-cell preparation shared by both K1 kernels ------------------------------------------
+// Lattice-unit moments of the stored state of cell c (gather = 1: one-buffer state after an odd
+// step, where f*_i(x) sits in slot i of x + c_i), in FP32 deviation form as the sweep takes
+// them; rho_f = max(rho, rho_min), u = m / rho_f, p = max(p_ref + (gamma-1)(dE - |m|^2 / (2
+// rho_f)), p_min), T = p / rho_f and mu(T) (constant or Sutherland).  The divisions are the
+// approximate reciprocal-and-multiply (within 2 ulp): u and mu feed FP32 transforms, and the
+// IEEE slow path costs the kernels time and registers.
+template <int S>
+__device__ __forceinline__ void prep_cell(const DomainDev& D, const typename Store<S>::T* __restrict__ fin,
+                                          int gather, const SpectralPlan& P, int64_t c, float& u0, float& u1,
+                                          float& u2, float& mu) {
+    const int nx = 1 << P.lgx, ny = 1 << P.lgy, nz = 1 << P.lgz;
+    int64_t at[NQ] = {c, c, c, c, c, c, c};
+    if (gather) {
+        const int x = (int)(c & (nx - 1));
+        const int y = (int)((c >> P.lgx) & (ny - 1));
+        const int z = (int)(c >> (P.lgx + P.lgy));
+        const int64_t rw = c - x, pl = (int64_t)nx * ny;
+        at[1] = rw + (x == nx - 1 ? 0 : x + 1);
+        at[2] = rw + (x == 0 ? nx - 1 : x - 1);
+        at[3] = c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
+        at[4] = c + (int64_t)((y == 0) ? (ny - 1) : -1) * nx;
+        at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
+        at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
+    }
+    float dQ[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
+        dQ[k] = acc * D.dec[k];
+    }
+    const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);
+    const float irf = __fdividef(1.0f, rf);
+    u0 = dQ[1] * irf;
+    u1 = dQ[2] * irf;
+    u2 = dQ[3] * irf;
+    const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
+    // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
+    const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
+    mu = D.mu_ref;
+    if (D.sutherland) {
+        const float t = (p * irf) * D.inv_T_ref;
+        mu *= __fdividef((1.0f + D.T_S) * t * sqrtf(t), t + D.T_S);
+    }
+}
+
 // ---- K1: prep + forward x ---------------------------------------------------------------------
 // Lattice-unit moments of the stored state in FP32 deviation form (as the sweep takes them),
 // then rho_f = max(rho, rho_min), u = m / rho_f, p = max((gamma-1)(E - |m|^2 / (2 rho_f)),
@@ -260,44 +308,14 @@ __global__ void __launch_bounds__(192, 3) spectral_k1_kernel(const DomainDev D, 
     __shared__ double red[256];
     const T* fin = static_cast<const T*>(fin_v);
     const int64_t N = P.N;
-    const int nx = 1 << P.lgx, ny = 1 << P.lgy, nz = 1 << P.lgz;
     const int64_t groups = (N >> LG) / L;
     double ke = 0.0;
     for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
         const int64_t c0 = g * L * n;
         for (int w = threadIdx.x; w < L * n; w += blockDim.x) {
             const int64_t c = c0 + w;
-            int64_t at[NQ] = {c, c, c, c, c, c, c};
-            if (gather) {
-                const int x = (int)(c & (nx - 1));
-                const int y = (int)((c >> P.lgx) & (ny - 1));
-                const int z = (int)(c >> (P.lgx + P.lgy));
-                const int64_t row = c - x, pl = (int64_t)nx * ny;
-                at[1] = row + (x == nx - 1 ? 0 : x + 1);
-                at[2] = row + (x == 0 ? nx - 1 : x - 1);
-                at[3] = c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
-                at[4] = c + (int64_t)((y == 0) ? (ny - 1) : -1) * nx;
-                at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
-                at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
-            }
-            float dQ[NF];
-#pragma unroll
-            for (int k = 0; k < NF; ++k) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
-                dQ[k] = acc * D.dec[k];
-            }
-            const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);
-            const float u0 = dQ[1] / rf, u1 = dQ[2] / rf, u2 = dQ[3] / rf;
-            const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
-            // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
-            const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
-            float mu = D.mu_ref;
-            if (D.sutherland) {
-                const float t = (p / rf) * D.inv_T_ref;
-                mu *= (1.0f + D.T_S) * t * sqrtf(t) / (t + D.T_S);
-            }
+            float u0, u1, u2, mu;
+            prep_cell<S>(D, fin, gather, P, c, u0, u1, u2, mu);
             mu_out[c] = mu;
             ke += (double)(0.5f * (u0 * u0 + u1 * u1 + u2 * u2));
             const int l = w >> LG, j = w & (n - 1);
@@ -338,7 +356,6 @@ __global__ void __launch_bounds__(128) spectral_k1_row_kernel(const DomainDev D,
     __shared__ double red[256];
     const T* fin = static_cast<const T*>(fin_v);
     const int64_t N = P.N;
-    const int nx = 1 << P.lgx, ny = 1 << P.lgy, nz = 1 << P.lgz;
     const int64_t groups = (N >> LG) / L;
     const int l = threadIdx.x / n2;
     const int q = threadIdx.x % n2;  // also p, the role after the transpose
@@ -350,39 +367,8 @@ __global__ void __launch_bounds__(128) spectral_k1_row_kernel(const DomainDev D,
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int64_t c = row + q + n2 * r;
-            int64_t at[NQ] = {c, c, c, c, c, c, c};
-            if (gather) {
-                const int x = (int)(c & (nx - 1));
-                const int y = (int)((c >> P.lgx) & (ny - 1));
-                const int z = (int)(c >> (P.lgx + P.lgy));
-                const int64_t rw = c - x, pl = (int64_t)nx * ny;
-                at[1] = rw + (x == nx - 1 ? 0 : x + 1);
-                at[2] = rw + (x == 0 ? nx - 1 : x - 1);
-                at[3] = c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx;
-                at[4] = c + (int64_t)((y == 0) ? (ny - 1) : -1) * nx;
-                at[5] = c + ((z == nz - 1) ? -(int64_t)(nz - 1) : 1) * pl;
-                at[6] = c + ((z == 0) ? (int64_t)(nz - 1) : -1) * pl;
-            }
-            float dQ[NF];
-#pragma unroll
-            for (int k = 0; k < NF; ++k) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
-                dQ[k] = acc * D.dec[k];
-            }
-            const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);
-            // approximate division (within 2 ulp): the IEEE slow path costs this kernel time and
-            // registers, and u, mu feed FP32 transforms
-            const float irf = __fdividef(1.0f, rf);
-            const float u0 = dQ[1] * irf, u1 = dQ[2] * irf, u2 = dQ[3] * irf;
-            const float ke_m = 0.5f * (dQ[1] * u0 + dQ[2] * u1 + dQ[3] * u2);
-            const float p = fmaxf(D.p_ref + D.gm1 * (dQ[4] - ke_m), D.p_min);
-            float mu = D.mu_ref;
-            if (D.sutherland) {
-                const float t = (p * irf) * D.inv_T_ref;
-                mu *= __fdividef((1.0f + D.T_S) * t * sqrtf(t), t + D.T_S);
-            }
+            float u0, u1, u2, mu;
+            prep_cell<S>(D, fin, gather, P, c, u0, u1, u2, mu);
             mu_out[c] = mu;
             fke += 0.5f * (u0 * u0 + u1 * u1 + u2 * u2);
             ur[0][r] = u0;
