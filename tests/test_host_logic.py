@@ -1,6 +1,6 @@
-"""Host-side logic of the batching and serving layers, without a GPU: the tile autotuner's size
-classes, plans and table files, the server's per-request parameters and latency summary, and
-the seeded workload generators (batched mix, serving trace) both run on."""
+"""Host-side logic without a GPU: the tile autotuner's size classes, plans and table files, the
+server's per-request parameters and latency summary, the seeded workload generators (batched
+mix, serving trace) both run on, and the test suite's reader of the checkpoint format."""
 import math
 
 import numpy as np
@@ -98,3 +98,50 @@ def test_serving_trace_is_seeded_poisson_and_within_its_ranges():
             assert 400 <= r.case.params.nx <= 4000
         else:
             assert 128 <= r.case.params.nx <= 2048
+
+
+@pytest.mark.parametrize("storage", [inputs.STORE_F32, inputs.STORE_F16, inputs.STORE_BF16])
+def test_checkpoint_decode_reads_the_documented_brick_layout(storage):
+    """decode_populations (used by the population-level GPU parity tests) against a checkpoint
+    body written here from the header's description: ceil(N / 128) bricks of 35 rows x 128
+    cells, element (c // 128) 4480 + 128 q + c % 128, deviations from the reference
+    equilibrium, FP16 deviations times 2^8 / M_k rounded to a power of two."""
+    from tests.common import CI, WI, decode_populations
+    prm = inputs.uniform(10, 7, 3, storage=storage).params  # N = 210: two bricks, ragged
+    N = 210
+    s = prm.dt / prm.dx
+    p_ref = prm.ref_p * s * s
+    E_ref = p_ref / (prm.gamma - 1)
+    rng = np.random.default_rng(3)
+    dev = rng.normal(size=(35, N)) * 1e-2  # deviations d_{k,i}
+    if storage == inputs.STORE_F16:
+        c_ref = math.sqrt(prm.gamma * p_ref / prm.ref_rho)
+        M = [prm.ref_rho, prm.ref_rho * c_ref, prm.ref_rho * c_ref, prm.ref_rho * c_ref, E_ref]
+        enc = [2.0 ** (8 - round(math.log2(m))) for m in M]
+    else:
+        enc = [1.0] * 5
+    stored = np.stack([dev[q] * enc[q // 7] for q in range(35)])
+    dtype = {inputs.STORE_F32: np.float32, inputs.STORE_F16: np.float16}.get(storage)
+    if storage == inputs.STORE_BF16:  # truncate FP32 to its top 16 bits (bfloat16)
+        bits = (stored.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+        stored_exact = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        body_vals = bits
+    else:
+        body_vals = stored.astype(dtype)
+        stored_exact = body_vals.astype(np.float64)
+    nb = 2
+    body = np.zeros((nb, 35, 128), dtype=body_vals.dtype)
+    for c in range(N):
+        body[c // 128, :, c % 128] = body_vals[:, c]
+    raw = np.concatenate([np.zeros(32, np.uint8), body.reshape(-1).view(np.uint8)])
+    f = decode_populations(raw, prm)
+    Qref = [prm.ref_rho, 0, 0, 0, E_ref]
+    for q in range(35):
+        k, i = divmod(q, 7)
+        Jref = np.zeros(3)
+        if 1 <= k <= 3:
+            Jref[k - 1] = p_ref
+        shift = WI[i] * (Qref[k] + 4.0 * CI[i] @ Jref)
+        np.testing.assert_allclose(f[q], stored_exact[q] / enc[k] + shift, rtol=0, atol=1e-15)
+    cells = np.array([0, 127, 128, 209])
+    np.testing.assert_array_equal(decode_populations(raw, prm, cells=cells), f[:, cells])
