@@ -53,7 +53,10 @@ typedef struct {
                                    hold the equilibrium of left_prim / right_prim; y, z
                                    periodic.  PERIODIC: every axis periodic.                 */
     int32_t collision;          /* grlb_collision (Sec. 2.2 BGK, Sec. 2.5 regularized)      */
-    int32_t storage;            /* grlb_storage: population storage type                   */
+    int32_t storage;            /* grlb_storage: population storage type; arithmetic is FP32
+                                   in every mode (FP64 for the diagnostic sums), and with FP16 /
+                                   BF16 storage the collision's four divisions are the
+                                   approximate reciprocal-and-multiply (within 2 ulp)         */
     double dx, dt;              /* physical cell size and time step (> 0)                  */
     double gamma;               /* ratio of specific heats (> 1)                            */
     double mu_ref;              /* dynamic viscosity at T_ref (>= 0)                        */
