@@ -875,12 +875,16 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
     for (size_t i = 0; i < b->doms.size(); ++i) nsolo += (b->active[i] && b->solo[i]) ? 1 : 0;
     if (nsolo > 0) {
         if (!b->fork) GRLB_CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-        while ((int)b->aux.size() < nsolo) {
+        while ((int)b->aux.size() < nsolo) {  // aux[k] and aux_done[k] are created in pairs
             cudaStream_t s;
             cudaEvent_t ev;
             GRLB_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(s);
+                return cuda_fail(e, "cudaEventCreateWithFlags (batch aux stream)");
+            }
             b->aux.push_back(s);
-            GRLB_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
             b->aux_done.push_back(ev);
         }
         GRLB_CU(cudaEventRecord(b->fork, b->stream));
