@@ -389,18 +389,34 @@ grlb_status grlb_stage_primitive(grlb_domain* d, const double* rho, const double
     if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_stage_primitive: NULL argument");
     if (d->stage_count == 2) return fail(GRLB_ESTATE, "both staging slots hold unconsumed states");
     const size_t N = (size_t)d->D.plane;
-    if (!d->copy_stream) {
-        GRLB_CU(cudaStreamCreateWithFlags(&d->copy_stream, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) GRLB_CU(cudaEventCreateWithFlags(&d->staged[i], cudaEventDisableTiming));
+    if (!d->copy_stream) {  // the copy stream and its two events exist together or not at all
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        cudaStream_t cs = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            return cuda_fail(e, "grlb_stage_primitive (copy stream)");
+        }
+        d->staged[0] = ev[0];
+        d->staged[1] = ev[1];
+        d->copy_stream = cs;
     }
     retain_pool();
     const int slot = d->stage_head;
     GRLB_CU(cudaMallocAsync(&d->stage[slot], 5 * N * sizeof(double), d->copy_stream));
     double* st = d->stage[slot];
-    GRLB_CU(cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
-    GRLB_CU(cudaMemcpyAsync(st + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
-    GRLB_CU(cudaMemcpyAsync(st + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream));
-    GRLB_CU(cudaEventRecord(d->staged[slot], d->copy_stream));
+    cudaError_t e = cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(d->staged[slot], d->copy_stream);
+    if (e != cudaSuccess) {  // the slot stays empty; its buffer goes back to the pool
+        cudaFreeAsync(st, d->copy_stream);
+        d->stage[slot] = nullptr;
+        return cuda_fail(e, "grlb_stage_primitive");
+    }
     d->stage_head ^= 1;
     d->stage_count += 1;
     return GRLB_OK;
