@@ -246,9 +246,11 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
  *           Q_ref = (ref_rho, 0, 0, 0, ref_p s^2/(gamma-1))).
  *  stream   cudaStream_t (may be NULL); the call only enqueues work on it.
  * Limits and behaviour: the launch may use at most GRLB_NOALLOC_MAX_BLOCKS CTAs of 128 cells
- * (8,388,608 cells, e.g. 128^3 or 256 x 256 x 128); larger domains return GRLB_EINVAL.  The
- * first call on a device looks up the device address of the static array on that device, so
- * make that first call before any stream capture begins.  Every call on a device shares the
+ * (8,388,608 cells, e.g. 128^3 or 256 x 256 x 128); larger domains return GRLB_EINVAL.  Each
+ * call looks up the device address of the static array on the current device (a lookup that
+ * allocates nothing); the first call on a device, and the first after a device reset, may load
+ * the library's device code for it, so make that call before any stream capture begins.  Every
+ * call on a device shares the
  * one array, which keeps the previous call's contents (each call overwrites every entry it
  * reads, so nothing needs clearing); calls whose sweeps overlap on the GPU race on it, so
  * serialise them (one stream, or events). */

@@ -503,6 +503,13 @@ static grlb_status capture_step_graph(grlb_domain* d) {
     return GRLB_OK;
 }
 
+// The captured sweeps read buf[graph_cur] first; a one-buffer domain's sweeps also depend on
+// the step parity (the AA pattern alternates), a two-buffer domain's do not.
+static bool at_graph_start(const grlb_domain* d) {
+    if (d->P.streaming) return (int)(d->steps & 1) == d->graph_parity;
+    return d->D.cur == d->graph_cur;
+}
+
 grlb_status grlb_step(grlb_domain* d, int nsteps) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
@@ -514,13 +521,14 @@ grlb_status grlb_step(grlb_domain* d, int nsteps) {
                 grlb_status st = capture_step_graph(d);
                 if (st != GRLB_OK) return st;
             }
-            // one plain sweep aligns the buffer and parity with the graph's start
-            if (d->D.cur != d->graph_cur || (int)(d->steps & 1) != d->graph_parity) {
+            // one plain sweep aligns the buffer (two buffers) or the step parity (one buffer,
+            // whose access pattern alternates) with the graph's start
+            if (!at_graph_start(d)) {
                 grlb_status st = sweep_once(d, false);
                 if (st != GRLB_OK) return st;
                 ++n;
             }
-            if (d->D.cur == d->graph_cur && (int)(d->steps & 1) == d->graph_parity) {
+            if (at_graph_start(d)) {
                 for (; n + kStepGraphSweeps <= nsteps; n += kStepGraphSweeps) {
                     GRLB_CU(cudaGraphLaunch(d->step_graph, d->stream));
                     d->steps += kStepGraphSweeps;
@@ -657,6 +665,10 @@ grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
     GRLB_CU(cudaStreamSynchronize(d->stream));
     d->steps = h.steps;
     d->diag_step = -1;
+    if (d->step_graph) {  // captured at another buffer / parity: re-captured at the loaded state
+        cudaGraphExecDestroy(d->step_graph);
+        d->step_graph = nullptr;
+    }
     return GRLB_OK;
 }
 
@@ -968,27 +980,19 @@ static grlb_status batch_table_steps(grlb_batch* b, int nsteps) {
 // in a file-scope static device array instead of scratch from cudaMalloc.
 // =========================================================================================
 namespace {
-constexpr int kNoallocMaxDevices = 64;
 // Block partials followed by the records of the first finalize stage.
 static __device__ __align__(256) double
     g_noalloc_partials[((size_t)GRLB_NOALLOC_MAX_BLOCKS + grlb::kDiagStageRecords) * NDIAG];
-// Device address of g_noalloc_partials per device ordinal (host code cannot use the symbol
-// itself as a device pointer).  Filled once per device by the first call on that device.
-double* g_noalloc_ptr[kNoallocMaxDevices] = {};
-std::mutex g_noalloc_mu;
 
+// Device address of g_noalloc_partials on the current device (host code cannot use the symbol
+// itself as a device pointer).  Looked up on every call: the lookup allocates nothing, and an
+// address kept from an earlier call would be stale after a device reset, which unloads the
+// library's device code (the next lookup loads it again).
 grlb_status noalloc_scratch(double** out) {
-    int dev = 0;
-    GRLB_CU(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(GRLB_EINVAL, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        double* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_partials);
-        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(static diagnostic scratch)");
-        g_noalloc_ptr[dev] = ptr;
-    }
-    *out = g_noalloc_ptr[dev];
+    double* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_partials);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(static diagnostic scratch)");
+    *out = ptr;
     return GRLB_OK;
 }
 }  // namespace

@@ -488,19 +488,23 @@ cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern,
     return cudaErrorInvalidValue;
 }
 
-// Persistent grid of the batched sweep: as many CTAs as can be resident at once (queried once
-// per kernel instantiation), capped by the number of tiles.
+// Persistent grid of the batched sweep: as many CTAs as can be resident at once on the current
+// device (queried once per kernel instantiation and device ordinal), capped by the number of
+// tiles.
 template <typename K>
 static int resident_ctas(K kernel) {
-    static int cached = 0;
-    if (cached == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, 0);
-        cached = (sms > 0 ? sms : 148) * (per > 0 ? per : 4);
-    }
-    return cached;
+    constexpr int kMaxDev = 64;
+    static int cached[kMaxDev] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool slot = dev >= 0 && dev < kMaxDev;
+    if (slot && cached[dev] > 0) return cached[dev];
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, 0);
+    const int n = (sms > 0 ? sms : 148) * (per > 0 ? per : 4);
+    if (slot) cached[dev] = n;
+    return n;
 }
 
 template <int S, int COLL>

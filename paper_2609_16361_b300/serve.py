@@ -207,6 +207,10 @@ class Server:
                     resident[i][2] -= k
                 done = [x for x in resident if x[2] == 0]
                 if done:
+                    # the batch lists these domains and reads their state when destroyed, so it
+                    # goes first; the reader thread closes the domains afterwards
+                    capi.grlb_batch_destroy(batch)
+                    batch = None
                     with lock:
                         state["draining"] += len(done)
                     todo.put((done, ev))

@@ -17,22 +17,36 @@ pytestmark = pytest.mark.gpu
 HDR = 32  # bytes of the grlb_save header before the populations
 
 
-@pytest.mark.parametrize("case", ["tgv32", "ragged"])
-def test_noalloc_diag_sweep_matches_allocating_entry_point_twice(case):
+CASES = {
+    # name: (grid, storage, collision)
+    "tgv32_f32_rlb": ("tgv32", inputs.STORE_F32, inputs.COLL_RLB_SENSOR),
+    "ragged_f32_rlb": ("ragged", inputs.STORE_F32, inputs.COLL_RLB_SENSOR),
+    "tgv32_f16_rlb": ("tgv32", inputs.STORE_F16, inputs.COLL_RLB_SENSOR),
+    "tgv32_bf16_rlb": ("tgv32", inputs.STORE_BF16, inputs.COLL_RLB_SENSOR),
+    "ragged_f32_bgk": ("ragged", inputs.STORE_F32, inputs.COLL_BGK),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_noalloc_diag_sweep_matches_allocating_entry_point_twice(name):
     """tgv32: 256 whole cell bricks; ragged: 40 x 21 x 7 = 5880 cells, 46 bricks, the last one
     partly used (the caller's buffers hold whole bricks; the unused cells are never written,
-    so the output buffer starts zeroed like the library's own)."""
+    so the output buffer starts zeroed like the library's own).  Both entry points run the same
+    kernel on the same record with the same launch shape, so populations and the diagnostic
+    record must agree bit for bit, for every storage type and both collisions."""
     torch = pytest.importorskip("torch")
     assert torch.cuda.is_available()
-    c = inputs.tgv3d(32) if case == "tgv32" else inputs.random_smooth(40, 21, 7, seed=9)
-    prm = c.params
+    grid, storage, collision = CASES[name]
+    c = inputs.tgv3d(32) if grid == "tgv32" else inputs.random_smooth(40, 21, 7, seed=9)
+    prm = c.params.replace(storage=storage, collision=collision)
     N = prm.ncells
+    esize = 4 if storage == inputs.STORE_F32 else 2
     d = capi.Domain(prm)
     d.init(c.rho, c.u, c.p)
     d.step(7)
     torch.cuda.synchronize()
     state = capi.grlb_save(d.h)[HDR:]
-    assert state.size == 35 * 128 * (-(-N // 128)) * 4
+    assert state.size == 35 * 128 * (-(-N // 128)) * esize
     f_a = torch.from_numpy(state.copy()).cuda()
     f_b = torch.zeros_like(f_a)
     diag = torch.zeros(13, dtype=torch.float64, device="cuda")
@@ -45,15 +59,13 @@ def test_noalloc_diag_sweep_matches_allocating_entry_point_twice(case):
         torch.cuda.synchronize()
         d.step_diag()
         want = d.diag()
-        ref_pops = capi.grlb_save(d.h)[HDR:].view(np.float32)
-        got_pops = dst.cpu().numpy().view(np.float32)
-        scale = np.abs(ref_pops).max()
-        assert np.abs(got_pops - ref_pops).max() <= 1e-5 * scale, f"call {call}: populations"
+        ref_pops = capi.grlb_save(d.h)[HDR:]
+        got_pops = dst.cpu().numpy()
+        assert np.array_equal(got_pops, ref_pops), f"call {call}: populations differ"
         g = diag.cpu().numpy()
-        np.testing.assert_allclose(N * Qref + g[:5], want["totals"], rtol=1e-6,
-                                   atol=1e-6 * N * prm.ref_rho)
-        np.testing.assert_allclose(g[5:8], [want["ke"], want["eps_s"], want["eps_d"]], rtol=1e-5)
-        np.testing.assert_allclose(g[8:10], [want["rho_min"], want["p_min"]], rtol=1e-6)
+        np.testing.assert_allclose(N * Qref + g[:5], want["totals"], rtol=1e-15, atol=0)
+        assert list(g[5:10]) == [want["ke"], want["eps_s"], want["eps_d"], want["rho_min"],
+                                 want["p_min"]], f"call {call}: diagnostic sums"
         assert [int(v) for v in g[10:13]] == [want["n_floor"], want["n_nan"], want["n_sensor"]]
         src, dst = dst, src
     d.close()
