@@ -16,7 +16,8 @@
  *    (grlb_read_*, grlb_diag_read, grlb_save) synchronize that stream first.
  *  - Errors: every call returns a grlb_status; on failure grlb_last_error() returns a
  *    thread-local message.  No call aborts the process.  A numeric blow-up is reported by
- *    the diagnostics (n_nan, n_floor), not by the plain sweep.
+ *    the diagnostics (n_nan, n_floor; grlb_diag_read then returns GRLB_ENUMERIC) or by
+ *    grlb_check_finite, not by the plain sweep.
  *  - Lattice units: dx = dt = 1 inside the kernels.  With s = dt/dx: rho unchanged,
  *    u_L = s u, (p, E, T)_L = s^2 (p, E, T), (mu, kappa)_L = (mu, kappa) dt/dx^2.
  */
@@ -35,8 +36,8 @@ typedef enum {
     GRLB_EINVAL = -1,   /* bad argument (null pointer, size, enum, parameter range)      */
     GRLB_ENOMEM = -2,   /* device or host allocation failed                              */
     GRLB_ECUDA = -3,    /* a CUDA runtime call failed; message carries cudaGetErrorString */
-    GRLB_ENUMERIC = -4, /* reserved: no call returns it; a non-finite state shows as
-                           grlb_diag.n_nan > 0 after a diagnostic sweep                  */
+    GRLB_ENUMERIC = -4, /* non-finite state: grlb_diag_read returns it (after filling its
+                           output) when the diagnostic sweep counted n_nan > 0 cells      */
     GRLB_ETIMEOUT = -5, /* reserved: no kernel of the library waits on another           */
     GRLB_ESTATE = -6    /* call not valid in the object's current state                  */
 } grlb_status;
@@ -163,8 +164,22 @@ grlb_status grlb_step(grlb_domain* d, int nsteps);
  * the grlb_diag quantities of the state it lands on into a device-side record, with
  * FP64 block partials summed in a fixed order (bitwise deterministic). */
 grlb_status grlb_step_diag(grlb_domain* d);
-/* Synchronize and copy the record of the last diagnostic sweep to *out. */
+/* Synchronize and copy the record of the last diagnostic sweep to *out.  Returns GRLB_ENUMERIC
+ * (with *out filled in) when that sweep found cells with a non-finite conserved moment
+ * (out->n_nan > 0): the state has blown up and further steps keep it non-finite; GRLB_ESTATE
+ * if no diagnostic sweep ran since the last initialisation. */
 grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out);
+
+/* Failure check without a diagnostic sweep: enqueue on the domain's stream one read-only pass
+ * over the stored populations of the current state (140 bytes per cell in FP32, 70 in FP16 /
+ * BF16; about half a sweep's traffic) that sets *flag = 1 if any stored value is non-finite
+ * (NaN or infinite).  It never writes 0: the caller clears the flag before the check.  flag must
+ * be device-accessible: device memory, or page-locked host memory (with unified addressing its
+ * host pointer is valid on the device), e.g. one slot per domain that a serving loop reads
+ * once the stream has passed the check.  A state the diagnostics would report with
+ * n_nan > 0 always sets the flag (a non-finite moment needs a non-finite population).
+ * Errors: GRLB_EINVAL for NULL arguments; GRLB_ECUDA on launch failure. */
+grlb_status grlb_check_finite(grlb_domain* d, int32_t* flag);
 
 /* Conserved fields in physical units: out[5*N] = planes rho, m_x, m_y, m_z, E. */
 grlb_status grlb_read_conserved(grlb_domain* d, double* out);

@@ -91,6 +91,7 @@ def lib():
             "grlb_set_source_device": ([vp, vp], i32),
             "grlb_step_diag": ([vp], i32),
             "grlb_diag_read": ([vp, C.POINTER(grlb_diag)], i32),
+            "grlb_check_finite": ([vp, vp], i32),
             "grlb_read_conserved": ([vp, dp], i32),
             "grlb_read_primitive": ([vp, dp, dp, dp, dp], i32),
             "grlb_save": ([vp, vp, C.POINTER(sz)], i32),
@@ -123,7 +124,8 @@ def exported_symbols():
             "grlb_device_bytes", "grlb_bytes_for", "grlb_init_primitive",
             "grlb_init_primitive_device", "grlb_stage_primitive", "grlb_init_from_stage",
             "grlb_set_source_device", "grlb_step",
-            "grlb_step_diag", "grlb_diag_read", "grlb_read_conserved", "grlb_read_primitive",
+            "grlb_step_diag", "grlb_diag_read", "grlb_check_finite", "grlb_read_conserved",
+            "grlb_read_primitive",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
@@ -216,10 +218,25 @@ def grlb_step_diag(h):
     check(lib().grlb_step_diag(h))
 
 
-def grlb_diag_read(h) -> dict:
+GRLB_ENUMERIC = -4
+
+
+def grlb_diag_read(h, allow_nonfinite: bool = False) -> dict:
+    """Diagnostics of the last diagnostic sweep.  A non-finite state (n_nan > 0) makes the C
+    call return GRLB_ENUMERIC: raised as GrlbError, or, with allow_nonfinite, the filled-in
+    record is returned."""
     d = grlb_diag()
-    check(lib().grlb_diag_read(h, C.byref(d)))
+    st = lib().grlb_diag_read(h, C.byref(d))
+    if st == GRLB_ENUMERIC and allow_nonfinite:
+        return d.as_dict()
+    check(st)
     return d.as_dict()
+
+
+def grlb_check_finite(h, flag_ptr):
+    """Enqueue the finiteness scan of the current state: sets the int32 at flag_ptr (device or
+    page-locked host memory, as an int) to 1 if a stored population is non-finite."""
+    check(lib().grlb_check_finite(h, flag_ptr))
 
 
 def grlb_read_conserved(h, N, out=None):
@@ -358,8 +375,8 @@ class Domain:
     def step_diag(self):
         grlb_step_diag(self.h)
 
-    def diag(self):
-        return grlb_diag_read(self.h)
+    def diag(self, allow_nonfinite=False):
+        return grlb_diag_read(self.h, allow_nonfinite)
 
     def conserved(self, out=None):
         return grlb_read_conserved(self.h, self.N, out)

@@ -572,6 +572,17 @@ grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out) {
     out->step = d->diag_step;
     out->s = d->s;
     out->ncells = d->D.plane;
+    if (out->n_nan > 0)
+        return fail(GRLB_ENUMERIC, "grlb_diag_read: " + std::to_string(out->n_nan) +
+                                       " cells with a non-finite conserved moment at step " +
+                                       std::to_string(out->step));
+    return GRLB_OK;
+}
+
+grlb_status grlb_check_finite(grlb_domain* d, int32_t* flag) {
+    if (!d || !flag) return fail(GRLB_EINVAL, "grlb_check_finite: NULL argument");
+    const size_t bytes = pop_bytes((size_t)d->D.plane, d->P.storage);
+    GRLB_CU(grlb::launch_check_finite(d->D.buf[d->D.cur], (int64_t)bytes, d->P.storage, flag, d->stream));
     return GRLB_OK;
 }
 

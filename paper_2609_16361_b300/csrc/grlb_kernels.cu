@@ -563,4 +563,36 @@ cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, d
     return cudaGetLastError();
 }
 
+// ---- finiteness scan: one read-only pass over a population buffer ------------------------
+// Stored values are non-finite exactly when their exponent field is all ones (FP32 8 bits,
+// FP16 5 bits, BF16 8 bits); a thread tests 16 bytes per load (4 FP32 or 8 16-bit values), a
+// warp writes *flag = 1 once if any lane saw one.  The buffer holds whole cell bricks (35 x 128
+// elements each), so its size is a multiple of 16 bytes.
+__global__ void __launch_bounds__(256) check_finite_kernel(const uint4* __restrict__ buf, int64_t n16,
+                                                           uint32_t mask_lo, uint32_t mask_hi,
+                                                           int32_t* __restrict__ flag) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldg(buf + i);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            bad = bad || ((w[j] & mask_lo) == mask_lo) || ((w[j] & mask_hi) == mask_hi);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+cudaError_t launch_check_finite(const void* buf, int64_t bytes, int storage, int32_t* flag, cudaStream_t st) {
+    // exponent masks of the value(s) in one 32-bit word: FP32 one value; 16-bit types two
+    uint32_t lo = 0x7f800000u, hi = 0x7f800000u;
+    if (storage == S_F16) { lo = 0x00007c00u; hi = 0x7c000000u; }
+    if (storage == S_BF16) { lo = 0x00007f80u; hi = 0x7f800000u; }
+    const int64_t n16 = bytes / 16;
+    int64_t blocks = (n16 + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    if (blocks < 1) blocks = 1;
+    check_finite_kernel<<<(int)blocks, 256, 0, st>>>(static_cast<const uint4*>(buf), n16, lo, hi, flag);
+    return cudaGetLastError();
+}
+
 }  // namespace grlb

@@ -60,6 +60,9 @@ cudaError_t launch_spectral_k2_to_k5(SpectralPlan& P, const float2* tw, float2* 
 // z-slab ghost exchange (grlb_halo.cu): lower's top interior +z slices -> upper's ghost plane
 // 0; upper's bottom interior -z slices -> lower's top ghost plane (nzl = lower's planes).
 cudaError_t launch_halo_z(void* lower, void* upper, int nzl, int64_t nxy, size_t elem, cudaStream_t st);
+// Writes *flag = 1 (device-accessible) if any stored value of the buffer (bytes, a multiple of
+// 16) is non-finite; never writes 0.
+cudaError_t launch_check_finite(const void* buf, int64_t bytes, int storage, int32_t* flag, cudaStream_t st);
 // FP32 FFMA issue-rate probe: ctas x 256 threads x iters x 128 FFMAs.
 cudaError_t launch_ffma_probe(float* sink, int ctas, int iters, cudaStream_t st);
 }  // namespace grlb

@@ -161,6 +161,33 @@ def sod(nx: int = 400, t_end: float = 0.2, steps: int = 1000, storage: int = STO
     return Case(prm, rho, u, p, dict(t_end=t_end, steps=steps, x=(xi + 0.5) * dx))
 
 
+def double_rarefaction(nx: int = 400, t_end: float = 0.15, steps: int = 750, p_min: float = 0.01,
+                       storage: int = STORE_F32, omega: float = 1.40) -> Case:
+    """Toro's test 2 (two strong rarefactions, near-vacuum star state p* = 0.00189,
+    rho* = 0.0219): (rho, u, p) = (1, -2, 0.4) | (1, 2, 0.4) on [0, 1], diaphragm at x = 0.5,
+    shock-tube settings of Tab. run_params (RLB, omega 1.40, g 20, J_min 3e-3, omega_min 1).
+    The pressure floor p_min (physical units) is raised above p* so that the positivity floor
+    of Alg. 1 acts in the star region.  dt = t_end / steps; 400 cells and 750 steps give
+    dt/dx = 0.08 and max(|u| + c) dt/dx = 0.22."""
+    gamma = 1.4
+    dx = 1.0 / nx
+    dt = t_end / steps
+    left = (1.0, -2.0, 0.0, 0.0, 0.4)
+    right = (1.0, 2.0, 0.0, 0.0, 0.4)
+    xi = np.arange(nx)
+    rho = np.ones(nx)
+    p = np.full(nx, 0.4)
+    u = np.zeros((3, nx))
+    u[0] = np.where(xi < nx // 2, left[1], right[1])
+    prm = CaseParams(nx=nx, ny=1, nz=1, bc=BC_X_DIRICHLET_EQ, collision=COLL_RLB_SENSOR,
+                     storage=storage, dx=dx, dt=dt, gamma=gamma, mu_ref=1e-6, prandtl=0.71,
+                     T_ref=1.0, sutherland=0, omega_rho=omega, omega_mom=omega, omega_E=omega,
+                     omega_min=1.0, sensor_gain=20.0, J_min=3e-3, rho_min=1e-4, p_min=p_min,
+                     ref_rho=0.5, ref_p=0.2, left_prim=left, right_prim=right,
+                     name=f"toro2_{nx}")
+    return Case(prm, rho, u, p, dict(t_end=t_end, steps=steps, x=(xi + 0.5) * dx))
+
+
 def becker_states(mach: float, gamma: float = 1.4):
     """Upstream (rho1=1, c1=1, u1=M) and Rankine-Hugoniot downstream state of a stationary
     normal shock.  Returns ((rho, u, p) upstream, (rho, u, p) downstream)."""

@@ -16,7 +16,14 @@ With one_buffer_large, large requests keep one population buffer (AA pattern: ha
 memory, the same traffic and collisions); small ones stay two-buffer for the batched kernel.
 
 A domain's result does not depend on which other domains share its launches, so every
-request's result is bitwise the same alone and in the mix.  `serial_plain` is the baseline:
+request's result is bitwise the same alone and in the mix.
+
+Failure detection: after every chunk each advanced request's state is scanned for non-finite
+populations (grlb_check_finite, a read-only pass of about half a sweep's traffic, into a
+page-locked flag the host reads once the chunk has run).  A request whose state went non-finite
+is evicted at once -- its memory is released and it is reported with status "nonfinite" --
+while the others continue unchanged (their launches never read another domain's memory).  A
+request that finishes in the chunk where it blew up is caught by its readback instead.  `serial_plain` is the baseline:
 the same trace first-in first-out, one domain at a time, one single-domain launch per step.
 """
 from __future__ import annotations
@@ -41,6 +48,7 @@ class Result:
     admitted: float = 0.0
     finished: float = 0.0
     digest: str = ""
+    status: str = "ok"        # "ok", or "nonfinite" (evicted or read back with NaN / inf)
     totals: np.ndarray = field(default_factory=lambda: np.zeros(5))
     fields: np.ndarray | None = None  # conserved fields, kept only when asked for
 
@@ -54,6 +62,8 @@ def _finish(res: Result, dom: capi.Domain, t0: float, keep: bool):
     res.finished = time.perf_counter() - t0
     res.digest = hashlib.sha256(Q.tobytes()).hexdigest()
     res.totals = Q.sum(axis=1)
+    if not np.isfinite(Q).all():
+        res.status = "nonfinite"
     if keep:
         res.fields = Q
 
@@ -62,7 +72,7 @@ class Server:
     def __init__(self, hbm_budget: float = 150e9, max_resident: int = 512, chunk: int = 200,
                  use_graph: bool = True, tile_table: dict | None = None, stream=None,
                  keep_fields: bool = False, large_cells: int = 262144, srpt: bool = True,
-                 one_buffer_large: bool = False):
+                 one_buffer_large: bool = False, check_finite: bool = True):
         import torch
         self.budget = float(hbm_budget)
         self.max_resident = max_resident
@@ -79,6 +89,8 @@ class Server:
         # large requests with one population buffer (AA pattern): half their memory, same
         # traffic; small ones run in the batched kernel, which needs two buffers
         self.one_buffer_large = one_buffer_large
+        self.check_finite = check_finite  # scan every advanced request after each chunk
+        self.evicted = 0
 
     def run(self, trace, realtime: bool = True, lookahead: int = 12):
         """Serve `trace` (list of inputs.Request sorted by arrival).  Returns Results in
@@ -101,6 +113,7 @@ class Server:
         lock = threading.Lock()
         state = {"used": 0.0, "draining": 0, "error": None}
         inflight = collections.deque()
+        checks = collections.deque()  # (event, page-locked flags, [(slot, resident entry)])
         batch = None
         mask = None
         dirty = True
@@ -114,12 +127,13 @@ class Server:
                 item = todo.get()
                 if item is None:
                     return
-                entries, ev = item
+                entries, ev, failed = item
                 try:
                     rstream.wait_event(ev)
                     for r, dom, _, need, res in entries:
                         capi.grlb_set_stream(dom.h, rstream.cuda_stream)
-                        _finish(res, dom, t0, self.keep_fields)
+                        if not failed:   # evicted requests are not read back
+                            _finish(res, dom, t0, self.keep_fields)
                         dom.close()
                         with lock:
                             results[r.rid] = res
@@ -130,10 +144,40 @@ class Server:
                         state["error"] = e
                         state["draining"] -= len(entries)
 
+        def failed_entries(block: bool):
+            """Resident entries whose finiteness flag is set, from the checks that have run."""
+            bad = []
+            while checks and (block or checks[0][0].query()):
+                cev, flags, entries = checks.popleft()
+                cev.synchronize()
+                f = flags.numpy()
+                for slot, x in entries:
+                    if f[slot] and any(y is x for y in resident) and not any(y is x for y in bad):
+                        bad.append(x)
+            return bad
+
         worker = threading.Thread(target=reader, daemon=True)
         worker.start()
         try:
             while True:
+                bad = failed_entries(block=False)
+                if bad:
+                    # the batch lists the failed domains: destroy it before they are released;
+                    # their memory is freed after everything already enqueued that touches them
+                    if batch is not None:
+                        capi.grlb_batch_destroy(batch)
+                        batch = None
+                    fev = torch.cuda.Event()
+                    fev.record(self.stream)
+                    for x in bad:
+                        x[4].status = "nonfinite"
+                        x[4].finished = now()
+                    resident = [x for x in resident if not any(x is y for y in bad)]
+                    self.evicted += len(bad)
+                    with lock:
+                        state["draining"] += len(bad)
+                    todo.put((bad, fev, True))
+                    dirty = True
                 with lock:
                     if state["error"] is not None:
                         raise state["error"]
@@ -200,9 +244,16 @@ class Server:
                 k = min(self.chunk, min(resident[i][2] for i in pick))
                 capi.grlb_batch_step(batch, k)
                 self.launch_steps += k
+                flags = None
+                if self.check_finite:
+                    flags = torch.zeros(len(resident), dtype=torch.int32, pin_memory=True)
+                    for i in pick:
+                        capi.grlb_check_finite(resident[i][1].h, flags.data_ptr() + 4 * i)
                 ev = torch.cuda.Event()
                 ev.record(self.stream)
                 inflight.append(ev)
+                if flags is not None:
+                    checks.append((ev, flags, [(i, resident[i]) for i in pick]))
                 for i in pick:
                     resident[i][2] -= k
                 done = [x for x in resident if x[2] == 0]
@@ -213,7 +264,7 @@ class Server:
                     batch = None
                     with lock:
                         state["draining"] += len(done)
-                    todo.put((done, ev))
+                    todo.put((done, ev, False))
                     resident = [x for x in resident if x[2] > 0]
                     dirty = True
                 while len(inflight) > lookahead:
@@ -263,6 +314,8 @@ def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = 
 
 
 def summarize(results, t_span: float | None = None) -> dict:
+    """Throughput and latency over all requests (a failed request counts with the time it was
+    reported); `failed` counts the requests with a non-finite state."""
     lat = np.array([r.latency for r in results])
     span = t_span if t_span is not None else max(r.finished for r in results) - min(
         r.arrival for r in results)
@@ -271,4 +324,4 @@ def summarize(results, t_span: float | None = None) -> dict:
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_latency_s": float(lat.mean()), "span_s": span,
-            "mlups": cells / span / 1e6}
+            "mlups": cells / span / 1e6, "failed": sum(r.status != "ok" for r in results)}

@@ -24,10 +24,10 @@ def rel_l1(Q, R):
     return np.abs(Q - R).sum(axis=1) / den
 
 
-def run_oracle(case, steps, keep_cells=False):
+def run_oracle(case, steps, keep_cells=False, ce_init=False):
     import oracle
     o = oracle.Oracle(case.params)
-    o.init_primitive(case.rho, case.u, case.p)
+    o.init_primitive(case.rho, case.u, case.p, ce_init=ce_init)
     o.step(steps, keep_cells=keep_cells)
     return o
 

@@ -27,6 +27,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         alone = serve.Server(chunk=16).run([r], realtime=False)[0]
         assert m.rid == r.rid == alone.rid == p.rid
         assert m.digest == alone.digest, f"request {r.rid} ({r.kind}) differs in the mix"
+        assert m.status == alone.status == p.status == "ok"
         err = rel_linf(m.fields, p.fields)
         tol = 1e-6 if r.storage == inputs.STORE_F32 else 1e-2
         assert np.all(err <= tol), (r.rid, r.kind, r.storage, err)
