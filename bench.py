@@ -38,6 +38,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SWEEPS_PER_STEP = 50
+# collision readings: name -> (grlb_collision, kernel label)
+COLLISIONS = {"rlb": (1, "RLB"), "gated": (2, "RLB_GATED"), "bgk": (0, "BGK")}
 BYTES_PER_LUP = {0: 280, 1: 140, 2: 140}
 KERNEL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh",
                   "paper_2609_16361_b300/csrc/grlb_kernels.cu"]
@@ -248,7 +250,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     n = args.n
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
-    case = inputs.tgv3d(n, storage=storage)
+    coll, coll_label = COLLISIONS[args.collision]
+    case = inputs.tgv3d(n, storage=storage, collision=coll)
     N = case.params.ncells
     dev = torch.device("cuda", local)
     rho_d = torch.from_numpy(case.rho).to(dev)
@@ -322,6 +325,19 @@ def run_ours(args):
         te = time.perf_counter() - te0
         barrier()
 
+        # ---- diagnostics of the same flow after a Chapman-Enskog start (outside the timed
+        # region): with omega -> 2 the equilibrium start of the timed steps leaves a
+        # non-equilibrium part that flips sign every step, so the cell-local dissipation of
+        # their diagnostic sweep is not the flow's; this start carries the gradients from step 0
+        capi.grlb_set_init_mode(h, 1)
+        capi.grlb_init_primitive_device(h, rho_d.data_ptr(), u_d.data_ptr(), p_d.data_ptr())
+        capi.grlb_step(h, SWEEPS_PER_STEP - 1)
+        capi.grlb_step_diag(h)
+        ce_diag = dom.diag(allow_nonfinite=True)
+        _, ce_spec = dom.spectral(nbins=0) if ce_diag["n_nan"] == 0 else (None, None)
+        capi.grlb_set_init_mode(h, 0)
+        stream.synchronize()
+
     # max over ranks
     ms, te, sweep_med = reduce_max_over_ranks([ms, te, float(np.median(sweep_ms))], ws, dev)
     ms_per_step = ms / args.steps
@@ -334,7 +350,7 @@ def run_ours(args):
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         t = json.load(open(TRAFFIC_FILE))
-        rec = t.get(f"tgv{n}_{args.storage}")
+        rec = t.get(f"tgv{n}_{args.storage}" + ("" if args.collision == "rlb" else f"_{args.collision}"))
         if rec and rec.get("source_sha") == kernel_source_sha():
             traffic = rec.get("dram_bytes_per_launch")
 
@@ -359,7 +375,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {0: "f32", 1: "f16-storage/f32", 2: "bf16-storage/f32"}[storage],
             "data": "synthetic",
-            "config": {"workload": f"tgv{n}_{args.storage}_rlb_sensor", "grid": [n, n, n],
+            "config": {"workload": f"tgv{n}_{args.storage}_{args.collision}", "grid": [n, n, n],
                        "mach": 1.25, "re": 1600, "sweeps_per_step": SWEEPS_PER_STEP,
                        "step": "init kernel + 49 sweeps + 1 diagnostic sweep (FP64 reductions)",
                        "parallelism": f"replicas{ws}",
@@ -370,21 +386,176 @@ def run_ours(args):
             "gpu_launches": args.steps * (SWEEPS_PER_STEP + 3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"sweep_kernel<{args.storage},RLB> (plain sweep)",
+                         "kernel": f"sweep_kernel<{args.storage},{coll_label}> (plain sweep)",
                          "bytes_per_launch": bpl * N, "launch_ms_median": sweep_med,
                          "peak_source": f"{peak_src} hbm_gbs"},
             "issue_ceiling": issue,
             "ffma_probe": {"warp_inst_per_s": rate, "fp32_tflops": 64.0 * rate / 1e12},
             "clocks": clocks,
             "cpu_baseline": cpu,
-            "diag_at_end": {"n_nan": diag["n_nan"], "n_sensor": diag["n_sensor"],
-                            "ke": diag["ke"], "step": diag["step"]},
+            "diag_timed_step": {"n_nan": diag["n_nan"], "n_sensor": diag["n_sensor"],
+                                "ke": diag["ke"], "step": diag["step"],
+                                "note": "equilibrium start: cell-local dissipation alternates "
+                                        "with the non-equilibrium part at omega -> 2"},
+            "diag_ce_start": diag_record(ce_diag, ce_spec, case),
         }
+        if rank == 0 and not args.no_legs:
+            line["batched"] = batched_leg(args)
+            line["served"] = served_leg(args)
         print(json.dumps(line), flush=True)
     dom.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_zslab(args):
+    """One periodic domain split along z over the ranks (one device each): every rank owns one
+    z-period of the n^3 Taylor-Green vortex, so N ranks advance an n x n x (n N) domain (weak
+    scaling), exchanging the ghost slices of their slabs with their neighbours before every
+    sweep (decomp.SlabRank: pack kernel, NCCL send / receive, unpack kernel).  A bench step =
+    initialisation from device-resident fields + 50 exchange-and-sweep iterations; value =
+    the interior cell updates of all ranks over the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    from paper_2609_16361_b300 import decomp, inputs
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    part = decomp.slab_case(inputs.tgv3d(n), 0, n)   # this rank's period, ghost planes wrapped
+    stream = torch.cuda.Stream()
+    r = decomp.SlabRank(None, rank, ws, stream=stream, part=part)
+    dev = torch.device("cuda", local)
+    rho_d = torch.from_numpy(part.rho).to(dev)
+    u_d = torch.from_numpy(part.u).to(dev).contiguous()
+    p_d = torch.from_numpy(part.p).to(dev)
+
+    def one_step():
+        r.init_device(rho_d, u_d, p_d)
+        r.step(SWEEPS_PER_STEP)
+
+    for _ in range(args.warmup):
+        one_step()
+    stream.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = reduce_max_over_ranks([e0.elapsed_time(e1)], ws, dev)[0]
+    cells = n ** 3
+    Q = r.conserved_interior()
+    finite = bool(__import__("numpy").isfinite(Q).all())
+    r.close()
+    if rank == 0:
+        line = {"metric": "MLUP/s", "value": job_mlups(ws, cells, SWEEPS_PER_STEP * args.steps, ms / 1e3),
+                "unit": "MLUP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"tgv{n}_f32_rlb z-period per rank: {n}x{n}x{n * ws} periodic domain",
+                           "parallelism": f"zslab{ws}", "sweeps_per_step": SWEEPS_PER_STEP,
+                           "step": "init kernel + 50 x (ghost pack, NCCL send/recv to both z "
+                                   "neighbours, unpack, sweep)",
+                           "halo_bytes_per_sweep_per_rank": 2 * 5 * n * n * 4,
+                           "l2": "inputs larger than L2, no flush"},
+                "gpu_launches": args.steps * (1 + 3 * SWEEPS_PER_STEP),
+                "clocks": clk.summary(), "finite_after_run": finite}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def diag_record(g, spec, case):
+    """FP64 diagnostics of a diagnostic sweep in physical units (volume averages normalised by
+    rho0 V0^2 and rho0 V0^3 / L0), with the spectral dissipation of the same state."""
+    prm = case.params
+    N = prm.ncells
+    s = prm.dt / prm.dx
+    unit = prm.dx ** 2 / prm.dt ** 3 / N
+    out = {"step": g["step"], "t_c": g["step"] * prm.dt, "n_nan": g["n_nan"],
+           "n_sensor": g["n_sensor"], "n_floor": g["n_floor"], "E_k": g["ke"] / (s * s) / N,
+           "eps_s": g["eps_s"] * unit, "eps_d": g["eps_d"] * unit}
+    if spec is not None:
+        out["eps_s_spectral"] = spec["eps_s"] * unit
+        out["eps_d_spectral"] = spec["eps_d"] * unit
+        out["eps_s_cell_over_spectral"] = out["eps_s"] / out["eps_s_spectral"]
+    return out
+
+
+def batched_leg(args, steps=200):
+    """Short batched leg of the default line: the 64-domain seed-0 mix (48 Becker tubes + 16
+    Taylor-Green boxes), `steps` steps in one batch (constant-table batched sweep, CUDA-graph
+    step loop, default tiles) against the same domains advanced one after another with one
+    launch per sweep (legacy stream: grlb_step replays no graph there)."""
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    stream = torch.cuda.Stream()
+    st = stream.cuda_stream
+    cases = inputs.batched_mix(0)
+    cells = sum(c.params.ncells for c in cases)
+    doms = [capi.Domain(c.params, stream=st) for c in cases]
+    for d, c in zip(doms, cases):
+        d.init(c.rho, c.u, c.p)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
+    capi.grlb_batch_set_stream(b, st)
+    capi.grlb_batch_step(b, 4)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    capi.grlb_batch_step(b, steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    capi.grlb_batch_destroy(b)
+    legacy = torch.cuda.default_stream()
+    for d, c in zip(doms, cases):
+        capi.grlb_set_stream(d.h, legacy.cuda_stream)
+        d.init(c.rho, c.u, c.p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(legacy)
+    for d in doms:
+        d.step(steps)
+    e1.record(legacy)
+    e1.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    for d in doms:
+        d.close()
+    mb, mp = cells * steps / t_batch / 1e6, cells * steps / t_plain / 1e6
+    return {"metric": "batched MLUP/s", "value": mb, "unit": "MLUP/s",
+            "sequential_plain_mlups": mp, "vs_sequential_plain": mb / mp,
+            "workload": "64 uneven domains (48 Becker 128-2048 x 4 x 4, 16 Taylor-Green 32^3-96^3 "
+                        "Re 100), seed 0", "cells": cells, "steps": steps}
+
+
+def served_leg(args, n_requests=40, rate=20.0):
+    """Short serving leg of the default line: the seed-0 trace of `n_requests` Poisson
+    arrivals at `rate`/s served with continuous batching, against the same trace served first
+    in, first out, one domain at a time through grlb_step."""
+    from paper_2609_16361_b300 import inputs, serve
+    trace = inputs.serving_trace(0, n_requests=n_requests, rate=rate)
+    res = serve.Server(hbm_budget=150e9, chunk=200).run(trace, realtime=True)
+    sb = serve.summarize(res)
+    sp = serve.summarize(serve.serial_plain(trace, realtime=True))
+    keep = ("solves_per_s", "p50_latency_s", "p99_latency_s", "mean_latency_s", "mlups", "failed")
+    return {"metric": "served solves/s", "value": sb["solves_per_s"], "unit": "solves/s",
+            **{k: sb[k] for k in keep if k != "solves_per_s"},
+            "serial_plain": {k: sp[k] for k in keep},
+            "vs_serial_plain": sb["solves_per_s"] / sp["solves_per_s"],
+            "p99_vs_serial_plain": sb["p99_latency_s"] / sp["p99_latency_s"],
+            "workload": f"Poisson {rate:g}/s, {n_requests} requests (Sod / Becker tubes, Taylor-Green "
+                        "64^3-192^3 Re 100, FP32 or FP16, 500-5000 steps), seed 0, 150 GB budget"}
 
 
 # ----------------------------------------------------------------------------------------
@@ -430,6 +601,28 @@ def run_batch(args):
         t = e0.elapsed_time(e1) / 1e3
         capi.grlb_batch_destroy(b)
         out[label] = {"mlups": cells * steps / t / 1e6, "seconds": t}
+    # the tube class alone (48 Becker tubes, all in the batched kernel): the two ways of
+    # reading the domain records, against the HBM roofline (280 B per cell update)
+    tubes = [i for i, c in enumerate(cases) if c.params.name.startswith("becker")]
+    tcells = sum(cases[i].params.ncells for i in tubes)
+    peak, _ = measured_peaks()
+    for label, mode in (("tubes_constant_records", 0), ("tubes_table_records", 1)):
+        for i in tubes:
+            doms[i].init(cases[i].rho, cases[i].u, cases[i].p)
+        b = capi.grlb_batch_create([doms[i].h for i in tubes], use_graph=1, record_mode=mode)
+        capi.grlb_batch_set_stream(b, st)
+        capi.grlb_batch_step(b, 4)
+        stream.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        capi.grlb_batch_step(b, steps)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        capi.grlb_batch_destroy(b)
+        gbs = 280 * tcells * steps / t / 1e9
+        out[label] = {"mlups": tcells * steps / t / 1e6, "seconds": t, "cells": tcells,
+                      "achieved_gbs": gbs, "roofline_frac": gbs / peak}
     legacy = torch.cuda.default_stream()
     for label, s_run in (("sequential_plain", legacy), ("sequential_graph_replay", stream)):
         for d, c in zip(doms, cases):
@@ -500,9 +693,11 @@ def run_serve(args):
 
 def run_precision(args):
     """Storage precision modes side by side: FP32, FP16 and BF16 shifted populations (FP32
-    arithmetic).  Accuracy: Taylor-Green 64^3 after 100 steps and the Sod tube (400 cells, 1000
-    steps) against the FP64 oracle, relative L-inf / L1 of rho, u, T.  Speed: the plain sweep
-    at 256^3 (CUDA events, 40 sweeps after warm-up) against the HBM roofline of each mode."""
+    arithmetic).  Accuracy against the FP64 oracle, relative L-inf / L1 of rho, u, T:
+    Taylor-Green 64^3 after 100 steps, the Sod tube (400 cells, 1000 steps), and the supersonic
+    Taylor-Green vortex at --prec-n^3 after --prec-steps steps (the precision study of the
+    storage modes; the collision of --collision, Chapman-Enskog start).  Speed: the plain sweep at 256^3 (CUDA
+    events, 40 sweeps after warm-up) against the HBM roofline of each mode."""
     import numpy as np
     import torch
     import oracle
@@ -539,23 +734,52 @@ def run_precision(args):
             d.step(nsteps)
             acc.setdefault(names[st], {})[cname] = errs(prim(d.conserved(), c.params.gamma), R)
             d.close()
-    # the 256^3 Taylor-Green after 2000 steps in each storage mode; at Re 1600 the case stops
-    # being finite after ~350 steps (the regularized-collision instability near omega = 2), so
-    # the comparison runs at Re 100 with the 128^3 rate setting (f_mu 0.9, omega 1.55), and
-    # the 16-bit modes are measured against FP32 storage (the FP64 oracle would need ~1.5 h for
-    # 2000 steps at 256^3; FP32 storage is pinned to it at 1e-5 on the cases above)
-    long_steps = 2000
+    # Storage modes against the FP64 oracle on a long run: the supersonic Taylor-Green vortex at
+    # --prec-n^3 (default 128^3: the largest size the oracle finishes in ~15 min on the host
+    # cores) after --prec-steps steps (default 2000) in each storage mode.  The oracle runs in
+    # a thread (its C stepper releases the GIL) while the device runs the three modes.
+    long_steps = args.prec_steps
+    pn = args.prec_n
+    coll = COLLISIONS[args.collision][0]
+    def mk_long(st):
+        c = inputs.tgv3d(pn, re=args.prec_re, storage=st, collision=coll)
+        if args.omega_min is not None:
+            c.params = c.params.replace(omega_min=args.omega_min)
+        return c
+
+    ref = mk_long(0)
+    orc = {}
+
+    def oracle_run():
+        try:
+            o = oracle.Oracle(ref.params)
+            o.init_primitive(ref.rho, ref.u, ref.p, ce_init=True)
+            t0 = time.perf_counter()
+            o.step(long_steps)
+            orc["seconds"] = time.perf_counter() - t0
+            orc["Q"] = o.conserved()
+        except RuntimeError as e:   # a non-finite state makes the reconstruction singular
+            orc["error"] = str(e)
+
+    th = threading.Thread(target=oracle_run)
+    th.start()
     fields = {}
     for st in (0, 1, 2):
-        c = inputs.tgv3d(args.n, re=100.0, fmu=0.9, storage=st)
+        c = mk_long(st)
         d = capi.Domain(c.params)
-        d.init(c.rho, c.u, c.p)
+        d.init(c.rho, c.u, c.p, ce_init=True)
         d.step(long_steps)
         fields[st] = prim(d.conserved(), c.params.gamma)
         d.close()
     finite = {names[st]: bool(all(np.isfinite(a).all() for a in fields[st])) for st in (0, 1, 2)}
+    th.join()
+    long_key = f"tgv{pn}_re{args.prec_re:g}_{args.collision}_{long_steps}_vs_oracle"
+    if "Q" in orc and np.isfinite(orc["Q"]).all():
+        R = prim(orc["Q"], ref.params.gamma)
+        for st in (0, 1, 2):
+            acc.setdefault(names[st], {})[long_key] = errs(fields[st], R)
     for st in (1, 2):
-        acc.setdefault(names[st], {})[f"tgv{args.n}_re100_{long_steps}_vs_f32"] = errs(fields[st], fields[0])
+        acc.setdefault(names[st], {})[f"tgv{pn}_re{args.prec_re:g}_{long_steps}_vs_f32"] = errs(fields[st], fields[0])
     del fields
     speed = {}
     peak, src = measured_peaks()
@@ -581,8 +805,12 @@ def run_precision(args):
             "value": speed["f16"]["mlups"], "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32 / f16 / bf16 storage, f32 arithmetic", "data": "synthetic",
             "config": {"workload": f"tgv{args.n} sweep speed; tgv64 x100 and sod400 x1000 accuracy "
-                                   f"vs the FP64 oracle; tgv{args.n} Re 100 x{long_steps} 16-bit vs FP32",
-                       "peak_gbs": peak, "peak_source": src},
+                                   f"vs the FP64 oracle; tgv{pn} Re {args.prec_re:g} ({args.collision} "
+                                   f"collision, omega_min {ref.params.omega_min:g}, Chapman-Enskog "
+                                   f"start) x{long_steps} vs the FP64 oracle",
+                       "peak_gbs": peak, "peak_source": src,
+                       "oracle_seconds": orc.get("seconds"), "oracle_threads": oracle.num_threads(),
+                       "oracle_error": orc.get("error")},
             "finite_after_long_run": finite, "accuracy": acc, "speed": speed}
     print(json.dumps(line), flush=True)
     return 0
@@ -596,7 +824,9 @@ def run_tgv_series(args):
     import torch
     from paper_2609_16361_b300 import capi, inputs
     torch.cuda.set_device(0)
-    c = inputs.tgv3d(args.n)
+    c = inputs.tgv3d(args.n, collision=COLLISIONS[args.collision][0])
+    if args.omega_min is not None:
+        c.params = c.params.replace(omega_min=args.omega_min)
     prm = c.params
     N = prm.ncells
     d = capi.Domain(prm)
@@ -634,14 +864,67 @@ def run_tgv_series(args):
     line = {"metric": "Taylor-Green run with FP64 diagnostics every 50 steps", "unit": "MLUP/s",
             "value": N * step / wall / 1e6, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"tgv{args.n}_f32_rlb_sensor", "steps_requested": args.run_steps,
-                       "omega": prm.omega_mom, "fmu": c.meta["fmu"],
+            "config": {"workload": f"tgv{args.n}_f32_{args.collision}", "steps_requested": args.run_steps,
+                       "omega": prm.omega_mom, "fmu": c.meta["fmu"], "omega_min": prm.omega_min,
                        "start": "chapman-enskog" if args.ce_init else "equilibrium"},
             "spectral": "eps_*_spectral: spectral derivatives of u = m / rho on the state the "
                         "step landed on; spectrum: shell sums of 1/2 |u^|^2 / N^2 in units of V0^2, "
                         "every 200 steps",
             "steps_run": step, "first_nonfinite_step": first_bad, "wall_s": wall,
             "series": series}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tgv_map(args):
+    """Stability map of the supersonic Taylor-Green vortex (M0 1.25, Re 1600, Sutherland, FP32,
+    Chapman-Enskog start) over the collision reading, the background damping f_mu and the
+    sensor floor rate omega_min: each run goes up to --run-steps steps with FP64 diagnostics
+    every 50 steps and reports how far it stays finite (step, t_c) and its kinetic energy at
+    t_c 2, 4, 8, 12, 16, 20.  The paper's setting (Tab. run_params, Sec. 3.4) is f_mu of the
+    resolution (0.9 at 128^3) with omega_min 1.987."""
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    n = args.n
+    rows = []
+    marks = (2.0, 4.0, 8.0, 12.0, 16.0, 20.0)
+    base_fmu = inputs.fmu_for_resolution(n)
+    for coll in ("rlb", "gated"):
+        for fmu_scale in (1.0, 2.0, 4.0):
+            for om_min in (1.987, 1.95, 1.9, 1.8, 1.5):
+                c = inputs.tgv3d(n, collision=COLLISIONS[coll][0], fmu=base_fmu * fmu_scale)
+                prm = c.params.replace(omega_min=om_min)
+                d = capi.Domain(prm)
+                d.init(c.rho, c.u, c.p, ce_init=True)
+                s = prm.dt / prm.dx
+                step, last_ok, ek_at, sensor_max = 0, 0, {}, 0
+                while step < args.run_steps:
+                    d.step(49)
+                    d.step_diag()
+                    g = d.diag(allow_nonfinite=True)
+                    step = g["step"]
+                    ke = g["ke"] / (s * s) / prm.ncells
+                    if g["n_nan"] > 0 or not math.isfinite(ke):
+                        break
+                    last_ok = step
+                    sensor_max = max(sensor_max, g["n_sensor"])
+                    tc = step * prm.dt
+                    for m in marks:
+                        if m not in ek_at and tc >= m:
+                            ek_at[m] = ke
+                d.close()
+                rows.append({"collision": coll, "fmu": base_fmu * fmu_scale, "omega": prm.omega_mom,
+                             "omega_min": om_min, "last_finite_step": last_ok,
+                             "last_finite_t_c": last_ok * prm.dt, "finite_to_end": last_ok >= args.run_steps,
+                             "E_k_at_t_c": {f"{m:g}": v for m, v in ek_at.items()},
+                             "max_sensor_cells": sensor_max})
+    line = {"metric": "Taylor-Green stability map (steps finite)", "unit": "steps",
+            "value": max(r["last_finite_step"] for r in rows), "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"tgv{n} M0 1.25 Re 1600, collision x f_mu x omega_min",
+                       "steps_requested": args.run_steps, "paper_setting": {"fmu": base_fmu, "omega_min": 1.987}},
+            "runs": rows}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -889,13 +1172,25 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parallelism", default="replicas", choices=["replicas", "zslab"],
+                    help="N > 1: independent replica domains, or one domain split along z over the ranks")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="leave the batched and served legs out of the default line")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
-                             "capacity", "spectral", "slabs", "cases"])
+                             "tgv-map", "capacity", "spectral", "slabs", "cases"])
     ap.add_argument("--run-steps", type=int, default=5000)
+    ap.add_argument("--prec-n", type=int, default=128, help="precision: grid of the long comparison")
+    ap.add_argument("--prec-steps", type=int, default=2000, help="precision: steps of the long comparison")
+    ap.add_argument("--prec-re", type=float, default=1600.0, help="precision: Reynolds number of the long run")
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--ce-init", action="store_true", help="tgv-series: Chapman-Enskog start")
+    ap.add_argument("--omega-min", type=float, default=None,
+                    help="Taylor-Green workloads: sensor floor rate (default: the paper's 1.987)")
+    ap.add_argument("--collision", default="rlb", choices=list(COLLISIONS),
+                    help="rlb: regularized collision in every cell (Alg. 1); gated: regularized "
+                         "where the sensor fires, BGK elsewhere; bgk")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -909,6 +1204,8 @@ def main():
         return run_precision(args)
     if args.workload == "tgv-series":
         return run_tgv_series(args)
+    if args.workload == "tgv-map":
+        return run_tgv_map(args)
     if args.workload == "spectral":
         return run_spectral(args)
     if args.workload == "slabs":
@@ -917,6 +1214,8 @@ def main():
         return run_cases(args)
     if args.workload == "capacity":
         return run_capacity(args)
+    if args.parallelism == "zslab":
+        return run_zslab(args)
     return run_ours(args)
 
 

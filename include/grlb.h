@@ -43,7 +43,13 @@ typedef enum {
 } grlb_status;
 
 typedef enum { GRLB_BC_PERIODIC = 0, GRLB_BC_X_DIRICHLET_EQ = 1 } grlb_bc;
-typedef enum { GRLB_COLL_BGK = 0, GRLB_COLL_RLB_SENSOR = 1 } grlb_collision;
+/* Collision operators.  BGK: f* = f + omega_k (f^eq - f) (Sec. 2.2).  RLB_SENSOR: the
+ * regularized collision of Sec. 2.5 / Algorithm 1 in every cell: f* = f^eq + (1 - omega_h) r,
+ * r the first-moment part of f - f^eq, omega_h = omega_k - chi max(omega_k - omega_min, 0).
+ * RLB_GATED: the reading of Sec. 2.2 in which the compression sensor activates the regularized
+ * collision in place of BGK: the RLB_SENSOR update where chi > 0, BGK at the nominal omega_k
+ * where chi = 0 (the sensor, reconstruction and flux are those of RLB_SENSOR). */
+typedef enum { GRLB_COLL_BGK = 0, GRLB_COLL_RLB_SENSOR = 1, GRLB_COLL_RLB_GATED = 2 } grlb_collision;
 typedef enum { GRLB_STORE_F32 = 0, GRLB_STORE_F16 = 1, GRLB_STORE_BF16 = 2 } grlb_storage;
 
 /* Physical description of one domain (Sec. 2.1 system, Listing 1 closures, Listing 2
@@ -53,7 +59,8 @@ typedef struct {
     int32_t bc;                 /* grlb_bc.  X_DIRICHLET_EQ: ghost cells at x=-1 and x=nx
                                    hold the equilibrium of left_prim / right_prim; y, z
                                    periodic.  PERIODIC: every axis periodic.                 */
-    int32_t collision;          /* grlb_collision (Sec. 2.2 BGK, Sec. 2.5 regularized)      */
+    int32_t collision;          /* grlb_collision (Sec. 2.2 BGK, Sec. 2.5 regularized, or
+                                   the sensor-gated pair of the two)                        */
     int32_t storage;            /* grlb_storage: population storage type; arithmetic is FP32
                                    in every mode (FP64 for the diagnostic sums), and with FP16 /
                                    BF16 storage the collision's four divisions are the
@@ -218,7 +225,11 @@ typedef struct {
                                domains with fewer cells along x)                             */
     int32_t solo_min_cells; /* 0 = 262144 (64^3); < 0: every domain goes through the table  */
     int32_t use_graph;      /* 1: replay the table launches of two steps from a CUDA graph  */
-    int32_t pad0;
+    int32_t record_mode;    /* 0: the small domains' records in a constant table of 160 slots
+                               shared by the process (one CTA per tile, constants read through
+                               the constant cache), or, if too few slots are free, as 1;
+                               1: records in device memory, copied to shared memory by a
+                               persistent kernel walking a tile table                        */
 } grlb_batch_config;
 
 grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_batch_config* cfg,
@@ -309,6 +320,23 @@ grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init);
  * Errors: GRLB_EINVAL for NULL domains, slabs that differ in nx, ny or storage, one-buffer
  * streaming, non-periodic slabs, nz < 3, or different streams; GRLB_ECUDA on launch failure. */
 grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upper);
+
+/* The same exchange between slabs on different devices (one slab per rank of a multi-device
+ * run): before every step each slab packs its two outgoing slices, the ranks swap them (e.g.
+ * NCCL send / receive of device buffers, on the domain's stream order), and each slab unpacks
+ * what it received.  Slices hold 5 x nx x ny stored values of the storage type (raw equilibrium-
+ * shift deviations, FP16 scaled), field-major (rho, m_x, m_y, m_z, E), x fastest within a field.
+ *  grlb_halo_pack_z:   to_upper <- the +z populations of the top interior plane (z = nz - 2),
+ *                      to_lower <- the -z populations of the bottom interior plane (z = 1).
+ *  grlb_halo_unpack_z: ghost plane z = 0 (+z populations) <- from_lower (the lower neighbour's
+ *                      to_upper), ghost plane z = nz - 1 (-z populations) <- from_upper.
+ * All buffers are device memory of the domain's device, 5 nx ny elements each, owned by the
+ * caller; both calls only enqueue on the domain's stream.  A slab that is its own neighbour (one
+ * rank, periodic) unpacks its own packed slices: the slab then evolves as the periodic domain.
+ * Errors: GRLB_EINVAL for NULL arguments, one-buffer streaming, a non-periodic domain or
+ * nz < 3; GRLB_ECUDA on launch failure. */
+grlb_status grlb_halo_pack_z(grlb_domain* d, void* to_upper, void* to_lower);
+grlb_status grlb_halo_unpack_z(grlb_domain* d, const void* from_lower, const void* from_upper);
 
 /* ---- spectral post-processing (Sec. 3.4) ------------------------------------------------
  * The paper evaluates the Taylor-Green dissipation spectrally and shows the shell-averaged

@@ -21,7 +21,9 @@
  *   chain rule to grad u, grad T (Sec. 2.4), compression sensor chi (Sec. 2.5 /
  *   Listing 2), Newtonian stress and Fourier flux (Eq. system), linear equilibrium with the
  *   full flux in its first moment (Sec. 2.2), regularized collision with reduced rate
- *   (Sec. 2.5) or BGK (Sec. 2.2), exact streaming (pull form).
+ *   (Sec. 2.5), BGK (Sec. 2.2), or the sensor-gated pair of the two (BGK where chi = 0, the
+ *   regularized collision where chi > 0: the reading of Sec. 2.2 in which the compression
+ *   sensor activates the regularized operator in place of BGK), exact streaming (pull form).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *  - D3Q7 weights for cs^2 = 1/4: w0 = 1/4, w1..6 = 1/8 (unique isotropic choice).
@@ -55,7 +57,8 @@ static const double CS2 = 0.25;
 typedef struct {
     int nx, ny, nz;
     int bc;          /* 0 periodic, 1 x-Dirichlet equilibrium ghosts */
-    int collision;   /* 0 BGK, 1 regularized + compression sensor */
+    int collision;   /* 0 BGK, 1 regularized + compression sensor, 2 sensor-gated:
+                        BGK where chi = 0, regularized with omega_h where chi > 0 */
     int sutherland;  /* 0 constant mu */
     double gamma;
     double mu_ref, kappa_ref, T_ref, T_S;
@@ -264,7 +267,7 @@ int orc_cell(const orc_params* P, const double fhat[NP], double fstar[NP], orc_c
     /* Alg. 1, compression sensor (Listing 2); cs = 1/2 in lattice units */
     double div = gu[0] + gu[4] + gu[8];
     double chi = 0.0;
-    if (P->collision == 1) {
+    if (P->collision == 1 || P->collision == 2) {
         double s = -div / sqrt(CS2);
         if (div < 0.0 && s > P->J_min) {
             chi = P->gain * s;
@@ -293,7 +296,8 @@ int orc_cell(const orc_params* P, const double fhat[NP], double fstar[NP], orc_c
     for (int k = 0; k < NF; ++k) {
         double feq[NQ];
         equilibrium(Q[k], Phi[k], feq);
-        if (P->collision == 1) {
+        const int regularized = P->collision == 1 || (P->collision == 2 && chi > 0.0);
+        if (regularized) {
             /* regularized: keep only the first-moment part r of f - f^eq (Sec. 2.5) */
             double om = P->omega[k];
             double red = om - P->omega_min;

@@ -55,7 +55,7 @@ class grlb_diag(C.Structure):
 
 class grlb_batch_config(C.Structure):
     _fields_ = [("block_x", C.c_int32), ("solo_min_cells", C.c_int32), ("use_graph", C.c_int32),
-                ("pad0", C.c_int32)]
+                ("record_mode", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -110,6 +110,8 @@ def lib():
             "grlb_ffma_probe": ([C.c_int32, C.c_int32, vp, vp, dp], i32),
             "grlb_set_init_mode": ([vp, C.c_int32], i32),
             "grlb_halo_exchange_z": ([vp, vp], i32),
+            "grlb_halo_pack_z": ([vp, vp, vp], i32),
+            "grlb_halo_unpack_z": ([vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -130,7 +132,7 @@ def exported_symbols():
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
             "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe",
-            "grlb_set_init_mode", "grlb_halo_exchange_z"]
+            "grlb_set_init_mode", "grlb_halo_exchange_z", "grlb_halo_pack_z", "grlb_halo_unpack_z"]
 
 
 def check(status):
@@ -270,9 +272,9 @@ def grlb_steps_done(h) -> int:
     return int(lib().grlb_steps_done(h))
 
 
-def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0):
+def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0, record_mode=0):
     arr = (C.c_void_p * len(handles))(*[h.value for h in handles])
-    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, 0)
+    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, record_mode)
     b = C.c_void_p()
     check(lib().grlb_batch_create(arr, len(handles), C.byref(cfg), C.byref(b)))
     return b
@@ -319,6 +321,16 @@ def grlb_set_init_mode(h, ce_init):
 
 def grlb_halo_exchange_z(lower, upper):
     check(lib().grlb_halo_exchange_z(lower, upper))
+
+
+def grlb_halo_pack_z(h, to_upper_ptr, to_lower_ptr):
+    """Enqueue the packing of a slab's outgoing ghost slices into device buffers (ints)."""
+    check(lib().grlb_halo_pack_z(h, to_upper_ptr, to_lower_ptr))
+
+
+def grlb_halo_unpack_z(h, from_lower_ptr, from_upper_ptr):
+    """Enqueue the unpacking of received ghost slices (device buffers, ints) into the slab."""
+    check(lib().grlb_halo_unpack_z(h, from_lower_ptr, from_upper_ptr))
 
 
 def grlb_spectrum_shells(prm) -> int:

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -112,7 +113,8 @@ static grlb_status validate(const grlb_params* p) {
     if (N >= 2147483647.0L) return fail(GRLB_EINVAL, "nx*ny*nz must be < 2^31");
     if (p->nz > 65535) return fail(GRLB_EINVAL, "nz must be <= 65535");
     if (p->bc != GRLB_BC_PERIODIC && p->bc != GRLB_BC_X_DIRICHLET_EQ) return fail(GRLB_EINVAL, "bad bc");
-    if (p->collision != GRLB_COLL_BGK && p->collision != GRLB_COLL_RLB_SENSOR)
+    if (p->collision != GRLB_COLL_BGK && p->collision != GRLB_COLL_RLB_SENSOR &&
+        p->collision != GRLB_COLL_RLB_GATED)
         return fail(GRLB_EINVAL, "bad collision");
     if (p->storage < GRLB_STORE_F32 || p->storage > GRLB_STORE_BF16) return fail(GRLB_EINVAL, "bad storage");
     if (p->streaming != 0 && p->streaming != 1) return fail(GRLB_EINVAL, "streaming must be 0 or 1");
@@ -697,12 +699,21 @@ struct grlb_batch {
     cudaStream_t stream = nullptr;
     DomainDev* d_doms = nullptr;
     std::vector<DomainDev> h_doms;  // records copied before each step (pageable: staged by the copy)
-    // tiles grouped by (storage, collision): group g occupies [off[g], off[g+1])
+    // tiles grouped by (storage, collision): group g = 3 storage + collision occupies
+    // [off[g], off[g+1])
     int4* d_tiles = nullptr;
     int ntiles = 0;
-    int group_off[7] = {0};
+    int group_off[10] = {0};
     cudaGraphExec_t graph = nullptr;
     bool dirty = true;
+    // constant-table path: the small domains' records in slots [slot0, slot0 + nsmall) of the
+    // constant table (small_idx[i]: domain i's offset in that range, -1 for large domains), one
+    // launch per group; slot0 < 0 when no slots were free (then the tile-table path above runs)
+    int slot0 = -1, nsmall = 0;
+    std::vector<int> small_idx;
+    std::vector<DomainDev> h_recs;
+    std::vector<grlb::BatchLaunch> launch;  // per group
+    std::vector<std::shared_ptr<void>> slot_waits;  // release events of the slots' last holders
     // large domains step on streams of their own, forked from and joined back into `stream`,
     // so that their launches overlap one another's tails and the table launches
     std::vector<cudaStream_t> aux;
@@ -711,7 +722,8 @@ struct grlb_batch {
 };
 
 namespace {
-int group_of(const grlb_params& p) { return p.storage * 2 + p.collision; }
+constexpr int kGroups = 9;  // 3 storage types x 3 collisions
+int group_of(const grlb_params& p) { return p.storage * 3 + p.collision; }
 
 // Tile width of domain i: the override, else block_x if the config fixes it, else the width
 // in {128, 64, 32} that pads its rows least, or 1 (linear tiles) when rows do not fill tiles.
@@ -738,8 +750,97 @@ int tile_width(const grlb_batch* b, size_t i) {
     return padded > 1.05 * (double)nx * ny ? 1 : tx;
 }
 
+// Slots of the constant record table (grlb_kernels.cu), shared by every batch of the process.
+// A batch takes a contiguous range at creation and gives it back when destroyed; the event
+// recorded then on its stream stays with the slots, and the next batch that takes them makes
+// its stream wait for it before writing its own records, so no record is overwritten while a
+// kernel of the previous holder may still read it.
+struct EventRef {
+    cudaEvent_t ev = nullptr;
+    ~EventRef() {
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+std::mutex g_slot_mu;
+bool g_slot_used[grlb::kBatchSlots] = {};
+// never destroyed: the events must not be released after the CUDA runtime has shut down
+std::shared_ptr<void>* const g_slot_release = new std::shared_ptr<void>[grlb::kBatchSlots];
+
+int take_slots(int n, std::vector<std::shared_ptr<void>>* waits) {
+    if (n <= 0) return -1;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int s0 = 0; s0 + n <= grlb::kBatchSlots; ++s0) {
+        int k = 0;
+        while (k < n && !g_slot_used[s0 + k]) ++k;
+        if (k < n) {
+            s0 += k;
+            continue;
+        }
+        for (int j = s0; j < s0 + n; ++j) {
+            g_slot_used[j] = true;
+            if (g_slot_release[j]) {
+                bool dup = false;
+                for (auto& w : *waits) dup = dup || w == g_slot_release[j];
+                if (!dup) waits->push_back(g_slot_release[j]);
+                g_slot_release[j].reset();
+            }
+        }
+        return s0;
+    }
+    return -1;
+}
+
+void give_slots(int s0, int n, cudaStream_t st) {
+    if (s0 < 0) return;
+    auto ref = std::make_shared<EventRef>();
+    if (cudaEventCreateWithFlags(&ref->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ref->ev, st) != cudaSuccess) {
+        cudaGetLastError();  // no event: wait for the device before the slots are reused
+        cudaDeviceSynchronize();
+        ref.reset();
+    }
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int j = s0; j < s0 + n; ++j) {
+        g_slot_used[j] = false;
+        g_slot_release[j] = ref;
+    }
+}
+
+// Number of CTAs (tiles) of small domain i.
+int64_t tiles_of(const grlb_batch* b, size_t i) {
+    const grlb_domain* d = b->doms[i];
+    const int tx = tile_width(b, i);
+    if (tx == 1) return (d->D.plane + 127) / 128;
+    const int ty = 128 / tx;
+    return (int64_t)((d->P.nx + tx - 1) / tx) * ((d->P.ny + ty - 1) / ty) * d->P.nz;
+}
+
+grlb_status rebuild_launches(grlb_batch* b) {
+    b->launch.assign(kGroups, grlb::BatchLaunch{});
+    int64_t total = 0;
+    for (int g = 0; g < kGroups; ++g) b->launch[g].nd = 0;
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        if (!b->active[i] || b->solo[i]) continue;
+        grlb::BatchLaunch& L = b->launch[group_of(b->doms[i]->P)];
+        const int64_t first = L.nd == 0 ? 0 : L.tile0[L.nd];
+        const int64_t end = first + tiles_of(b, i);
+        if (end > 2147483647LL) return fail(GRLB_EINVAL, "batch: more than 2^31 tiles in one launch");
+        L.slot[L.nd] = b->slot0 + b->small_idx[i];
+        L.tile0[L.nd] = (int32_t)first;
+        L.tile0[L.nd + 1] = (int32_t)end;
+        L.nd += 1;
+    }
+    for (int g = 0; g < kGroups; ++g) total += b->launch[g].nd ? b->launch[g].tile0[b->launch[g].nd] : 0;
+    b->ntiles = (int)std::min<int64_t>(total, 2147483647LL);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->dirty = false;
+    return GRLB_OK;
+}
+
 grlb_status rebuild_tiles(grlb_batch* b) {
-    std::vector<int4> groups[6];
+    if (b->slot0 >= 0) return rebuild_launches(b);
+    std::vector<int4> groups[kGroups];
     for (size_t i = 0; i < b->doms.size(); ++i) {
         if (!b->active[i] || b->solo[i]) continue;
         const grlb_domain* d = b->doms[i];
@@ -755,11 +856,11 @@ grlb_status rebuild_tiles(grlb_batch* b) {
                 for (int x = 0; x < d->P.nx; x += tx) g.push_back(make_int4((int)i, x, y, z));
     }
     std::vector<int4> all;
-    for (int g = 0; g < 6; ++g) {
+    for (int g = 0; g < kGroups; ++g) {
         b->group_off[g] = (int)all.size();
         all.insert(all.end(), groups[g].begin(), groups[g].end());
     }
-    b->group_off[6] = (int)all.size();
+    b->group_off[kGroups] = (int)all.size();
     if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
     b->d_tiles = nullptr;
     b->ntiles = (int)all.size();
@@ -787,10 +888,19 @@ cudaError_t order_after_domains(grlb_batch* b) {
 }
 
 cudaError_t enqueue_batch_step(grlb_batch* b, int parity) {
-    for (int g = 0; g < 6; ++g) {
+    if (b->slot0 >= 0) {
+        for (int g = 0; g < kGroups; ++g) {
+            if (b->launch[g].nd == 0) continue;
+            b->launch[g].parity = parity;
+            cudaError_t e = grlb::launch_batch_sweep_const(g / 3, g % 3, b->launch[g], b->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    for (int g = 0; g < kGroups; ++g) {
         const int n = b->group_off[g + 1] - b->group_off[g];
         if (n == 0) continue;
-        cudaError_t e = grlb::launch_batch_sweep(g / 2, g % 2, b->d_doms, b->d_tiles + b->group_off[g], n, parity,
+        cudaError_t e = grlb::launch_batch_sweep(g / 3, g % 3, b->d_doms, b->d_tiles + b->group_off[g], n, parity,
                                                  b->stream);
         if (e != cudaSuccess) return e;
     }
@@ -832,8 +942,18 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
     }
     b->stream = domains[0]->stream;
     retain_pool();
+    b->small_idx.assign(n, -1);
+    for (int i = 0; i < n; ++i)
+        if (!b->solo[i]) b->small_idx[i] = b->nsmall++;
+    if (b->cfg.record_mode != 0 && b->cfg.record_mode != 1) {
+        delete b;
+        return fail(GRLB_EINVAL, "record_mode must be 0 or 1");
+    }
+    if (b->cfg.record_mode == 0) b->slot0 = take_slots(b->nsmall, &b->slot_waits);
+    b->h_recs.resize(b->nsmall);
     b->h_doms.resize(n);
-    cudaError_t e = cudaMallocAsync(&b->d_doms, n * sizeof(DomainDev), b->stream);
+    cudaError_t e = cudaSuccess;
+    if (b->slot0 < 0) e = cudaMallocAsync(&b->d_doms, n * sizeof(DomainDev), b->stream);
     // the batch stream must not run ahead of work already queued on the domains' streams
     if (e == cudaSuccess) e = order_after_domains(b);
     if (e != cudaSuccess) {
@@ -863,6 +983,7 @@ void grlb_batch_destroy(grlb_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_doms) cudaFreeAsync(b->d_doms, b->stream);
     if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
+    give_slots(b->slot0, b->nsmall, b->stream);
     // pending work on the side streams completes before their resources are released
     for (cudaStream_t s : b->aux) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->aux_done) cudaEventDestroy(e);
@@ -951,13 +1072,29 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
 // The small domains' part of grlb_batch_step: nsteps launches of the batched sweep over the
 // tile table (pairs of steps replayed from a CUDA graph).
 static grlb_status batch_table_steps(grlb_batch* b, int nsteps) {
-    for (size_t i = 0; i < b->doms.size(); ++i) {
-        b->h_doms[i] = b->doms[i]->D;
-        b->h_doms[i].tile_x = tile_width(b, i);
+    if (b->slot0 >= 0) {
+        for (const auto& w : b->slot_waits) {  // the slots' previous holder is done with them
+            const EventRef* r = static_cast<const EventRef*>(w.get());
+            if (r && r->ev) GRLB_CU(cudaStreamWaitEvent(b->stream, r->ev, 0));
+        }
+        b->slot_waits.clear();
+        for (size_t i = 0; i < b->doms.size(); ++i) {
+            if (b->small_idx[i] < 0) continue;
+            DomainDev& r = b->h_recs[b->small_idx[i]];
+            r = b->doms[i]->D;
+            r.tile_x = tile_width(b, i);
+        }
+        // from pageable memory: the host copy is staged before the call returns
+        GRLB_CU(grlb::upload_batch_records(b->h_recs.data(), b->slot0, b->nsmall, b->stream));
+    } else {
+        for (size_t i = 0; i < b->doms.size(); ++i) {
+            b->h_doms[i] = b->doms[i]->D;
+            b->h_doms[i].tile_x = tile_width(b, i);
+        }
+        // from pageable memory: the host copy is staged before the call returns, no stream wait
+        GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms.data(), b->doms.size() * sizeof(DomainDev),
+                                cudaMemcpyHostToDevice, b->stream));
     }
-    // from pageable memory: the host copy is staged before the call returns, no stream wait
-    GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms.data(), b->doms.size() * sizeof(DomainDev),
-                            cudaMemcpyHostToDevice, b->stream));
     int done = 0;
     if (b->cfg.use_graph && b->stream != nullptr && nsteps >= 2) {
         if (!b->graph) {
@@ -1179,6 +1316,34 @@ extern "C" grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upp
         return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs must share one stream");
     GRLB_CU(grlb::launch_halo_z(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], a.nz, (int64_t)a.nx * a.ny,
                                 elem_bytes(a.storage), lower->stream));
+    return GRLB_OK;
+}
+
+static grlb_status check_slab(const grlb_domain* d, const char* who) {
+    const grlb_params& a = d->P;
+    if (a.streaming) return fail(GRLB_EINVAL, std::string(who) + ": two-buffer streaming only");
+    if (a.bc != GRLB_BC_PERIODIC) return fail(GRLB_EINVAL, std::string(who) + ": slabs are periodic domains");
+    if (a.nz < 3) return fail(GRLB_EINVAL, std::string(who) + ": a slab needs nz >= 3 (2 ghost planes)");
+    return GRLB_OK;
+}
+
+extern "C" grlb_status grlb_halo_pack_z(grlb_domain* d, void* to_upper, void* to_lower) {
+    if (!d || !to_upper || !to_lower) return fail(GRLB_EINVAL, "grlb_halo_pack_z: NULL argument");
+    grlb_status st = check_slab(d, "grlb_halo_pack_z");
+    if (st != GRLB_OK) return st;
+    const grlb_params& a = d->P;
+    GRLB_CU(grlb::launch_halo_pack_z(d->D.buf[d->D.cur], to_upper, to_lower, a.nz, (int64_t)a.nx * a.ny,
+                                     elem_bytes(a.storage), d->stream));
+    return GRLB_OK;
+}
+
+extern "C" grlb_status grlb_halo_unpack_z(grlb_domain* d, const void* from_lower, const void* from_upper) {
+    if (!d || !from_lower || !from_upper) return fail(GRLB_EINVAL, "grlb_halo_unpack_z: NULL argument");
+    grlb_status st = check_slab(d, "grlb_halo_unpack_z");
+    if (st != GRLB_OK) return st;
+    const grlb_params& a = d->P;
+    GRLB_CU(grlb::launch_halo_unpack_z(d->D.buf[d->D.cur], from_lower, from_upper, a.nz, (int64_t)a.nx * a.ny,
+                                       elem_bytes(a.storage), d->stream));
     return GRLB_OK;
 }
 

@@ -53,7 +53,9 @@ __host__ __device__ __forceinline__ int64_t brick_elems(int64_t N) {
 static_assert(kBrick == 128, "brick_at_u32 shifts by log2(kBrick)");
 
 enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
-enum Collision { C_BGK = 0, C_RLB = 1 };
+// C_GATED: BGK where the sensor is off (chi = 0), the regularized collision with omega_h where
+// it fires (chi > 0).
+enum Collision { C_BGK = 0, C_RLB = 1, C_GATED = 2 };
 
 // Per-domain lattice-unit constants.  Plain old data: passed by value as a kernel
 // parameter for single-domain launches, read from a device array by the batched sweep.
@@ -314,7 +316,7 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
     const float theta = gu[0][0] + gu[1][1] + gu[2][2];
     // compression sensor (Listing 2): s = -div u / cs, cs = 1/2
     float chi = 0.0f;
-    if (COLL == C_RLB) {
+    if (COLL == C_RLB || COLL == C_GATED) {
         const float s = -2.0f * theta;
         if (theta < 0.0f && s > D.J_min) chi = fminf(fmaxf(D.gain * s, 0.0f), 1.0f);
     }
@@ -342,7 +344,9 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
         Pd[4][c] = Hp * uv[c] + Fd[4][c];
     }
 
-    if (COLL == C_RLB) {
+    // C_GATED takes one of the two per cell (chi is uniform over the cell's five fields)
+    const bool regularized = COLL == C_RLB || (COLL == C_GATED && chi > 0.0f);
+    if (regularized) {
         // regularized collision with reduced rate (Sec. 2.5):
         // f* = f^eq + (1 - omega_h) r, r = first-moment part of f - f^eq, so the outgoing
         // set is w_i (Q + c_i . J* / cs^2) with J* = Phi + (1 - omega_h)(J - Phi).

@@ -45,4 +45,58 @@ cudaError_t launch_halo_z(void* lower, void* upper, int nzl, int64_t nxy, size_t
     return cudaGetLastError();
 }
 
+// Ghost exchange between slabs on different devices: the sender packs its two outgoing slices
+// into contiguous buffers (5 fields x nx ny, field-major), the buffers travel between ranks, and
+// the receiver unpacks them into its ghost planes.  Same slices as halo_z_kernel.
+template <typename T>
+__global__ void __launch_bounds__(256) halo_pack_kernel(const T* __restrict__ f, T* __restrict__ to_upper,
+                                                        T* __restrict__ to_lower, int nz, int64_t nxy) {
+    const int s = blockIdx.y;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
+        if (s < 5) to_upper[s * nxy + c] = f[brick_at((int64_t)(nz - 2) * nxy + c) + (7 * s + 5) * kBrick];
+        else to_lower[(s - 5) * nxy + c] = f[brick_at(nxy + c) + (7 * (s - 5) + 6) * kBrick];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) halo_unpack_kernel(T* __restrict__ f, const T* __restrict__ from_lower,
+                                                          const T* __restrict__ from_upper, int nz, int64_t nxy) {
+    const int s = blockIdx.y;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
+        if (s < 5) f[brick_at(c) + (7 * s + 5) * kBrick] = from_lower[s * nxy + c];
+        else f[brick_at((int64_t)(nz - 1) * nxy + c) + (7 * (s - 5) + 6) * kBrick] = from_upper[(s - 5) * nxy + c];
+    }
+}
+
+cudaError_t launch_halo_pack_z(const void* f, void* to_upper, void* to_lower, int nz, int64_t nxy, size_t elem,
+                               cudaStream_t st) {
+    int64_t blocks = (nxy + 255) / 256;
+    if (blocks > 148 * 4) blocks = 148 * 4;
+    const dim3 grid((unsigned)blocks, 10);
+    if (elem == 4)
+        halo_pack_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(f), static_cast<float*>(to_upper),
+                                                      static_cast<float*>(to_lower), nz, nxy);
+    else
+        halo_pack_kernel<unsigned short><<<grid, 256, 0, st>>>(static_cast<const unsigned short*>(f),
+                                                               static_cast<unsigned short*>(to_upper),
+                                                               static_cast<unsigned short*>(to_lower), nz, nxy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
+                                 size_t elem, cudaStream_t st) {
+    int64_t blocks = (nxy + 255) / 256;
+    if (blocks > 148 * 4) blocks = 148 * 4;
+    const dim3 grid((unsigned)blocks, 10);
+    if (elem == 4)
+        halo_unpack_kernel<float><<<grid, 256, 0, st>>>(static_cast<float*>(f), static_cast<const float*>(from_lower),
+                                                        static_cast<const float*>(from_upper), nz, nxy);
+    else
+        halo_unpack_kernel<unsigned short><<<grid, 256, 0, st>>>(static_cast<unsigned short*>(f),
+                                                                 static_cast<const unsigned short*>(from_lower),
+                                                                 static_cast<const unsigned short*>(from_upper), nz,
+                                                                 nxy);
+    return cudaGetLastError();
+}
+
 }  // namespace grlb

@@ -311,6 +311,85 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __res
     }
 }
 
+// ---- batched sweep with the domain records in constant memory -----------------------------
+// The records of a batch's small domains sit in slots of a constant table, written before each
+// batched step.  One CTA per tile, no tile table: CTA t of a launch finds its domain by a
+// search over the launch's tile prefix sums (kernel parameters), so the domain index, the
+// record's address and every constant read from it are the same for all threads of the CTA,
+// and the constants are read through the constant cache as in the single-domain sweep instead
+// of with a shared-memory load per use.
+static_assert(kBatchSlots * sizeof(DomainDev) <= 60 * 1024, "constant record table exceeds its budget");
+__constant__ DomainDev c_batch_doms[kBatchSlots];
+
+template <int S, int COLL>
+__global__ void __launch_bounds__(128) batch_sweep_const_kernel(const __grid_constant__ BatchLaunch L) {
+    using T = typename Store<S>::T;
+    const int t = blockIdx.x;
+    int lo = 0, hi = L.nd - 1;  // domain of tile t: the last i with tile0[i] <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.tile0[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const DomainDev& D = c_batch_doms[L.slot[lo]];
+    const int lt = t - L.tile0[lo];
+    int x, y, z;
+    bool active;
+    if (D.tile_x == 1) {  // linear tile: 128 consecutive cells in storage order
+        const int64_t cidx = (int64_t)lt * 128 + threadIdx.x;
+        active = cidx < D.plane;
+        const uint32_t c = active ? (uint32_t)cidx : 0u;
+        const uint32_t r = c / (uint32_t)D.nx;
+        x = (int)(c - r * (uint32_t)D.nx);
+        z = (int)(r / (uint32_t)D.ny);
+        y = (int)(r - (uint32_t)z * (uint32_t)D.ny);
+    } else {  // tile of tile_x cells x 128 / tile_x rows of one z plane, x fastest
+        const int tx = D.tile_x, ty = 128 / tx;
+        const int ntx = (D.nx + tx - 1) / tx, nty = (D.ny + ty - 1) / ty;
+        const int r = lt / ntx;
+        x = (lt - r * ntx) * tx + (int)threadIdx.x % tx;
+        y = (r % nty) * ty + (int)threadIdx.x / tx;
+        z = r / nty;
+        active = x < D.nx && y < D.ny;
+    }
+    if (active) {
+        const int c = D.cur ^ L.parity;
+        const T* __restrict__ fin = static_cast<const T*>(D.buf[c]);
+        T* __restrict__ fout = static_cast<T*>(D.buf[c ^ 1]);
+        const PullIdx P = pull_index(D, x, y, z);
+        const PullAt A = pull_at(P);
+        float d[NF][NQ], o[NF][NQ];
+        load_cell<S, PULL>(D, fin, P, A, d);
+        collide<S, COLL, false>(D, d, o, nullptr);
+        store_cell<S, PULL>(D, fout, P, A, o);
+    }
+}
+
+template <int S, int COLL>
+static cudaError_t launch_batch_const_t(const BatchLaunch& L, int ntiles, cudaStream_t st) {
+    batch_sweep_const_kernel<S, COLL><<<ntiles, 128, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sweep_const(int storage, int coll, const BatchLaunch& L, cudaStream_t st) {
+    if (L.nd <= 0) return cudaSuccess;
+    const int ntiles = L.tile0[L.nd];
+#define GRLB_CASE(SS, CC) \
+    if (storage == SS && coll == CC) return launch_batch_const_t<SS, CC>(L, ntiles, st);
+    GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F32, C_GATED)
+    GRLB_CASE(S_F16, C_RLB) GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_F16, C_GATED)
+    GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK) GRLB_CASE(S_BF16, C_GATED)
+#undef GRLB_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t upload_batch_records(const DomainDev* recs, int first_slot, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (first_slot < 0 || first_slot + n > kBatchSlots) return cudaErrorInvalidValue;
+    return cudaMemcpyToSymbolAsync(c_batch_doms, recs, (size_t)n * sizeof(DomainDev),
+                                   (size_t)first_slot * sizeof(DomainDev), cudaMemcpyHostToDevice, st);
+}
+
 // ---- diagnostics: fixed-order sum of the block partials ----------------------------------
 // Two deterministic stages.  Stage 1: CTA g sums the partial records [g*per, (g+1)*per) --
 // thread t takes records g*per + t, + 256, ... in order (FP64), then a fixed shared-memory
@@ -482,8 +561,9 @@ cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern,
 #define GRLB_CASE(SS, CC) \
     if (storage == SS && coll == CC)                                                               \
         return launch_sweep_t<SS, CC>(D, pattern, fin, fout, diag, partials, grid, block, st);
-    GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F16, C_RLB)
-    GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK)
+    GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F32, C_GATED)
+    GRLB_CASE(S_F16, C_RLB) GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_F16, C_GATED)
+    GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK) GRLB_CASE(S_BF16, C_GATED)
 #undef GRLB_CASE
     return cudaErrorInvalidValue;
 }
@@ -522,8 +602,9 @@ cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, con
     if (ntiles <= 0) return cudaSuccess;
 #define GRLB_CASE(SS, CC) \
     if (storage == SS && coll == CC) return launch_batch_t<SS, CC>(doms, tiles, ntiles, parity, st);
-    GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F16, C_RLB)
-    GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK)
+    GRLB_CASE(S_F32, C_RLB) GRLB_CASE(S_F32, C_BGK) GRLB_CASE(S_F32, C_GATED)
+    GRLB_CASE(S_F16, C_RLB) GRLB_CASE(S_F16, C_BGK) GRLB_CASE(S_F16, C_GATED)
+    GRLB_CASE(S_BF16, C_RLB) GRLB_CASE(S_BF16, C_BGK) GRLB_CASE(S_BF16, C_GATED)
 #undef GRLB_CASE
     return cudaErrorInvalidValue;
 }

@@ -15,6 +15,20 @@ cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern,
 // of the persistent batched kernel.
 cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, const int4* tiles, int ntiles,
                                int parity, cudaStream_t st);
+// Constant-table batched sweep: the records of up to kBatchSlots small domains live in a
+// __constant__ table (slots written by upload_batch_records, stream-ordered); one launch covers
+// the tiles of nd domains, domain i owning CTAs [tile0[i], tile0[i+1]) and its record in slot
+// slot[i].  Tiles as in the tile-table sweep (tile_x cells x 128 / tile_x rows, or 128
+// consecutive cells when tile_x == 1).
+constexpr int kBatchSlots = 160;  // 160 x 336-byte records: 53.8 KB of the 64 KB constant bank
+struct BatchLaunch {
+    int32_t nd;
+    int32_t parity;
+    int32_t slot[kBatchSlots];
+    int32_t tile0[kBatchSlots + 1];
+};
+cudaError_t launch_batch_sweep_const(int storage, int coll, const BatchLaunch& L, cudaStream_t st);
+cudaError_t upload_batch_records(const DomainDev* recs, int first_slot, int n, cudaStream_t st);
 cudaError_t launch_diag_finalize(const double* partials, int64_t nblocks, double* out,
                                  cudaStream_t st);
 // swap = 1 writes the one-buffer layout (population i in slot opp(i)).
@@ -60,6 +74,13 @@ cudaError_t launch_spectral_k2_to_k5(SpectralPlan& P, const float2* tw, float2* 
 // z-slab ghost exchange (grlb_halo.cu): lower's top interior +z slices -> upper's ghost plane
 // 0; upper's bottom interior -z slices -> lower's top ghost plane (nzl = lower's planes).
 cudaError_t launch_halo_z(void* lower, void* upper, int nzl, int64_t nxy, size_t elem, cudaStream_t st);
+// Cross-device form of the same exchange: pack the two outgoing slices of a slab (nz planes
+// including its ghosts) into contiguous buffers of 5 nxy elements, unpack received ones into its
+// ghost planes.
+cudaError_t launch_halo_pack_z(const void* f, void* to_upper, void* to_lower, int nz, int64_t nxy, size_t elem,
+                               cudaStream_t st);
+cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
+                                 size_t elem, cudaStream_t st);
 // Writes *flag = 1 (device-accessible) if any stored value of the buffer (bytes, a multiple of
 // 16) is non-finite; never writes 0.
 cudaError_t launch_check_finite(const void* buf, int64_t bytes, int storage, int32_t* flag, cudaStream_t st);

@@ -7,9 +7,12 @@ below and nz_s + 1 above, initialised with the whole domain's planes z0 - 1 .. z
 pulls from them: the +z population of the lower neighbour's top interior plane (into ghost
 plane 0) and the -z population of the upper neighbour's bottom interior plane (into the top
 ghost plane), for the five fields.  Interior cells then evolve exactly as in the undivided
-domain.  `SlabSet` runs this with the C ABI (grlb_halo_exchange_z); `exchange_planes` is the
-same rule on host population arrays (35 planes of nx ny nz, x fastest), for checks on the CPU
-and for ranks that exchange slices over torch.distributed.
+domain.  `SlabSet` runs this with the C ABI (grlb_halo_exchange_z) for slabs on one device;
+`SlabRank` is one slab per rank of a multi-device run, its slices packed into device buffers
+(grlb_halo_pack_z), swapped with the neighbouring ranks by `ring_exchange` (torch.distributed
+point-to-point send / receive: NCCL between devices, gloo between CPU ranks) and unpacked into
+the ghost planes (grlb_halo_unpack_z); `exchange_planes` is the rule on host population arrays
+(35 planes of nx ny nz, x fastest), for checks on the CPU.
 """
 from __future__ import annotations
 
@@ -125,6 +128,88 @@ class SlabSet:
         for d in self.doms:
             d.close()
         self.doms = []
+
+
+def ring_exchange(top, bottom, rank: int, world: int):
+    """The ghost slices of this rank's slab in a periodic ring of z-slabs, one slab per rank
+    (rank r owns the planes above rank r - 1's).  Sends `top` (the +z populations of the top
+    interior plane) to rank r + 1 and `bottom` (the -z populations of the bottom interior plane)
+    to rank r - 1, both mod world, and returns (from_below, from_above): rank r - 1's top and
+    rank r + 1's bottom, the values of this slab's ghost planes 0 and nz - 1.  One rank closes
+    the ring on itself (no communication).  Point-to-point operations of one batch are matched
+    in the order they are issued, so with two ranks (the same peer above and below) the first
+    send meets the first receive."""
+    if world == 1:
+        return top, bottom
+    import torch
+    import torch.distributed as dist
+    up, down = (rank + 1) % world, (rank - 1) % world
+    from_below = torch.empty_like(top)
+    from_above = torch.empty_like(bottom)
+    ops = [dist.P2POp(dist.isend, top, up), dist.P2POp(dist.isend, bottom, down),
+           dist.P2POp(dist.irecv, from_below, down), dist.P2POp(dist.irecv, from_above, up)]
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+    return from_below, from_above
+
+
+class SlabRank:
+    """This rank's z-slab of a periodic domain split over `world` ranks, one device each: the
+    slab's own domain on the current device, and before every step its outgoing slices packed
+    on the device, swapped with the neighbouring ranks by ring_exchange and unpacked into its
+    ghost planes.  All of it runs on `stream` (a torch stream; NCCL orders its transfers after
+    the packing and the unpacking after them), so the interior evolves bitwise as the
+    undivided domain's planes z0 .. z0 + nzs - 1."""
+
+    def __init__(self, case: inputs.Case | None, rank: int, world: int, stream=None, sizes=None,
+                 part: inputs.Case | None = None):
+        """case: the whole domain, split by `sizes` (default: even slabs); or part: this rank's
+        slab (with its ghost planes, as slab_case builds it) when the whole domain is too large
+        to build on one host."""
+        import torch
+        from . import capi
+        self.capi = capi
+        self.rank, self.world = rank, world
+        if part is None:
+            prm = case.params
+            self.sizes = list(sizes) if sizes is not None else slab_sizes(prm.nz, world)
+            self.z0 = slab_starts(self.sizes)[rank]
+            self.part = slab_case(case, self.z0, self.sizes[rank])
+        else:
+            self.part = part
+            self.z0 = part.meta.get("z0", 0)
+        prm = self.part.params
+        self.stream = stream or torch.cuda.Stream()
+        self.dom = capi.Domain(self.part.params.replace(streaming=0), stream=self.stream.cuda_stream)
+        nxy = prm.nx * prm.ny
+        dtype = torch.float32 if prm.storage == inputs.STORE_F32 else torch.int16  # raw 16-bit values
+        self.top = torch.empty((5, nxy), dtype=dtype, device="cuda")
+        self.bottom = torch.empty_like(self.top)
+        self.nx, self.ny = prm.nx, prm.ny
+
+    def init(self, ce_init: bool | None = None):
+        p = self.part
+        self.dom.init(p.rho, p.u, p.p, ce_init=ce_init)
+
+    def init_device(self, rho, u, p):
+        """Initialise from the slab's fields already on the device (torch FP64 tensors)."""
+        self.capi.grlb_init_primitive_device(self.dom.h, rho.data_ptr(), u.data_ptr(), p.data_ptr())
+
+    def step(self, n: int = 1):
+        import torch
+        c = self.capi
+        with torch.cuda.stream(self.stream):
+            for _ in range(n):
+                c.grlb_halo_pack_z(self.dom.h, self.top.data_ptr(), self.bottom.data_ptr())
+                below, above = ring_exchange(self.top, self.bottom, self.rank, self.world)
+                c.grlb_halo_unpack_z(self.dom.h, below.data_ptr(), above.data_ptr())
+                self.dom.step(1)
+
+    def conserved_interior(self) -> np.ndarray:
+        return interior(self.dom.conserved(), self.nx, self.ny)
+
+    def close(self):
+        self.dom.close()
 
 
 def allreduce_sum(values: np.ndarray) -> np.ndarray:

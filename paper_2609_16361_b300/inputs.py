@@ -23,6 +23,7 @@ BC_PERIODIC = 0
 BC_X_DIRICHLET_EQ = 1
 COLL_BGK = 0
 COLL_RLB_SENSOR = 1
+COLL_RLB_GATED = 2   # BGK where the sensor is off, regularized where it fires
 STORE_F32 = 0
 STORE_F16 = 1
 STORE_BF16 = 2

@@ -1,6 +1,8 @@
 """z-slab decomposition on the CPU (no GPU): the ghost-plane exchange rule, applied to the FP64
 oracle's populations, reproduces the undivided run bitwise; two gloo ranks, each owning one
-slab, exchange the ghost slices over torch.distributed and all-reduce the interior totals."""
+slab, exchange the ghost slices with the multi-device path's rank-level exchange
+(decomp.ring_exchange over torch.distributed) and all-reduce the interior totals; one rank
+closes the ring on itself."""
 import os
 import sys
 
@@ -92,16 +94,12 @@ def _rank(rank, ws, port, out):
         o = orc.Oracle(p.params)
         o.init_primitive(p.rho, p.u, p.p)
         nxy = 80
-        up, down = (rank + 1) % ws, (rank - 1) % ws
         for _ in range(8):
+            # the rank-level exchange of the multi-device path (decomp.ring_exchange), on the
+            # oracle slab's host slices instead of packed device buffers
             top = torch.from_numpy(np.ascontiguousarray(dc.top_slice(o.f, nxy)))
             bot = torch.from_numpy(np.ascontiguousarray(dc.bottom_slice(o.f, nxy)))
-            from_down = torch.empty_like(top)
-            from_up = torch.empty_like(bot)
-            reqs = [dist.isend(top, up, tag=1), dist.isend(bot, down, tag=2),
-                    dist.irecv(from_down, down, tag=1), dist.irecv(from_up, up, tag=2)]
-            for r in reqs:
-                r.wait()
+            from_down, from_up = dc.ring_exchange(top, bot, rank, ws)
             dc.put_bottom_ghost(o.f, nxy, from_down.numpy())
             dc.put_top_ghost(o.f, nxy, from_up.numpy())
             o.step(1)
@@ -116,11 +114,13 @@ def _rank(rank, ws, port, out):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_exchange_ghost_slices_and_allreduce_totals():
+@pytest.mark.parametrize("ws", [2, 3])
+def test_gloo_ranks_exchange_ghost_slices_and_allreduce_totals(ws):
+    """Two ranks (the same peer above and below) and three (distinct peers)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 29700 + os.getpid() % 1000
-    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    port = 29700 + os.getpid() % 1000 + 10 * ws
+    ps = [ctx.Process(target=_rank, args=(r, ws, port, q)) for r in range(ws)]
     for p in ps:
         p.start()
     got = [q.get(timeout=180) for _ in ps]
@@ -130,3 +130,8 @@ def test_two_gloo_ranks_exchange_ghost_slices_and_allreduce_totals():
     for rank, same, totals, ref in got:
         assert same, rank
         np.testing.assert_allclose(totals, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_one_rank_closes_the_ring_on_itself():
+    top, bot = object(), object()
+    assert decomp.ring_exchange(top, bot, 0, 1) == (top, bot)

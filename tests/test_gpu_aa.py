@@ -5,12 +5,14 @@ slots, push to the neighbours) and even steps (own slots, swapped on write) appl
 collisions of the two-buffer pull sweep to the same inputs.  The kernels are separate
 instantiations, so the compiler may contract products differently: results agree to FP32
 rounding (relative L-inf <= 1e-6 over 30 steps), and a one-buffer run is bitwise
-reproducible against itself and across a checkpoint."""
+reproducible against itself and across a checkpoint.  Every case also matches the FP64 oracle
+(rel L-inf 1e-5 smooth / rel L1 1e-4 tubes for FP32 storage)."""
 import numpy as np
 import pytest
 
 from paper_2609_16361_b300 import capi, inputs
-from tests.common import rel_linf
+from tests.common import rel_linf, run_oracle
+from tests.test_gpu_batch import oracle_gate
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +51,21 @@ def test_in_place_equals_two_buffers(steps):
         assert np.array_equal(b.conserved(), b2.conserved())
         for d in (a, b, b2):
             d.close()
+
+
+@pytest.mark.parametrize("steps", [7, 100])
+def test_in_place_matches_the_oracle(steps):
+    for c in cases():
+        b = run(c, steps, 1)
+        R = run_oracle(c, steps).conserved()
+        Q = b.conserved()
+        if c.params.ncells == 1:   # a single cell: no flow, compare with a floor on the scale
+            scale = np.maximum(np.abs(R).max(1), 1e-3)
+            assert np.all(np.abs(Q - R).max(1) / scale <= 1e-5)
+        else:
+            ok, err = oracle_gate(c, Q, R)
+            assert ok, (c.params.name, steps, err)
+        b.close()
 
 
 def test_in_place_diagnostics_and_memory():

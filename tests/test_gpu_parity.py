@@ -41,15 +41,16 @@ def test_uniform_state_stays_uniform(collision):
     assert np.abs(Q[0] - 1.0).max() < 1e-6
 
 
-def test_taylor_green_32_rlb_sutherland():
-    c = inputs.tgv3d(32)
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_RLB_GATED])
+def test_taylor_green_32_rlb_sutherland(collision):
+    c = inputs.tgv3d(32, collision=collision)
     d = gpu_run(c, 100)
     o = run_oracle(c, 100)
     err = rel_linf(d.conserved(), o.conserved())
     assert np.all(err <= LINF_SMOOTH), err
 
 
-@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_BGK])
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_BGK, inputs.COLL_RLB_GATED])
 def test_random_smooth_ragged_tiles(collision):
     # 40 x 21 x 7: CTA tiles of 64 x 2 leave a ragged x tail and a ragged y row
     c = inputs.random_smooth(40, 21, 7, seed=5, collision=collision)
@@ -84,8 +85,10 @@ def close_counts(a, b, rel=0.1, slack=3):
     return abs(a - b) <= max(slack, rel * max(a, b))
 
 
-def test_sod_tube_400_cells_1000_steps():
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_RLB_GATED])
+def test_sod_tube_400_cells_1000_steps(collision):
     c = inputs.sod(400)
+    c.params = c.params.replace(collision=collision)
     d = gpu_run(c, 1000, diag_last=True)
     o = run_oracle(c, 1000, keep_cells=True)
     err = rel_l1(d.conserved(), o.conserved())

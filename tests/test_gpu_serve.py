@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from paper_2609_16361_b300 import capi, inputs, serve
-from tests.common import rel_linf
+from tests.common import rel_linf, run_oracle
+from tests.test_gpu_batch import oracle_gate
 
 pytestmark = pytest.mark.gpu
 
@@ -81,3 +82,16 @@ def test_one_buffer_large_requests():
     r0 = big[0]
     alone = serve.Server(chunk=12, large_cells=large, one_buffer_large=True).run([r0], realtime=False)[0]
     assert alone.digest == a[trace.index(r0)].digest
+
+
+def test_served_results_match_the_oracle():
+    """Every request of the mixed trace against the FP64 oracle run of its own case: FP32
+    requests at rel L-inf 1e-5 (Taylor-Green boxes) / rel L1 1e-4 (Sod and Becker tubes), FP16
+    requests within 1e-2."""
+    trace = small_trace()
+    res = serve.Server(chunk=16, keep_fields=True).run(trace, realtime=False)
+    assert sum(r.storage == inputs.STORE_F32 for r in trace) >= 3
+    for r, x in zip(trace, res):
+        R = run_oracle(r.case, r.steps).conserved()
+        ok, err = oracle_gate(r.case, x.fields, R)
+        assert ok, (r.rid, r.kind, r.storage, err)

@@ -1,6 +1,9 @@
 """z-slab decomposition on one GPU (grlb_halo_exchange_z): the interior of the slabs evolves
 bitwise as the undivided domain, for uneven slabs, ragged CTA tiles, FP16 storage and the
-Chapman-Enskog start; interior totals add up to the whole domain's."""
+Chapman-Enskog start; interior totals add up to the whole domain's.  The multi-device form
+(grlb_halo_pack_z / grlb_halo_unpack_z around a transfer of device buffers) gives the same:
+one rank whose ring closes on itself (decomp.SlabRank, world 1), and slabs that swap their packed
+slices through device buffers as ranks on different devices would."""
 import numpy as np
 import pytest
 
@@ -56,4 +59,47 @@ def test_exchange_rejects_unsuitable_slabs():
         with pytest.raises(capi.GrlbError):
             capi.grlb_halo_exchange_z(x.h, y.h)
     for d in (a, b, e):
+        d.close()
+
+
+@pytest.mark.parametrize("storage", [inputs.STORE_F32, inputs.STORE_F16])
+def test_one_rank_ring_equals_the_periodic_domain(storage):
+    c = inputs.tgv3d(32, storage=storage)
+    r = decomp.SlabRank(c, 0, 1)
+    r.init()
+    r.step(25)
+    assert np.array_equal(r.conserved_interior(), whole_run(c, 25))
+    r.close()
+
+
+def test_packed_slices_between_slabs_equal_the_undivided_run():
+    """Three slabs exchange through packed device buffers (the transfer a multi-rank run makes
+    with NCCL is a plain copy here): bitwise the undivided run."""
+    torch = pytest.importorskip("torch")
+    c = inputs.random_smooth(40, 21, 24, seed=5)
+    sizes = [7, 9, 8]
+    parts = [decomp.slab_case(c, z0, n) for z0, n in zip(decomp.slab_starts(sizes), sizes)]
+    doms = [capi.Domain(p.params) for p in parts]
+    for d, p in zip(doms, parts):
+        d.init(p.rho, p.u, p.p)
+    nxy = 40 * 21
+    bufs = [(torch.empty((5, nxy), device="cuda"), torch.empty((5, nxy), device="cuda")) for _ in doms]
+    recv = [(torch.empty((5, nxy), device="cuda"), torch.empty((5, nxy), device="cuda")) for _ in doms]
+    S = len(doms)
+    for _ in range(30):
+        for d, (up, down) in zip(doms, bufs):
+            capi.grlb_halo_pack_z(d.h, up.data_ptr(), down.data_ptr())
+        torch.cuda.synchronize()
+        for i in range(S):
+            recv[i][0].copy_(bufs[(i - 1) % S][0])   # from below: the lower slab's top slice
+            recv[i][1].copy_(bufs[(i + 1) % S][1])   # from above: the upper slab's bottom slice
+        torch.cuda.synchronize()
+        for d, (below, above) in zip(doms, recv):
+            capi.grlb_halo_unpack_z(d.h, below.data_ptr(), above.data_ptr())
+            d.step(1)
+    Q = decomp.stitch(decomp.interior(d.conserved(), 40, 21) for d in doms)
+    assert np.array_equal(Q, whole_run(c, 30))
+    with pytest.raises(capi.GrlbError):
+        capi.grlb_halo_pack_z(capi.Domain(inputs.sod(64).params).h, 1, 2)
+    for d in doms:
         d.close()

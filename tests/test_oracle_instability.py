@@ -1,17 +1,26 @@
-"""The finding that the regularized collision with the linear equilibrium is unstable near
-omega = 2, pinned twice:
+"""The regularized collision with the linear equilibrium is unstable near omega = 2; the
+readings of Sec. 2.2 / 2.5 / Algorithm 1, checked one by one.
 
-- on the scalar model the finding is derived from (one advected field on the 1-D reduction of
-  D3Q7: rest weight 3/4, link weights 1/8, cs^2 = 1/4, equilibrium w_i (Q + c_i a Q / cs^2)),
-  built here from those definitions alone: at omega = 2 the regularized map (Q, J) ->
-  (Q, omega a Q + (1 - omega) J) followed by streaming has, at cos k = -1/3, an eigenvalue of
-  modulus sqrt(1 + 4 a^2 sin^2 k) > 1 for every a != 0, whereas BGK at omega = 2 keeps every
-  eigenvalue on or inside the unit circle up to |a| = 1/4 and leaves it beyond;
-- on the FP64 oracle (five fields, full Euler flux): a 1e-10 pressure perturbation of a
-  uniform moving state whose characteristic speeds stay below 1/4 (|u| + c = 0.17 in lattice
-  units) grows by more than 1e3 over 180 steps under the regularized collision at omega = 1.99
-  and stays bounded under BGK.
+Scalar model (one advected field, Phi = a Q + b (J - a Q): a the lattice wave speed, b =
+beta/(1 + beta) the share of the non-equilibrium first moment the gradient reconstruction
+returns as diffusive flux), built here from the D3Q7 weights and the linear equilibrium alone,
+on the 1-D reduction (rest weight 3/4, link weights 1/8) and on the full 3-D lattice:
+
+  (a) regularized, r = first-moment part of f - f^eq(Q, Phi)      (the oracle's RLB_SENSOR)
+  (b) regularized, r from Pi^(1) = J - Phi^adv
+  (c) omega_h also in the reconstruction: on smooth cells (chi = 0) identical to (a)
+  (d) sensor acting on the discarded (second-moment) part, (e) regularized only where the
+      sensor fires, BGK elsewhere (the oracle's RLB_GATED): on smooth cells both are BGK.
+
+Findings pinned here: (a)-(c) have, near omega = 2, eigenvalues outside the unit circle for
+every a != 0 (closed form at cos k = -1/3 for (a)), also in 3-D at the supersonic Taylor-Green
+wave speeds (5-8 % growth per step); (d)/(e) reduce to BGK on smooth flow, which at omega = 2
+keeps every eigenvalue on or inside the unit circle up to |a| = 1/4 per axis, is stable at the
+128^3 Taylor-Green point and grows by less than 0.2 % per step at the 256^3 point.  On the FP64 oracle a perturbation of a
+uniform moving state grows under (a) and not under BGK, and the supersonic Taylor-Green vortex
+with the Tab. run_params parameters goes non-finite under (a) long before it does under (e).
 """
+import itertools
 import math
 
 import numpy as np
@@ -20,42 +29,93 @@ import pytest
 import oracle
 from paper_2609_16361_b300 import inputs
 
-W = np.array([0.75, 0.125, 0.125])
-C = np.array([0.0, 1.0, -1.0])
+W1 = np.array([0.75, 0.125, 0.125])
+C1 = np.array([0.0, 1.0, -1.0])
+C3 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+W3 = np.array([0.25] + [0.125] * 6)
 CS2 = 0.25
 
 
-def stream(k):
-    return np.diag(np.exp(-1j * C * k))  # f_i(x) <- f*_i(x - c_i)
+def collision_map(reading, a, omega, b=0.0, three_d=False):
+    """Linear map f -> f* of one cell (rows: outgoing population, columns: incoming)."""
+    W, C = (W3, C3) if three_d else (W1, C1[:, None])
+    a = np.atleast_1d(np.asarray(a, float))
+    n = len(W)
+    Qrow = np.ones(n)
+    Jrows = C.T                                               # first moment per axis
+    Phi_adv = np.outer(a, Qrow)
+    Phi = Phi_adv + b * (Jrows - Phi_adv)                     # advective + returned diffusive flux
+    Feq = np.outer(W, Qrow) + (W[:, None] * C) @ Phi / CS2    # linear equilibrium
+    if reading in ("a", "c"):
+        return Feq + (1 - omega) * (W[:, None] * C) @ (Jrows - Phi) / CS2
+    if reading == "b":
+        return Feq + (1 - omega) * (W[:, None] * C) @ (Jrows - Phi_adv) / CS2
+    if reading in ("d", "e", "bgk"):
+        return np.eye(n) + omega * (Feq - np.eye(n))
+    raise ValueError(reading)
 
 
-def rlb_map(a, omega):
-    Jstar = omega * a * np.ones(3) + (1.0 - omega) * C
-    return np.outer(W, np.ones(3)) + np.outer(W * C / CS2, Jstar)
+def spectral_radius(M, k, three_d=False):
+    C = C3 if three_d else C1[:, None]
+    S = np.diag(np.exp(-1j * (C @ np.atleast_1d(k))))        # pull streaming f_i(x) <- f*_i(x - c_i)
+    return np.abs(np.linalg.eigvals(S @ M)).max()
 
 
-def bgk_map(a, omega):
-    E = np.outer(W * (1.0 + C * a / CS2), np.ones(3))
-    return np.eye(3) + omega * (E - np.eye(3))
-
-
-def spectral_radius(M, k):
-    return np.abs(np.linalg.eigvals(stream(k) @ M)).max()
+def max_radius(reading, a, omega, b=0.0, three_d=False, n=16):
+    ks = np.linspace(-math.pi, math.pi, n, endpoint=False) + 1e-3
+    M = collision_map(reading, a, omega, b, three_d)
+    grid = itertools.product(ks, ks, ks) if three_d else ((k,) for k in ks)
+    return max(spectral_radius(M, np.array(k), three_d) for k in grid)
 
 
 @pytest.mark.parametrize("a", [0.02, 0.05, 0.1, 0.2])
 def test_regularized_eigenvalue_closed_form(a):
+    """(a) at omega = 2, cos k = -1/3: the update's determinant vanishes and the other
+    eigenvalue is 1 - 2 i a sin k, of modulus sqrt(1 + 4 a^2 sin^2 k)."""
     k = math.acos(-1.0 / 3.0)
-    assert spectral_radius(rlb_map(a, 2.0), k) == pytest.approx(math.sqrt(1 + 4 * a * a * math.sin(k) ** 2),
-                                                                rel=1e-12)
+    M = collision_map("a", a, 2.0)
+    assert spectral_radius(M, k) == pytest.approx(math.sqrt(1 + 4 * a * a * math.sin(k) ** 2), rel=1e-12)
 
 
-def test_bgk_at_omega_two_is_stable_up_to_a_quarter():
+# Taylor-Green operating points (Sec. 3.4, Tab. run_params): nominal omega from f_mu and the
+# feedback share b = beta / (1 + beta) with beta ~ 0.02 at 128^3 (Sec. 2.4), halving per doubling
+POINTS = {"128^3": (1.98183, 0.02), "256^3": (1.99996, 0.01)}
+DIRS = ((0.18, 0.0, 0.0), (0.127, 0.127, 0.0), (0.104, 0.104, 0.104))
+
+
+@pytest.mark.parametrize("point", list(POINTS))
+def test_regularized_readings_grow_at_the_taylor_green_point(point):
+    """(a), (b), (c) at the wave speeds of the supersonic vortex (|u| + c ~ 0.18 per step in
+    lattice units): growth > 5 % per step on the 1-D reduction, > 0.1 % per step in 3-D along
+    an axis, a face diagonal and the body diagonal."""
+    omega, beta = POINTS[point]
+    b = beta / (1 + beta)
+    for reading in ("a", "b", "c"):
+        assert max_radius(reading, 0.18, omega, b, n=2000) > 1.05, (reading, point)
+        for a in DIRS:
+            assert max_radius(reading, a, omega, b, three_d=True) > 1.001, (reading, point, a)
+
+
+def test_gated_readings_are_bgk_on_smooth_flow():
+    """(d), (e) on smooth cells are BGK: without feedback stable at omega = 2 for |a| <= 1/4 per
+    axis and unstable beyond; at the 128^3 Taylor-Green point stable (1-D and 3-D); at the
+    256^3 point (omega -> 2, first moment relaxed at omega / (1 + beta) but the discarded
+    moments at omega) growing by less than 0.2 % per step, forty times slower than (a)."""
     ks = np.linspace(1e-3, math.pi, 1201)
     for a in (0.05, 0.1, 0.2, 0.25):
-        assert max(spectral_radius(bgk_map(a, 2.0), k) for k in ks) <= 1 + 1e-9, a
-    assert max(spectral_radius(bgk_map(0.27, 2.0), k) for k in ks) > 1 + 1e-3
-    assert max(spectral_radius(rlb_map(0.05, 2.0), k) for k in ks) > 1 + 1e-3
+        assert max(spectral_radius(collision_map("e", a, 2.0), k) for k in ks) <= 1 + 1e-9, a
+    assert max(spectral_radius(collision_map("e", 0.27, 2.0), k) for k in ks) > 1 + 1e-3
+    omega, beta = POINTS["128^3"]
+    b = beta / (1 + beta)
+    for reading in ("d", "e"):
+        assert max_radius(reading, 0.18, omega, b, n=2000) <= 1 + 1e-9
+        for a in DIRS:
+            assert max_radius(reading, a, omega, b, three_d=True) <= 1 + 1e-9, (reading, a)
+    omega, beta = POINTS["256^3"]
+    b = beta / (1 + beta)
+    gated = max_radius("e", 0.18, omega, b, n=2000)
+    assert 1.0 < gated < 1.002
+    assert max_radius("a", 0.18, omega, b, n=2000) - 1 > 40 * (gated - 1)
 
 
 def perturbation_growth(collision, steps=180):
@@ -72,5 +132,30 @@ def perturbation_growth(collision, steps=180):
 
 
 def test_oracle_regularized_grows_bgk_stays_bounded():
+    """A uniform moving state with |u| + c = 0.17 < 1/4: the regularized collision (a) amplifies
+    a 1e-10 pressure perturbation > 1e3 times in 180 steps at omega = 1.99; BGK (what (d) and
+    (e) do with the sensor off) does not."""
     assert perturbation_growth(inputs.COLL_RLB_SENSOR) > 1e3
     assert perturbation_growth(inputs.COLL_BGK) < 2.0
+    assert perturbation_growth(inputs.COLL_RLB_GATED) < 2.0
+
+
+def test_supersonic_taylor_green_regularized_fails_first():
+    """The supersonic Taylor-Green vortex with the parameters of Tab. run_params (32^3, RLB,
+    g 40, J_min 1e-2, omega_min 1.987, dt = 0.1 dx): reading (a) is non-finite before step 250
+    (t_c 4.9); the gated reading (e) is still finite there, kinetic energy within 10 % of its
+    initial value (it decays by 8 % by then)."""
+    c = inputs.tgv3d(32)
+    ke = {}
+    for coll in (inputs.COLL_RLB_SENSOR, inputs.COLL_RLB_GATED):
+        o = oracle.Oracle(c.params.replace(collision=coll))
+        o.init_primitive(c.rho, c.u, c.p)
+        try:
+            o.step(250)
+        except RuntimeError:   # the reconstruction system of a non-finite cell is singular
+            ke[coll] = np.nan
+            continue
+        Q = o.conserved()
+        ke[coll] = float((0.5 * (Q[1:4] ** 2).sum(0) / Q[0]).mean()) if np.isfinite(Q).all() else np.nan
+    assert np.isnan(ke[inputs.COLL_RLB_SENSOR])
+    assert ke[inputs.COLL_RLB_GATED] == pytest.approx(0.125, rel=0.1)

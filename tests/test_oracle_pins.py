@@ -173,8 +173,57 @@ def test_sensor_gate_uniform_compression():
         assert info.chi == pytest.approx(expect, abs=1e-12)
 
 
+def test_gated_collision_is_bgk_off_the_sensor_and_regularized_on_it():
+    """Sensor-gated collision (the reading of Sec. 2.2 in which the sensor activates the
+    regularized operator in place of BGK), checked by the post-collision moments of an
+    inviscid cell whose populations carry a second-moment non-equilibrium part:
+      chi = 0 (expansion): BGK keeps (1 - omega) of it, Sigma f* c_x^2 - cs^2 Q =
+                           (1 - omega)(Sigma f c_x^2 - cs^2 Q);
+      chi > 0 (compression): the regularized collision discards it (Sec. 2.5);
+    and in both the first moment is J + omega_r (Phi - J) with Phi the Euler flux and
+    omega_r = omega (BGK) or omega_h = omega - chi (omega - omega_min) (Listing 2)."""
+    g, jmin, om_min = 20.0, 3e-3, 1.0
+    P = lattice_P(mu_ref=0.0, sensor_gain=g, J_min=jmin, omega_min=om_min, collision=2)
+    om = P.omega[0]
+    rho, p, u = 1.0, 0.5, np.array([0.03, -0.02, 0.01])
+    for a in (-1e-3, 3e-3):                          # expansion, compression (chi = 0.36)
+        gu = -a * np.eye(3)
+        Q, J, _ = build_first_moments(rho, u, p, np.zeros(3), gu, np.zeros(3), 0.0, 0.0,
+                                      np.full(5, om), 1.4)
+        f = pops_with_moments(Q, J)
+        dev = 1e-3 * np.arange(1, 6)                 # second-moment deviation per field
+        for k in range(5):
+            f[7 * k + 1] += dev[k]
+            f[7 * k + 2] += dev[k]
+            f[7 * k + 0] -= 2 * dev[k]              # Q and J unchanged
+        fstar, info = oracle.cell(P, f)
+        chi = 0.0 if 6 * a <= jmin else min(g * 6 * a, 1.0)
+        assert info.chi == pytest.approx(chi, abs=1e-12)
+        _, Phi = euler_flux(rho, u, p, 1.4)
+        om_r = om - chi * max(om - om_min, 0.0)
+        for k in range(5):
+            Pin = f[7 * k + 1] + f[7 * k + 2] - CS2 * Q[k]
+            Pout = fstar[7 * k + 1] + fstar[7 * k + 2] - CS2 * Q[k]
+            want = 0.0 if chi > 0 else (1.0 - om) * Pin
+            assert Pout == pytest.approx(want, abs=1e-14)
+            Jout = CI.T @ fstar[7 * k:7 * k + 7]
+            np.testing.assert_allclose(Jout, J[k] + om_r * (Phi[k] - J[k]), atol=1e-14)
+
+
+def test_gated_collision_without_sensor_gain_is_bgk():
+    """With gain 0 the sensor never fires, so the gated collision is BGK on every cell."""
+    c = inputs.random_smooth(10, 7, 5, seed=4)
+    runs = []
+    for coll, gain in ((2, 0.0), (0, 0.0)):
+        o = oracle.Oracle(c.params.replace(collision=coll, sensor_gain=gain))
+        o.init_primitive(c.rho, c.u, c.p)
+        o.step(15)
+        runs.append(o.f.copy())
+    assert np.array_equal(runs[0], runs[1])
+
+
 # ---- invariants ----------------------------------------------------------------------------
-@pytest.mark.parametrize("collision", [0, 1])
+@pytest.mark.parametrize("collision", [0, 1, 2])
 def test_conservation_on_periodic_domain(collision):
     c = inputs.random_smooth(8, 6, 5, seed=1, collision=collision)
     o = oracle.Oracle(c.params)
@@ -188,7 +237,7 @@ def test_conservation_on_periodic_domain(collision):
     assert np.abs(Q1 - Q0).max() > 1e-4             # the flow did evolve
 
 
-@pytest.mark.parametrize("collision", [0, 1])
+@pytest.mark.parametrize("collision", [0, 1, 2])
 def test_uniform_state_is_invariant(collision):
     c = inputs.uniform(6, 5, 4, collision=collision)
     o = oracle.Oracle(c.params)
