@@ -657,6 +657,46 @@ def run_batch(args):
     return 0
 
 
+def run_batch_tubes(args):
+    """The tube class of the batched workload alone: the 48 Becker tubes of the seed-0 mix
+    (128-2048 x 4 x 4 cells, all below solo_min_cells, so all in the batched kernel), one batch
+    with the domain records of --record-mode, --batch-steps steps (CUDA-graph step loop),
+    against the HBM roofline (280 B per cell update)."""
+    import torch
+    from paper_2609_16361_b300 import capi, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    st = stream.cuda_stream
+    cases = [c for c in inputs.batched_mix(0) if c.params.name.startswith("becker")]
+    cells = sum(c.params.ncells for c in cases)
+    doms = [capi.Domain(c.params, stream=st) for c in cases]
+    for d, c in zip(doms, cases):
+        d.init(c.rho, c.u, c.p)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, record_mode=args.record_mode)
+    capi.grlb_batch_set_stream(b, st)
+    capi.grlb_batch_step(b, 4)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    capi.grlb_batch_step(b, args.batch_steps)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    capi.grlb_batch_destroy(b)
+    for d in doms:
+        d.close()
+    peak, src = measured_peaks()
+    gbs = 280 * cells * args.batch_steps / t / 1e9
+    line = {"metric": "batched MLUP/s (48 Becker tubes)", "value": cells * args.batch_steps / t / 1e6,
+            "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "48 Becker tubes 128-2048 x 4 x 4 (M 1.5-5), seed 0", "cells": cells,
+                       "steps": args.batch_steps, "record_mode": args.record_mode},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": f"{src} hbm_gbs", "bytes_per_cell": 280}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Poisson trace (seed 0, --rate requests/s, default 20): continuous-batching server against
     the same trace served first-in first-out one domain at a time with plain launches."""
@@ -750,37 +790,55 @@ def run_precision(args):
     ref = mk_long(0)
     orc = {}
 
+    # snapshots along the run: the storage error first, then, once the under-resolved vortex
+    # turns chaotic (t_c ~ 5-10), the divergence every pair of runs shows whatever the precision
+    marks = sorted({m for m in (long_steps // 8, long_steps // 4, long_steps // 2) if m > 0} | {long_steps})
+
     def oracle_run():
         try:
             o = oracle.Oracle(ref.params)
             o.init_primitive(ref.rho, ref.u, ref.p, ce_init=True)
             t0 = time.perf_counter()
-            o.step(long_steps)
+            done = 0
+            for m in marks:
+                o.step(m - done)
+                done = m
+                orc[m] = o.conserved()
             orc["seconds"] = time.perf_counter() - t0
-            orc["Q"] = o.conserved()
         except RuntimeError as e:   # a non-finite state makes the reconstruction singular
             orc["error"] = str(e)
 
+    def ke_mean(Q):
+        return float((0.5 * (Q[1:4] ** 2).sum(0) / Q[0]).mean())
+
     th = threading.Thread(target=oracle_run)
     th.start()
-    fields = {}
+    snaps = {}
     for st in (0, 1, 2):
         c = mk_long(st)
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p, ce_init=True)
-        d.step(long_steps)
-        fields[st] = prim(d.conserved(), c.params.gamma)
+        done = 0
+        for m in marks:
+            d.step(m - done)
+            done = m
+            snaps[(st, m)] = d.conserved()
         d.close()
-    finite = {names[st]: bool(all(np.isfinite(a).all() for a in fields[st])) for st in (0, 1, 2)}
+    finite = {names[st]: bool(np.isfinite(snaps[(st, long_steps)]).all()) for st in (0, 1, 2)}
     th.join()
-    long_key = f"tgv{pn}_re{args.prec_re:g}_{args.collision}_{long_steps}_vs_oracle"
-    if "Q" in orc and np.isfinite(orc["Q"]).all():
-        R = prim(orc["Q"], ref.params.gamma)
-        for st in (0, 1, 2):
-            acc.setdefault(names[st], {})[long_key] = errs(fields[st], R)
-    for st in (1, 2):
-        acc.setdefault(names[st], {})[f"tgv{pn}_re{args.prec_re:g}_{long_steps}_vs_f32"] = errs(fields[st], fields[0])
-    del fields
+    for m in marks:
+        key = f"tgv{pn}_re{args.prec_re:g}_{args.collision}_{m}_vs_oracle"
+        if m in orc and np.isfinite(orc[m]).all():
+            R = prim(orc[m], ref.params.gamma)
+            for st in (0, 1, 2):
+                e = errs(prim(snaps[(st, m)], ref.params.gamma), R)
+                e["E_k_rel"] = abs(ke_mean(snaps[(st, m)]) / ke_mean(orc[m]) - 1.0)
+                acc.setdefault(names[st], {})[key] = e
+        for st in (1, 2):
+            e = errs(prim(snaps[(st, m)], ref.params.gamma), prim(snaps[(0, m)], ref.params.gamma))
+            e["E_k_rel"] = abs(ke_mean(snaps[(st, m)]) / ke_mean(snaps[(0, m)]) - 1.0)
+            acc.setdefault(names[st], {})[f"tgv{pn}_re{args.prec_re:g}_{m}_vs_f32"] = e
+    del snaps
     speed = {}
     peak, src = measured_peaks()
     for st in (0, 1, 2):
@@ -1177,7 +1235,9 @@ def main():
     ap.add_argument("--no-legs", action="store_true",
                     help="leave the batched and served legs out of the default line")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
-                             "tgv-map", "capacity", "spectral", "slabs", "cases"])
+                             "tgv-map", "batch-tubes", "capacity", "spectral", "slabs", "cases"])
+    ap.add_argument("--record-mode", type=int, default=0, choices=[0, 1],
+                    help="batch-tubes: 0 constant-table domain records, 1 device-memory records")
     ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--prec-n", type=int, default=128, help="precision: grid of the long comparison")
     ap.add_argument("--prec-steps", type=int, default=2000, help="precision: steps of the long comparison")
@@ -1206,6 +1266,8 @@ def main():
         return run_tgv_series(args)
     if args.workload == "tgv-map":
         return run_tgv_map(args)
+    if args.workload == "batch-tubes":
+        return run_batch_tubes(args)
     if args.workload == "spectral":
         return run_spectral(args)
     if args.workload == "slabs":
