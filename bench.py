@@ -495,9 +495,9 @@ def diag_record(g, spec, case):
 
 def batched_leg(args, steps=200):
     """Short batched leg of the default line: the 64-domain seed-0 mix (48 Becker tubes + 16
-    Taylor-Green boxes), `steps` steps in one batch (constant-table batched sweep, CUDA-graph
-    step loop, default tiles) against the same domains advanced one after another with one
-    launch per sweep (legacy stream: grlb_step replays no graph there)."""
+    Taylor-Green boxes), `steps` steps in one batch (default schedule: concurrent single-domain
+    sweeps replayed from CUDA graphs) against the same domains advanced one after another with
+    one launch per sweep (legacy stream: grlb_step replays no graph there)."""
     import torch
     from paper_2609_16361_b300 import capi, inputs
     stream = torch.cuda.Stream()
@@ -509,7 +509,7 @@ def batched_leg(args, steps=200):
         d.init(c.rho, c.u, c.p)
     b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
     capi.grlb_batch_set_stream(b, st)
-    capi.grlb_batch_step(b, 4)
+    capi.grlb_batch_step(b, 20)   # warm-up; also captures the step graphs (>= 16 steps)
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -560,12 +560,14 @@ def served_leg(args, n_requests=40, rate=20.0):
 
 # ----------------------------------------------------------------------------------------
 def run_batch(args):
-    """64 uneven domains (48 Becker tubes + 16 Taylor-Green boxes, seed 0), 1000 steps each:
-    persistent batched sweep with autotuned tile widths and a CUDA-graph step loop, against
-    64 sequential single-domain runs through grlb_step -- one launch per sweep (the domains on
-    the legacy default stream, where grlb_step replays no graph: the baseline `vs_sequential_plain`
-    divides by) and, for reference, on a stream of their own, where grlb_step replays the
-    small domains' sweeps from CUDA graphs."""
+    """64 uneven domains (48 Becker tubes + 16 Taylor-Green boxes, seed 0), 1000 steps each,
+    under the three batch schedules (concurrent single-domain sweeps -- the value --; one
+    launch per step with constant-table records, autotuned or default tiles; the same with
+    device-memory records and no graph), the tube class alone under each, against 64
+    sequential single-domain runs through grlb_step -- one launch per sweep (the domains on the
+    legacy default stream, where grlb_step replays no graph: the baseline `vs_sequential_plain`
+    divides by) and, for reference, on a stream of their own, where grlb_step replays the small
+    domains' sweeps from CUDA graphs."""
     import torch
     from paper_2609_16361_b300 import autotune, capi, inputs
     torch.cuda.set_device(0)
@@ -582,16 +584,19 @@ def run_batch(args):
         doms.append(d)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     out = {}
-    for label, use_graph, plan in (("batched_graph_tuned", 1, autotune.plan(cases, table)),
-                                   ("batched_graph_default", 1, None),
-                                   ("batched_nograph_default", 0, None)):
+    S = capi
+    for label, sched, use_graph, plan in (
+            ("batched_concurrent", S.SCHED_CONCURRENT, 1, None),
+            ("batched_table_const_graph_tuned", S.SCHED_TABLE_CONST, 1, autotune.plan(cases, table)),
+            ("batched_table_const_graph_default", S.SCHED_TABLE_CONST, 1, None),
+            ("batched_table_nograph_default", S.SCHED_TABLE, 0, None)):
         for d, c in zip(doms, cases):
             d.init(c.rho, c.u, c.p)
-        b = capi.grlb_batch_create([d.h for d in doms], use_graph=use_graph)
+        b = capi.grlb_batch_create([d.h for d in doms], use_graph=use_graph, schedule=sched)
         capi.grlb_batch_set_stream(b, st)
         if plan:
             capi.grlb_batch_set_tile_x(b, plan)
-        capi.grlb_batch_step(b, 4)
+        capi.grlb_batch_step(b, 20)   # warm-up; also captures the step graphs (>= 16 steps)
         stream.synchronize()
         e0, e1 = ev(), ev()
         e0.record(stream)
@@ -606,12 +611,13 @@ def run_batch(args):
     tubes = [i for i, c in enumerate(cases) if c.params.name.startswith("becker")]
     tcells = sum(cases[i].params.ncells for i in tubes)
     peak, _ = measured_peaks()
-    for label, mode in (("tubes_constant_records", 0), ("tubes_table_records", 1)):
+    for label, mode in (("tubes_concurrent", S.SCHED_CONCURRENT), ("tubes_table_const", S.SCHED_TABLE_CONST),
+                        ("tubes_table", S.SCHED_TABLE)):
         for i in tubes:
             doms[i].init(cases[i].rho, cases[i].u, cases[i].p)
-        b = capi.grlb_batch_create([doms[i].h for i in tubes], use_graph=1, record_mode=mode)
+        b = capi.grlb_batch_create([doms[i].h for i in tubes], use_graph=1, schedule=mode)
         capi.grlb_batch_set_stream(b, st)
-        capi.grlb_batch_step(b, 4)
+        capi.grlb_batch_step(b, 20)   # warm-up; also captures the step graphs (>= 16 steps)
         stream.synchronize()
         e0, e1 = ev(), ev()
         e0.record(stream)
@@ -643,7 +649,7 @@ def run_batch(args):
         diag_ok &= d.diag(allow_nonfinite=True)["n_nan"] == 0
     for d in doms:
         d.close()
-    best = out["batched_graph_tuned"]["mlups"]
+    best = out["batched_concurrent"]["mlups"]
     line = {"metric": "batched MLUP/s (64 uneven domains, 1000 steps each)", "value": best,
             "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True,
             "vs_sequential_plain": best / out["sequential_plain"]["mlups"],
@@ -659,9 +665,8 @@ def run_batch(args):
 
 def run_batch_tubes(args):
     """The tube class of the batched workload alone: the 48 Becker tubes of the seed-0 mix
-    (128-2048 x 4 x 4 cells, all below solo_min_cells, so all in the batched kernel), one batch
-    with the domain records of --record-mode, --batch-steps steps (CUDA-graph step loop),
-    against the HBM roofline (280 B per cell update)."""
+    (128-2048 x 4 x 4 cells, all below solo_min_cells), one batch under --schedule,
+    --batch-steps steps (CUDA graphs), against the HBM roofline (280 B per cell update)."""
     import torch
     from paper_2609_16361_b300 import capi, inputs
     torch.cuda.set_device(0)
@@ -672,9 +677,11 @@ def run_batch_tubes(args):
     doms = [capi.Domain(c.params, stream=st) for c in cases]
     for d, c in zip(doms, cases):
         d.init(c.rho, c.u, c.p)
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, record_mode=args.record_mode)
+    sched = {"concurrent": capi.SCHED_CONCURRENT, "table_const": capi.SCHED_TABLE_CONST,
+             "table": capi.SCHED_TABLE}[args.schedule]
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=sched)
     capi.grlb_batch_set_stream(b, st)
-    capi.grlb_batch_step(b, 4)
+    capi.grlb_batch_step(b, 20)   # warm-up; also captures the step graphs (>= 16 steps)
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -690,7 +697,7 @@ def run_batch_tubes(args):
     line = {"metric": "batched MLUP/s (48 Becker tubes)", "value": cells * args.batch_steps / t / 1e6,
             "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "48 Becker tubes 128-2048 x 4 x 4 (M 1.5-5), seed 0", "cells": cells,
-                       "steps": args.batch_steps, "record_mode": args.record_mode},
+                       "steps": args.batch_steps, "schedule": args.schedule},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_source": f"{src} hbm_gbs", "bytes_per_cell": 280}}
     print(json.dumps(line), flush=True)
@@ -1236,8 +1243,9 @@ def main():
                     help="leave the batched and served legs out of the default line")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
                              "tgv-map", "batch-tubes", "capacity", "spectral", "slabs", "cases"])
-    ap.add_argument("--record-mode", type=int, default=0, choices=[0, 1],
-                    help="batch-tubes: 0 constant-table domain records, 1 device-memory records")
+    ap.add_argument("--schedule", default="concurrent", choices=["concurrent", "table_const", "table"],
+                    help="batch-tubes: concurrent single-domain sweeps, or one launch per step with "
+                         "constant-table / device-memory records")
     ap.add_argument("--run-steps", type=int, default=5000)
     ap.add_argument("--prec-n", type=int, default=128, help="precision: grid of the long comparison")
     ap.add_argument("--prec-steps", type=int, default=2000, help="precision: steps of the long comparison")

@@ -209,27 +209,39 @@ grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes);
 grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes);
 int64_t grlb_steps_done(const grlb_domain* d);
 
-/* ---- batching: many domains, one launch per step -------------------------------------
- * A batch references existing domains (it does not own them; destroy the batch first).
- * One step = one launch of the persistent batched sweep over a tile table that concatenates
- * the tiles of every active small domain (one launch per storage/collision group), plus one
- * single-domain sweep per active large domain (at least solo_min_cells cells; it saturates
- * the GPU on its own and runs the kernel grlb_step runs, so its result is bitwise that of
- * grlb_step; a large domain may use one-buffer streaming, a small one may not).  A 128-thread CTA covers tile_x cells along x times 128/tile_x rows.  A small
- * domain's result does not depend on the other domains of the batch and matches grlb_step
- * within FP32 rounding (16-bit storage: up to a few stored values one 16-bit rounding apart).
- * All domains must live on the same device; the batch runs on the
- * stream of domains[0] (or the one set with grlb_batch_set_stream). */
+/* ---- batching: many domains advanced by one call ------------------------------------------
+ * A batch references existing domains (it does not own them; destroy the batch first) and
+ * advances every active one by nsteps per grlb_batch_step, on the stream of domains[0] (or the
+ * one set with grlb_batch_set_stream).  All domains must live on the same device.  A domain's
+ * result never depends on the other domains of the batch.  Three schedules:
+ *  GRLB_SCHED_CONCURRENT (default): every domain is advanced by the single-domain sweep that
+ *    grlb_step runs (its record a kernel parameter, so its constants are constant-bank operands;
+ *    domains of at most 4,194,304 cells replay their sweeps from their own CUDA graph), and the
+ *    domains are dealt, largest first, over up to 32 side streams forked from and joined back
+ *    into the batch stream, so that the kernels of different domains run concurrently and fill
+ *    one another's waves.  Results are bitwise those of grlb_step.  Domains may use one-buffer
+ *    streaming.
+ *  GRLB_SCHED_TABLE_CONST: the small domains (below solo_min_cells) advance together in one
+ *    launch per step and (storage, collision) group of the batched sweep, one 128-thread CTA per
+ *    tile, their records in a constant table of 160 slots shared by the process (a batch that
+ *    finds too few free slots runs as GRLB_SCHED_TABLE); with enough tiles they are split into
+ *    two groups on two streams.  Large domains as under GRLB_SCHED_CONCURRENT.
+ *  GRLB_SCHED_TABLE: as GRLB_SCHED_TABLE_CONST with the records in device memory, staged in
+ *    shared memory by a persistent kernel walking a tile table.
+ * Under the two table schedules a CTA covers tile_x cells along x times 128/tile_x rows, a
+ * small domain's result matches grlb_step within FP32 rounding (16-bit storage: up to a few
+ * stored values one 16-bit rounding apart; the two kernels read the constants from different
+ * memory spaces) and small domains need two-buffer streaming.  No schedule takes a domain with a
+ * source term. */
+typedef enum { GRLB_SCHED_CONCURRENT = 0, GRLB_SCHED_TABLE_CONST = 1, GRLB_SCHED_TABLE = 2 } grlb_schedule;
 typedef struct {
-    int32_t block_x;        /* default tile width: 32, 64 or 128 (0 = 128, narrowed for
-                               domains with fewer cells along x)                             */
-    int32_t solo_min_cells; /* 0 = 262144 (64^3); < 0: every domain goes through the table  */
-    int32_t use_graph;      /* 1: replay the table launches of two steps from a CUDA graph  */
-    int32_t record_mode;    /* 0: the small domains' records in a constant table of 160 slots
-                               shared by the process (one CTA per tile, constants read through
-                               the constant cache), or, if too few slots are free, as 1;
-                               1: records in device memory, copied to shared memory by a
-                               persistent kernel walking a tile table                        */
+    int32_t block_x;        /* table schedules: default tile width 32, 64 or 128 (0 = 128,
+                               narrowed for domains with fewer cells along x)                */
+    int32_t solo_min_cells; /* table schedules: 0 = 262144 (64^3); < 0: every domain goes
+                               through the table                                            */
+    int32_t use_graph;      /* table schedules: 1 = replay the table launches of two steps
+                               from a CUDA graph                                            */
+    int32_t schedule;       /* grlb_schedule                                                */
 } grlb_batch_config;
 
 grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_batch_config* cfg,
@@ -239,14 +251,13 @@ grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream);
 /* Mark which domains advance (active[i] != 0); rebuilds the tile table.  active == NULL
  * activates all. */
 grlb_status grlb_batch_set_active(grlb_batch* b, const int* active);
-/* Per-domain tile shape, e.g. from an autotuner: 32, 64 or 128 cells along x of a 128-thread
- * CTA (times 4, 2, 1 rows); 1 = linear tiles of 128 consecutive cells in storage order; 0 = the
- * default (block_x if the config sets it, else the least-padding width, or linear tiles when
- * rows do not fill whole tiles).  tile_x == NULL resets all to 0.  Rebuilds the tile table.
- * Results do not depend on the tile shape. */
+/* Per-domain tile shape of the table schedules, e.g. from an autotuner: 32, 64 or 128 cells
+ * along x of a 128-thread CTA (times 4, 2, 1 rows); 1 = linear tiles of 128 consecutive cells in
+ * storage order; 0 = the default (block_x if the config sets it, else the least-padding width,
+ * or linear tiles when rows do not fill whole tiles).  tile_x == NULL resets all to 0.  Rebuilds
+ * the tile table.  Results do not depend on the tile shape; GRLB_SCHED_CONCURRENT ignores it. */
 grlb_status grlb_batch_set_tile_x(grlb_batch* b, const int* tile_x);
-/* Enqueue nsteps sweeps of every active domain, one launch per step (per storage/collision
- * group), replayed from a captured CUDA graph when use_graph is set. */
+/* Enqueue nsteps sweeps of every active domain by the batch's schedule (above). */
 grlb_status grlb_batch_step(grlb_batch* b, int nsteps);
 
 /* ---- diagnostic sweep without device allocation ---------------------------------------

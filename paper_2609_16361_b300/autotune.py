@@ -33,7 +33,7 @@ def size_class(prm) -> str:
 
 def _time_batch(handles, tile_x, steps, stream):
     import torch
-    b = capi.grlb_batch_create(handles, use_graph=1)
+    b = capi.grlb_batch_create(handles, use_graph=1, schedule=capi.SCHED_TABLE_CONST)
     try:
         capi.grlb_batch_set_stream(b, stream.cuda_stream)
         capi.grlb_batch_set_tile_x(b, [tile_x] * len(handles))

@@ -55,7 +55,7 @@ class grlb_diag(C.Structure):
 
 class grlb_batch_config(C.Structure):
     _fields_ = [("block_x", C.c_int32), ("solo_min_cells", C.c_int32), ("use_graph", C.c_int32),
-                ("record_mode", C.c_int32)]
+                ("schedule", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -272,9 +272,12 @@ def grlb_steps_done(h) -> int:
     return int(lib().grlb_steps_done(h))
 
 
-def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0, record_mode=0):
+SCHED_CONCURRENT, SCHED_TABLE_CONST, SCHED_TABLE = 0, 1, 2
+
+
+def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0, schedule=SCHED_CONCURRENT):
     arr = (C.c_void_p * len(handles))(*[h.value for h in handles])
-    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, record_mode)
+    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, schedule)
     b = C.c_void_p()
     check(lib().grlb_batch_create(arr, len(handles), C.byref(cfg), C.byref(b)))
     return b

@@ -512,9 +512,16 @@ static bool at_graph_start(const grlb_domain* d) {
     return d->D.cur == d->graph_cur;
 }
 
+static grlb_status step_domain(grlb_domain* d, int nsteps);
+
 grlb_status grlb_step(grlb_domain* d, int nsteps) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
+    return step_domain(d, nsteps);
+}
+
+// nsteps sweeps on d->stream: graph replays where they apply, plain sweeps otherwise.
+static grlb_status step_domain(grlb_domain* d, int nsteps) {
     int n = 0;
     if (d->stream && nsteps >= 2 * kStepGraphSweeps && d->D.plane <= kStepGraphMaxCells) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -712,7 +719,15 @@ struct grlb_batch {
     int slot0 = -1, nsmall = 0;
     std::vector<int> small_idx;
     std::vector<DomainDev> h_recs;
-    std::vector<grlb::BatchLaunch> launch;  // per group
+    std::vector<grlb::BatchLaunch> launch;  // [lane * kGroups + group]
+    // the small domains split into nlanes groups of about equal tile counts (two when there are
+    // enough tiles), each stepped on its own stream (lane 0: `stream`, lane 1: lane_stream,
+    // forked from and joined back into `stream`) with its own graph: the domains are
+    // independent, so one lane's launches fill the other's wave ramp and tail
+    int nlanes = 1;
+    cudaGraphExec_t lane_graph[2] = {nullptr, nullptr};
+    cudaStream_t lane_stream = nullptr;
+    cudaEvent_t lane_fork = nullptr, lane_done = nullptr;
     std::vector<std::shared_ptr<void>> slot_waits;  // release events of the slots' last holders
     // large domains step on streams of their own, forked from and joined back into `stream`,
     // so that their launches overlap one another's tails and the table launches
@@ -723,6 +738,7 @@ struct grlb_batch {
 
 namespace {
 constexpr int kGroups = 9;  // 3 storage types x 3 collisions
+constexpr size_t kSoloLanes = 32;  // side streams of the single-domain path of a batch
 int group_of(const grlb_params& p) { return p.storage * 3 + p.collision; }
 
 // Tile width of domain i: the override, else block_x if the config fixes it, else the width
@@ -815,25 +831,54 @@ int64_t tiles_of(const grlb_batch* b, size_t i) {
     return (int64_t)((d->P.nx + tx - 1) / tx) * ((d->P.ny + ty - 1) / ty) * d->P.nz;
 }
 
+void drop_lane_graphs(grlb_batch* b) {
+    for (cudaGraphExec_t& g : b->lane_graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// Two lanes when the small domains have enough tiles for both to fill the device (at least
+// four waves of one CTA per SM each) and there are at least two of them.
+constexpr int64_t kLaneMinTiles = 4 * 2 * 148;
+
 grlb_status rebuild_launches(grlb_batch* b) {
-    b->launch.assign(kGroups, grlb::BatchLaunch{});
+    std::vector<size_t> small;
+    std::vector<int64_t> tiles(b->doms.size(), 0);
     int64_t total = 0;
-    for (int g = 0; g < kGroups; ++g) b->launch[g].nd = 0;
     for (size_t i = 0; i < b->doms.size(); ++i) {
         if (!b->active[i] || b->solo[i]) continue;
-        grlb::BatchLaunch& L = b->launch[group_of(b->doms[i]->P)];
+        small.push_back(i);
+        tiles[i] = tiles_of(b, i);
+        total += tiles[i];
+    }
+    b->nlanes = (small.size() >= 2 && total >= kLaneMinTiles) ? 2 : 1;
+    // lane of each domain: largest first into the lane with fewer tiles
+    std::vector<int> lane_of(b->doms.size(), 0);
+    if (b->nlanes == 2) {
+        std::vector<size_t> order = small;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return tiles[a] > tiles[c]; });
+        int64_t load[2] = {0, 0};
+        for (size_t i : order) {
+            const int l = load[1] < load[0] ? 1 : 0;
+            lane_of[i] = l;
+            load[l] += tiles[i];
+        }
+    }
+    b->launch.assign(2 * kGroups, grlb::BatchLaunch{});
+    for (grlb::BatchLaunch& L : b->launch) L.nd = 0;
+    for (size_t i : small) {
+        grlb::BatchLaunch& L = b->launch[lane_of[i] * kGroups + group_of(b->doms[i]->P)];
         const int64_t first = L.nd == 0 ? 0 : L.tile0[L.nd];
-        const int64_t end = first + tiles_of(b, i);
+        const int64_t end = first + tiles[i];
         if (end > 2147483647LL) return fail(GRLB_EINVAL, "batch: more than 2^31 tiles in one launch");
         L.slot[L.nd] = b->slot0 + b->small_idx[i];
         L.tile0[L.nd] = (int32_t)first;
         L.tile0[L.nd + 1] = (int32_t)end;
         L.nd += 1;
     }
-    for (int g = 0; g < kGroups; ++g) total += b->launch[g].nd ? b->launch[g].tile0[b->launch[g].nd] : 0;
     b->ntiles = (int)std::min<int64_t>(total, 2147483647LL);
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+    drop_lane_graphs(b);
     b->dirty = false;
     return GRLB_OK;
 }
@@ -887,12 +932,13 @@ cudaError_t order_after_domains(grlb_batch* b) {
     return e;
 }
 
-cudaError_t enqueue_batch_step(grlb_batch* b, int parity) {
+cudaError_t enqueue_batch_step(grlb_batch* b, int parity, int lane = 0, cudaStream_t st = nullptr) {
     if (b->slot0 >= 0) {
         for (int g = 0; g < kGroups; ++g) {
-            if (b->launch[g].nd == 0) continue;
-            b->launch[g].parity = parity;
-            cudaError_t e = grlb::launch_batch_sweep_const(g / 3, g % 3, b->launch[g], b->stream);
+            grlb::BatchLaunch& L = b->launch[lane * kGroups + g];
+            if (L.nd == 0) continue;
+            L.parity = parity;
+            cudaError_t e = grlb::launch_batch_sweep_const(g / 3, g % 3, L, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -901,7 +947,7 @@ cudaError_t enqueue_batch_step(grlb_batch* b, int parity) {
         const int n = b->group_off[g + 1] - b->group_off[g];
         if (n == 0) continue;
         cudaError_t e = grlb::launch_batch_sweep(g / 3, g % 3, b->d_doms, b->d_tiles + b->group_off[g], n, parity,
-                                                 b->stream);
+                                                 st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -921,13 +967,18 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
         delete b;
         return fail(GRLB_EINVAL, "block_x must be 32, 64 or 128");
     }
+    const int sched = b->cfg.schedule;
+    if (sched != GRLB_SCHED_CONCURRENT && sched != GRLB_SCHED_TABLE_CONST && sched != GRLB_SCHED_TABLE) {
+        delete b;
+        return fail(GRLB_EINVAL, "schedule must be GRLB_SCHED_CONCURRENT, _TABLE_CONST or _TABLE");
+    }
     for (int i = 0; i < n; ++i) {
         if (!domains[i]) {
             delete b;
             return fail(GRLB_EINVAL, "NULL domain in batch");
         }
         const int64_t thr = b->cfg.solo_min_cells == 0 ? 262144 : b->cfg.solo_min_cells;
-        const int solo = thr > 0 && domains[i]->D.plane >= thr ? 1 : 0;
+        const int solo = sched == GRLB_SCHED_CONCURRENT || (thr > 0 && domains[i]->D.plane >= thr) ? 1 : 0;
         // the batched kernel runs two-buffer domains without a source; a domain advanced on its
         // own (solo) may use one-buffer streaming
         if (domains[i]->D.src || (domains[i]->P.streaming && !solo)) {
@@ -945,11 +996,7 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
     b->small_idx.assign(n, -1);
     for (int i = 0; i < n; ++i)
         if (!b->solo[i]) b->small_idx[i] = b->nsmall++;
-    if (b->cfg.record_mode != 0 && b->cfg.record_mode != 1) {
-        delete b;
-        return fail(GRLB_EINVAL, "record_mode must be 0 or 1");
-    }
-    if (b->cfg.record_mode == 0) b->slot0 = take_slots(b->nsmall, &b->slot_waits);
+    if (sched == GRLB_SCHED_TABLE_CONST) b->slot0 = take_slots(b->nsmall, &b->slot_waits);
     b->h_recs.resize(b->nsmall);
     b->h_doms.resize(n);
     cudaError_t e = cudaSuccess;
@@ -984,6 +1031,10 @@ void grlb_batch_destroy(grlb_batch* b) {
     if (b->d_doms) cudaFreeAsync(b->d_doms, b->stream);
     if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
     give_slots(b->slot0, b->nsmall, b->stream);
+    drop_lane_graphs(b);
+    if (b->lane_stream) cudaStreamDestroy(b->lane_stream);  // its pending work completes first
+    if (b->lane_fork) cudaEventDestroy(b->lane_fork);
+    if (b->lane_done) cudaEventDestroy(b->lane_done);
     // pending work on the side streams completes before their resources are released
     for (cudaStream_t s : b->aux) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->aux_done) cudaEventDestroy(e);
@@ -1003,6 +1054,7 @@ grlb_status grlb_batch_set_stream(grlb_batch* b, void* stream) {
     GRLB_CU(order_after_domains(b));
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    drop_lane_graphs(b);  // lane 0's graph was captured on the old stream
     return GRLB_OK;
 }
 
@@ -1029,13 +1081,20 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
     if (!b) return fail(GRLB_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(GRLB_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return GRLB_OK;
-    // large domains: the single-domain sweep, one launch per step (bitwise = grlb_step), each
-    // domain on its own stream forked from the batch stream
-    int nsolo = 0;
-    for (size_t i = 0; i < b->doms.size(); ++i) nsolo += (b->active[i] && b->solo[i]) ? 1 : 0;
-    if (nsolo > 0) {
+    // domains advanced by the single-domain sweep (every domain under GRLB_SCHED_CONCURRENT, the
+    // large ones otherwise): grlb_step's stepping (graph replays where they apply), bitwise its
+    // result, on up to kSoloLanes side streams forked from the batch stream -- the largest
+    // domains first, dealt round-robin, so that the lanes carry similar work and their kernels
+    // run concurrently, filling one another's waves
+    std::vector<size_t> solo;
+    for (size_t i = 0; i < b->doms.size(); ++i)
+        if (b->active[i] && b->solo[i]) solo.push_back(i);
+    std::stable_sort(solo.begin(), solo.end(),
+                     [&](size_t a, size_t c) { return b->doms[a]->D.plane > b->doms[c]->D.plane; });
+    const int nlanes = (int)std::min<size_t>(solo.size(), kSoloLanes);
+    if (nlanes > 0) {
         if (!b->fork) GRLB_CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-        while ((int)b->aux.size() < nsolo) {  // aux[k] and aux_done[k] are created in pairs
+        while ((int)b->aux.size() < nlanes) {  // aux[k] and aux_done[k] are created in pairs
             cudaStream_t s;
             cudaEvent_t ev;
             GRLB_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -1048,24 +1107,20 @@ grlb_status grlb_batch_step(grlb_batch* b, int nsteps) {
             b->aux_done.push_back(ev);
         }
         GRLB_CU(cudaEventRecord(b->fork, b->stream));
-        int k = 0;
-        for (size_t i = 0; i < b->doms.size(); ++i) {
-            if (!b->active[i] || !b->solo[i]) continue;
-            grlb_domain* d = b->doms[i];
-            GRLB_CU(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+        for (int k = 0; k < nlanes; ++k) GRLB_CU(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+        for (size_t j = 0; j < solo.size(); ++j) {
+            grlb_domain* d = b->doms[solo[j]];
             cudaStream_t keep = d->stream;
-            d->stream = b->aux[k];
-            grlb_status st = GRLB_OK;
-            for (int n = 0; n < nsteps && st == GRLB_OK; ++n) st = sweep_once(d, false);
+            d->stream = b->aux[j % nlanes];
+            const grlb_status st = step_domain(d, nsteps);
             d->stream = keep;
             if (st != GRLB_OK) return st;
-            GRLB_CU(cudaEventRecord(b->aux_done[k], b->aux[k]));
-            ++k;
         }
+        for (int k = 0; k < nlanes; ++k) GRLB_CU(cudaEventRecord(b->aux_done[k], b->aux[k]));
     }
     grlb_status tst = GRLB_OK;
     if (b->ntiles > 0) tst = batch_table_steps(b, nsteps);
-    for (int k = 0; k < nsolo; ++k) GRLB_CU(cudaStreamWaitEvent(b->stream, b->aux_done[k], 0));
+    for (int k = 0; k < nlanes; ++k) GRLB_CU(cudaStreamWaitEvent(b->stream, b->aux_done[k], 0));
     return tst;
 }
 
@@ -1095,23 +1150,55 @@ static grlb_status batch_table_steps(grlb_batch* b, int nsteps) {
         GRLB_CU(cudaMemcpyAsync(b->d_doms, b->h_doms.data(), b->doms.size() * sizeof(DomainDev),
                                 cudaMemcpyHostToDevice, b->stream));
     }
-    int done = 0;
-    if (b->cfg.use_graph && b->stream != nullptr && nsteps >= 2) {
-        if (!b->graph) {
-            cudaGraph_t g;
-            GRLB_CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_batch_step(b, 0);
-            if (e == cudaSuccess) e = enqueue_batch_step(b, 1);
-            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-            if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
-            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&b->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    const int nl = b->slot0 >= 0 ? b->nlanes : 1;
+    if (nl == 2) {
+        if (!b->lane_stream) {  // the lane stream and its two events exist together or not at all
+            cudaStream_t ls = nullptr;
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            cudaError_t e = cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                if (ls) cudaStreamDestroy(ls);
+                for (cudaEvent_t x : ev)
+                    if (x) cudaEventDestroy(x);
+                return cuda_fail(e, "batch lane stream");
+            }
+            b->lane_stream = ls;
+            b->lane_fork = ev[0];
+            b->lane_done = ev[1];
         }
-        for (; done + 2 <= nsteps; done += 2) GRLB_CU(cudaGraphLaunch(b->graph, b->stream));
+        GRLB_CU(cudaEventRecord(b->lane_fork, b->stream));  // after the record upload
+        GRLB_CU(cudaStreamWaitEvent(b->lane_stream, b->lane_fork, 0));
     }
-    for (; done < nsteps; ++done) GRLB_CU(enqueue_batch_step(b, done & 1));
+    for (int lane = 0; lane < nl; ++lane) {
+        cudaStream_t st = lane == 0 ? b->stream : b->lane_stream;
+        cudaGraphExec_t& G = b->slot0 >= 0 ? b->lane_graph[lane] : b->graph;
+        int done = 0;
+        if (b->cfg.use_graph && st != nullptr && nsteps >= 2) {
+            if (!G) {
+                cudaGraph_t g;
+                GRLB_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = enqueue_batch_step(b, 0, lane, st);
+                if (e == cudaSuccess) e = enqueue_batch_step(b, 1, lane, st);
+                cudaError_t e2 = cudaStreamEndCapture(st, &g);
+                if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+                if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&G, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    G = nullptr;
+                    return cuda_fail(e, "cudaGraphInstantiate");
+                }
+            }
+            for (; done + 2 <= nsteps; done += 2) GRLB_CU(cudaGraphLaunch(G, st));
+        }
+        for (; done < nsteps; ++done) GRLB_CU(enqueue_batch_step(b, done & 1, lane, st));
+    }
+    if (nl == 2) {
+        GRLB_CU(cudaEventRecord(b->lane_done, b->lane_stream));
+        GRLB_CU(cudaStreamWaitEvent(b->stream, b->lane_done, 0));
+    }
     for (size_t i = 0; i < b->doms.size(); ++i) {
         if (!b->active[i] || b->solo[i]) continue;
         grlb_domain* d = b->doms[i];

@@ -5,11 +5,12 @@ Requests arrive over time.  A request is admitted as soon as its populations fit
 budget (FIFO, head of line waits) and a slot is free; its domain is created and initialised
 on the device and stays resident until it finishes.  Resident domains advance together,
 `chunk` steps at a time, so a request that arrives while others run joins at the next chunk
-boundary.  Per chunk every small resident domain advances (they share one persistent
-batched launch per step and storage/collision group, CUDA-graph step loop), and of the large
-ones (each fills the GPU on its own) only the one with the least remaining work
-(cells x steps) — shortest-remaining-work-first, so short large requests are not held
-behind long ones.  A finished request's conserved fields are read back and its memory is
+boundary.  Per chunk every small resident domain advances (one batch call: under the default
+schedule each domain replays its own single-domain sweeps from a CUDA graph, the domains spread
+over concurrent streams; the table schedules share one launch per step and storage/collision
+group), and of the large ones (each fills the GPU on its own) only the one with the least
+remaining work (cells x steps) — shortest-remaining-work-first, so short large requests are not
+held behind long ones.  A finished request's conserved fields are read back and its memory is
 released, which may admit waiting requests.
 
 With one_buffer_large, large requests keep one population buffer (AA pattern: half their

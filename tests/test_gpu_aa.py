@@ -102,4 +102,8 @@ def test_in_place_refuses_sources_and_batches():
     with pytest.raises(capi.GrlbError):
         capi.grlb_set_source_device(d.h, 1)
     with pytest.raises(capi.GrlbError):
-        capi.grlb_batch_create([d.h])
+        capi.grlb_batch_create([d.h], schedule=capi.SCHED_TABLE_CONST)
+    b = capi.grlb_batch_create([d.h])          # the concurrent schedule takes it
+    capi.grlb_batch_step(b, 3)
+    capi.grlb_batch_destroy(b)
+    assert d.steps == 3

@@ -1,11 +1,14 @@
-"""Batched sweep: many uneven domains (Becker tubes, Taylor-Green boxes, mixed storage and
-collision) advanced by one persistent launch per step over a tile table.
+"""Batches: many uneven domains (Becker tubes, Taylor-Green boxes, mixed storage and
+collision) advanced by one call, under the three schedules: concurrent single-domain sweeps
+(default; bitwise grlb_step), and one launch per step over all small domains with the records
+in the constant table or in device memory (tile table).
 
-* A domain's batched result is bitwise independent of the other domains in the launch (alone
-  in a batch == in the mix).
-* It equals the solo single-domain sweep within FP32 rounding (the two kernels read the domain
-  constants from different memory spaces, so the compiler may contract different products;
-  relative L-infinity <= 1e-6 after 30 steps).
+* A domain's batched result is bitwise independent of the other domains in the batch (alone
+  in a batch == in the mix), under every schedule.
+* Under the concurrent schedule it is bitwise the solo run; under the table schedules it equals
+  the solo single-domain sweep within FP32 rounding (the kernels read the domain constants from
+  different memory spaces, so the compiler may contract different products; relative
+  L-infinity <= 1e-6 after 30 steps).
 * Every domain of the mix matches the FP64 oracle after 100 batched steps: relative L-inf
   <= 1e-5 for smooth fields and relative L1 <= 1e-4 for the shock tubes (FP32 storage; the
   FP16 / BF16 domains within the loose bounds of their other oracle comparisons).
@@ -43,10 +46,14 @@ def solo(case, n):
     return Q, raw
 
 
-def batched_alone(case, n, block_x=0, use_graph=1):
+SCHEDULES = [capi.SCHED_CONCURRENT, capi.SCHED_TABLE_CONST, capi.SCHED_TABLE]
+TABLES = [capi.SCHED_TABLE_CONST, capi.SCHED_TABLE]
+
+
+def batched_alone(case, n, block_x=0, use_graph=1, schedule=capi.SCHED_TABLE_CONST):
     d = capi.Domain(case.params)
     d.init(case.rho, case.u, case.p)
-    b = capi.grlb_batch_create([d.h], block_x=block_x, use_graph=use_graph)
+    b = capi.grlb_batch_create([d.h], block_x=block_x, use_graph=use_graph, schedule=schedule)
     capi.grlb_batch_step(b, n)
     raw = capi.grlb_save(d.h)[32:]
     capi.grlb_batch_destroy(b)
@@ -54,15 +61,17 @@ def batched_alone(case, n, block_x=0, use_graph=1):
     return raw
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("use_graph,nsteps,block_x", [(1, 30, 0), (0, 17, 64), (1, 13, 32)])
-def test_batch_equals_solo_runs(use_graph, nsteps, block_x):
+def test_batch_equals_solo_runs(use_graph, nsteps, block_x, schedule):
     cases = mixed_cases()
     doms = []
     for c in cases:
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    b = capi.grlb_batch_create([d.h for d in doms], block_x=block_x, use_graph=use_graph)
+    b = capi.grlb_batch_create([d.h for d in doms], block_x=block_x, use_graph=use_graph,
+                               schedule=schedule)
     # two calls, so the second starts from each domain's flipped buffer
     k = nsteps // 2
     capi.grlb_batch_step(b, k)
@@ -71,25 +80,29 @@ def test_batch_equals_solo_runs(use_graph, nsteps, block_x):
         assert d.steps == nsteps
         raw = capi.grlb_save(d.h)[32:]
         # alone in a batch == in the mix, bitwise
-        assert np.array_equal(raw, batched_alone(c, nsteps, block_x, use_graph)), c.params.name
+        assert np.array_equal(raw, batched_alone(c, nsteps, block_x, use_graph, schedule)), c.params.name
+        Q_ref, raw_ref = solo(c, nsteps)
+        if schedule == capi.SCHED_CONCURRENT:   # the single-domain sweep itself
+            assert np.array_equal(raw, raw_ref), c.params.name
+            continue
         # == the solo sweep within FP32 rounding; with 16-bit storage an FP32 rounding difference
         # between the two kernels can round a stored value to the neighbouring 16-bit number
         # (the tolerance of the other 16-bit path comparisons)
-        Q_ref, _ = solo(c, nsteps)
         err = rel_linf(d.conserved(), Q_ref)
         tol = 1e-6 if c.params.storage == inputs.STORE_F32 else 1e-2
         assert np.all(err <= tol), (c.params.name, err)
     capi.grlb_batch_destroy(b)
 
 
-def test_inactive_domains_do_not_move():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_inactive_domains_do_not_move(schedule):
     cases = mixed_cases()[:3]
     doms = []
     for c in cases:
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=schedule)
     before = capi.grlb_save(doms[1].h)[32:].copy()
     capi.grlb_batch_set_active(b, [1, 0, 1])
     capi.grlb_batch_step(b, 6)
@@ -98,7 +111,7 @@ def test_inactive_domains_do_not_move():
     capi.grlb_batch_set_active(b, None)
     capi.grlb_batch_step(b, 4)
     assert doms[1].steps == 4 and doms[0].steps == 10
-    assert np.array_equal(capi.grlb_save(doms[0].h)[32:], batched_alone(cases[0], 10))
+    assert np.array_equal(capi.grlb_save(doms[0].h)[32:], batched_alone(cases[0], 10, schedule=schedule))
     capi.grlb_batch_destroy(b)
 
 
@@ -113,7 +126,8 @@ def test_large_domains_run_the_single_domain_sweep_inside_a_batch():
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, solo_min_cells=50000)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, solo_min_cells=50000,
+                               schedule=capi.SCHED_TABLE_CONST)
     capi.grlb_batch_step(b, 7)
     capi.grlb_batch_step(b, 6)
     _, raw_ref = solo(big, 13)
@@ -124,17 +138,18 @@ def test_large_domains_run_the_single_domain_sweep_inside_a_batch():
     capi.grlb_batch_destroy(b)
 
 
+@pytest.mark.parametrize("schedule", TABLES)
 @pytest.mark.parametrize("tile", [1, 32, 64, 128])
-def test_every_tile_shape_gives_the_same_result(tile):
+def test_every_tile_shape_gives_the_same_result(tile, schedule):
     """Linear tiles (1) and x-tiles of every width: bitwise the same batched result."""
     cases = mixed_cases()
-    ref = [batched_alone(c, 9) for c in cases]
+    ref = [batched_alone(c, 9, schedule=schedule) for c in cases]
     doms = []
     for c in cases:
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=schedule)
     capi.grlb_batch_set_tile_x(b, [tile] * len(doms))
     capi.grlb_batch_step(b, 9)
     for c, d, r in zip(cases, doms, ref):
@@ -157,14 +172,15 @@ def oracle_gate(case, Q, R):
     return np.all(err[fields] <= tol), err
 
 
-def test_batched_domains_match_the_oracle():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_batched_domains_match_the_oracle(schedule):
     cases = mixed_cases()
     doms = []
     for c in cases:
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=schedule)
     capi.grlb_batch_step(b, 100)
     capi.grlb_batch_destroy(b)
     for c, d in zip(cases, doms):
@@ -185,18 +201,19 @@ def test_batches_beyond_the_constant_record_slots_fall_back_to_the_tile_table():
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    big = capi.grlb_batch_create([d.h for d in doms], use_graph=1)   # 170 > 160: tile table
+    big = capi.grlb_batch_create([d.h for d in doms], use_graph=1,   # 170 > 160: tile table
+                                 schedule=capi.SCHED_TABLE_CONST)
     capi.grlb_batch_step(big, 9)
     capi.grlb_batch_destroy(big)
     for c, d in zip(cases[:12], doms[:12]):
-        ref = batched_alone(c, 9)                                    # constant-table path
+        ref = batched_alone(c, 9)                                    # constant-table records
         got = np.frombuffer(capi.grlb_save(d.h)[32:].tobytes(), np.float32)
         want = np.frombuffer(ref.tobytes(), np.float32)
         assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), c.params.name
     # many batches in turn reuse the slots (each must find its own records)
     for rnd in range(3):
         part = doms[rnd * 50:(rnd + 1) * 50]
-        b = capi.grlb_batch_create([d.h for d in part], use_graph=1)
+        b = capi.grlb_batch_create([d.h for d in part], use_graph=1, schedule=capi.SCHED_TABLE_CONST)
         capi.grlb_batch_step(b, 2)
         capi.grlb_batch_destroy(b)
         assert all(d.steps == 11 for d in part)
@@ -204,19 +221,19 @@ def test_batches_beyond_the_constant_record_slots_fall_back_to_the_tile_table():
         d.close()
 
 
-def test_record_modes_agree():
-    """Records in the constant table (record_mode 0) or in device memory (1): the same
-    updates, within FP32 rounding (the kernels read the constants from different memory
-    spaces); each mode bitwise reproducible."""
+def test_table_schedules_agree():
+    """Records in the constant table or in device memory: the same updates, within FP32
+    rounding (the kernels read the constants from different memory spaces); each schedule
+    bitwise reproducible."""
     cases = mixed_cases()
     res = {}
-    for mode in (0, 1, 0):
+    for mode in (capi.SCHED_TABLE_CONST, capi.SCHED_TABLE, capi.SCHED_TABLE_CONST):
         doms = []
         for c in cases:
             d = capi.Domain(c.params)
             d.init(c.rho, c.u, c.p)
             doms.append(d)
-        b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, record_mode=mode)
+        b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=mode)
         capi.grlb_batch_step(b, 11)
         capi.grlb_batch_destroy(b)
         got = [d.conserved() for d in doms]
@@ -225,8 +242,58 @@ def test_record_modes_agree():
         res[mode] = got
         for d in doms:
             d.close()
-    for c, x, y in zip(cases, res[0], res[1]):
+    for c, x, y in zip(cases, res[capi.SCHED_TABLE_CONST], res[capi.SCHED_TABLE]):
         tol = 1e-6 if c.params.storage == inputs.STORE_F32 else 1e-2
         assert np.all(rel_linf(x, y) <= tol), c.params.name
     with pytest.raises(capi.GrlbError):
-        capi.grlb_batch_create([capi.Domain(cases[0].params).h], record_mode=2)
+        capi.grlb_batch_create([capi.Domain(cases[0].params).h], schedule=3)
+
+
+def test_two_lanes_give_each_domain_its_solo_batched_result():
+    """Constant-table schedule: with enough tiles (here ~2000) the small domains are split into
+    two lanes stepped on two streams; every domain's result is still bitwise what it is batched
+    alone (one lane)."""
+    om = inputs.becker_tied_omega(8.0)
+    cases = [inputs.tgv3d(48, mach=0.8, re=100.0), inputs.tgv3d(44, mach=1.0, re=100.0),
+             inputs.becker(2048, mach=2.5, cells_per_front=8, omega=om, cfl_max=0.1, ny=4, nz=4),
+             inputs.becker(1500, mach=4.0, cells_per_front=8, omega=om, cfl_max=0.1, ny=4, nz=4),
+             inputs.tgv3d(20, storage=inputs.STORE_F16)]
+    doms = []
+    for c in cases:
+        d = capi.Domain(c.params)
+        d.init(c.rho, c.u, c.p)
+        doms.append(d)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, solo_min_cells=10 ** 6,
+                               schedule=capi.SCHED_TABLE_CONST)
+    capi.grlb_batch_step(b, 5)
+    capi.grlb_batch_step(b, 8)
+    capi.grlb_batch_destroy(b)
+    for c, d in zip(cases, doms):
+        assert d.steps == 13
+        assert np.array_equal(capi.grlb_save(d.h)[32:], batched_alone(c, 13)), c.params.name
+        d.close()
+
+
+def test_concurrent_schedule_with_many_domains_and_one_buffer():
+    """Concurrent schedule: 40 domains over 32 side streams, one of them with one-buffer
+    streaming, each bitwise its grlb_step result; the batch stream sees all of it done."""
+    torch = pytest.importorskip("torch")
+    cases = [inputs.random_smooth(8 + s % 7, 5, 3 + s % 4, seed=s) for s in range(39)]
+    one = inputs.tgv3d(24)
+    one.params = one.params.replace(streaming=1)
+    cases.append(one)
+    stream = torch.cuda.Stream()
+    doms = []
+    for c in cases:
+        d = capi.Domain(c.params, stream=stream.cuda_stream)
+        d.init(c.rho, c.u, c.p)
+        doms.append(d)
+    b = capi.grlb_batch_create([d.h for d in doms])
+    capi.grlb_batch_step(b, 21)
+    capi.grlb_batch_step(b, 18)
+    capi.grlb_batch_destroy(b)
+    for c, d in zip(cases, doms):
+        assert d.steps == 39
+        _, raw = solo(c, 39)
+        assert np.array_equal(capi.grlb_save(d.h)[32:], raw), c.params.name
+        d.close()

@@ -275,9 +275,9 @@ def oracle_update_at(fpre_raw, prm, cells):
     return out
 
 
-@pytest.mark.parametrize("n", [256])
-def test_full_size_taylor_green_sampled_cells(n):
-    c = inputs.tgv3d(n)
+@pytest.mark.parametrize("n,collision", [(256, inputs.COLL_RLB_SENSOR), (256, inputs.COLL_RLB_GATED)])
+def test_full_size_taylor_green_sampled_cells(n, collision):
+    c = inputs.tgv3d(n, collision=collision)
     d = gpu_run(c, 5)
     pre = capi.grlb_save(d.h)
     d.step(1)
