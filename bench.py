@@ -416,6 +416,7 @@ def run_zslab(args):
     sweep (decomp.SlabRank: pack kernel, NCCL send / receive, unpack kernel).  A bench step =
     initialisation from device-resident fields + 50 exchange-and-sweep iterations; value =
     the interior cell updates of all ranks over the slowest rank's time."""
+    import numpy as np
     import torch
     import torch.distributed as dist
     from paper_2609_16361_b300 import decomp, inputs
@@ -455,7 +456,7 @@ def run_zslab(args):
     ms = reduce_max_over_ranks([e0.elapsed_time(e1)], ws, dev)[0]
     cells = n ** 3
     Q = r.conserved_interior()
-    finite = bool(__import__("numpy").isfinite(Q).all())
+    finite = bool(np.isfinite(Q).all())
     r.close()
     if rank == 0:
         line = {"metric": "MLUP/s", "value": job_mlups(ws, cells, SWEEPS_PER_STEP * args.steps, ms / 1e3),

@@ -1030,6 +1030,12 @@ void grlb_batch_destroy(grlb_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_doms) cudaFreeAsync(b->d_doms, b->stream);
     if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
+    // slots taken but never written (no step ran): their previous holders' release events have
+    // not been waited for yet, so this batch's release must follow them too
+    for (const auto& w : b->slot_waits) {
+        const EventRef* r = static_cast<const EventRef*>(w.get());
+        if (r && r->ev) cudaStreamWaitEvent(b->stream, r->ev, 0);
+    }
     give_slots(b->slot0, b->nsmall, b->stream);
     drop_lane_graphs(b);
     if (b->lane_stream) cudaStreamDestroy(b->lane_stream);  // its pending work completes first
