@@ -223,7 +223,7 @@ def run_reference(args):
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"tgv{n}_fp32_rlb_sensor (oracle: FP64, bounded slab)",
+            "config": {"workload": f"tgv{n}_f32_rlb (oracle: FP64, bounded slab)",
                        "grid": [n, n, 16], "sweeps_per_step": 1},
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0,
