@@ -162,8 +162,9 @@ TUBES = ("becker", "sod")
 
 def oracle_gate(case, Q, R):
     """The oracle comparison of a domain: rel L-inf 1e-5 on smooth fields, rel L1 1e-4 on the
-    tubes (FP32 storage); 1e-2 / 6e-2 for FP16 / BF16 storage (no independent pin exists for
-    the 16-bit modes; these are the bounds of their other oracle comparisons)."""
+    tubes (FP32 storage); 1e-2 / 6e-2 for FP16 / BF16 storage (the bounds of their other
+    multi-step oracle comparisons; their rounding is pinned one sweep at a time in
+    test_gpu_storage.py)."""
     tube = case.params.name.startswith(TUBES)
     err = rel_l1(Q, R) if tube else rel_linf(Q, R)
     fields = [0, 1, 4] if tube else [0, 1, 2, 3, 4]

@@ -145,3 +145,14 @@ def test_checkpoint_decode_reads_the_documented_brick_layout(storage):
         np.testing.assert_allclose(f[q], stored_exact[q] / enc[k] + shift, rtol=0, atol=1e-15)
     cells = np.array([0, 127, 128, 209])
     np.testing.assert_array_equal(decode_populations(raw, prm, cells=cells), f[:, cells])
+
+
+def test_bf16_rounding_helper_matches_torch():
+    """The storage test's own bfloat16 rounding (nearest, ties to even) against torch's
+    conversion, on the CPU."""
+    torch = pytest.importorskip("torch")
+    from tests.test_gpu_storage import bf16_round
+    x = np.random.default_rng(1).normal(size=20000) * np.logspace(-3, 3, 20000)
+    x = np.concatenate([x, [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 0.0]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(bf16_round(x), ref)
