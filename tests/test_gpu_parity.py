@@ -295,6 +295,48 @@ def test_full_size_taylor_green_sampled_cells(n, collision):
         assert np.abs(got[blk] - want[blk]).max() / scale < 2e-6
 
 
+def oracle_update_info(fpre_raw, prm, cells):
+    """As oracle_update_at, with each sampled cell's oracle record (chi, floors)."""
+    P = oracle.lattice_params(prm)
+    nx, ny, nz = prm.nx, prm.ny, prm.nz
+    x, y, z = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    planes = {}
+    for i in range(7):
+        src = (x - CI[i][0]) % nx + nx * ((y - CI[i][1]) % ny + ny * ((z - CI[i][2]) % nz))
+        planes[i] = decode_populations(fpre_raw, prm, cells=src)
+    out = np.zeros((35, cells.size))
+    chi = np.zeros(cells.size)
+    for n in range(cells.size):
+        fhat = np.array([planes[i][7 * k + i, n] for k in range(5) for i in range(7)])
+        out[:, n], info = oracle.cell(P, fhat)
+        chi[n] = info.chi
+    return out, chi
+
+
+def test_developed_flow_sampled_cells_with_shocklets():
+    """The 128^3 supersonic vortex at step 1000 (t_c 4.9: shocklets formed, the sensor active in
+    ~9 % of the cells; the algorithm as written at omega_min 1.8, Chapman-Enskog start), in the
+    launch configuration of the series workload: one sweep of 2500 sampled cells, among them
+    cells where the sensor fires, against the oracle's update of the same cells."""
+    c = inputs.tgv3d(128, omega_min=1.8)
+    d = capi.Domain(c.params)
+    d.init(c.rho, c.u, c.p, ce_init=True)
+    d.step(1000)
+    pre = capi.grlb_save(d.h)
+    d.step(1)
+    post = capi.grlb_save(d.h)
+    rng = np.random.default_rng(7)
+    cells = np.unique(rng.integers(0, c.params.ncells, 2500))
+    want, chi = oracle_update_info(pre, c.params, cells)
+    got = decode_populations(post, c.params, cells=cells)
+    assert (chi > 0).sum() >= 50, int((chi > 0).sum())
+    for k in range(5):
+        blk = slice(7 * k, 7 * k + 7)
+        scale = max(np.abs(want[blk]).max(), 1e-12)
+        assert np.abs(got[blk] - want[blk]).max() / scale < 2e-6, k
+    d.close()
+
+
 def test_full_size_conservation_over_diagnostic_sweeps():
     c = inputs.tgv3d(256)
     d = capi.Domain(c.params)

@@ -305,9 +305,9 @@ def test_becker_profile_solves_the_viscous_shock_ode():
     np.testing.assert_allclose(en[5:-5], (E1 + p1) * u1, rtol=2e-5)
 
 
-def sod_errors(nx):
+def sod_errors(nx, collision=inputs.COLL_RLB_SENSOR):
     c = inputs.sod(nx, steps=int(round(0.2 / (0.08 / nx))))
-    o = oracle.Oracle(c.params)
+    o = oracle.Oracle(c.params.replace(collision=collision))
     o.init_primitive(c.rho, c.u, c.p)
     o.step(c.meta["steps"])
     rho, u, p, _ = o.primitive()
@@ -318,9 +318,11 @@ def sod_errors(nx):
     return L2(rho, re), L2(p, pe), L2(u[0], ue)
 
 
-def test_sod_tube_against_exact_riemann_solution():
-    """Sod tube, 400 cells, 1000 steps to t = 0.2 (dt/dx = 0.08): inviscid limit."""
-    er, ep, eu = sod_errors(400)
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_RLB_GATED])
+def test_sod_tube_against_exact_riemann_solution(collision):
+    """Sod tube, 400 cells, 1000 steps to t = 0.2 (dt/dx = 0.08): inviscid limit; the
+    regularized collision of Alg. 1 and the gated reading of Sec. 2.2 alike."""
+    er, ep, eu = sod_errors(400, collision)
     assert er < 5e-2 and ep < 5e-2 and eu < 1e-1
 
 
@@ -334,13 +336,13 @@ def test_sod_tube_error_comparable_to_paper_table():
     assert er < 2.5 * gold["rho"][0] and ep < 2.5 * gold["p"][0] and eu < 2.5 * gold["u"][0]
 
 
-def becker_error(nx, cpf):
+def becker_error(nx, cpf, collision=inputs.COLL_RLB_SENSOR):
     # omega tied to dt: tau - 1/2 proportional to dt, omega = 1.99 at 128 cells per front
     om = 1.0 / (0.5 + (1.0 / 1.99 - 0.5) * 128.0 / cpf)
     c = inputs.becker(nx, cells_per_front=cpf, omega=om, cfl_max=0.1)
     x = c.meta["x"]
     re, ue, pe = exact.becker_profile(x, 2.0, c.meta["mu"], 0.5)
-    o = oracle.Oracle(c.params)
+    o = oracle.Oracle(c.params.replace(collision=collision))
     o.init_primitive(re, np.stack([ue, 0 * ue, 0 * ue]), pe)
     o.step(int(1.0 / c.params.dt))
     rho, u, p, _ = o.primitive()
@@ -354,12 +356,13 @@ def becker_error(nx, cpf):
     return L2(rho, r2), L2(p, p2), L2(u[0], u2)
 
 
-def test_becker_viscous_shock_converges_at_second_order():
+@pytest.mark.parametrize("collision", [inputs.COLL_RLB_SENSOR, inputs.COLL_RLB_GATED])
+def test_becker_viscous_shock_converges_at_second_order(collision):
     """Becker closed form, 8 -> 16 cells across the front: the error falls at about second
-    order and stays below the paper's Tab. becker_conv rows."""
+    order and stays below the paper's Tab. becker_conv rows (both readings of the collision)."""
     gold = json.load(open(os.path.join(GOLDEN, "paper_tables.json")))["becker_conv"]
-    e8 = becker_error(128, 8)
-    e16 = becker_error(256, 16)
+    e8 = becker_error(128, 8, collision)
+    e16 = becker_error(256, 16, collision)
     for a, b in zip(e8, e16):
         assert math.log2(a / b) > 1.5
     assert e8[0] < gold["rho"][0] and e16[0] < gold["rho"][1]
