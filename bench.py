@@ -680,7 +680,7 @@ def run_batch_tubes(args):
         d.init(c.rho, c.u, c.p)
     sched = {"concurrent": capi.SCHED_CONCURRENT, "table_const": capi.SCHED_TABLE_CONST,
              "table": capi.SCHED_TABLE}[args.schedule]
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=sched)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=sched, max_lanes=args.max_lanes)
     capi.grlb_batch_set_stream(b, st)
     capi.grlb_batch_step(b, 20)   # warm-up; also captures the step graphs (>= 16 steps)
     stream.synchronize()
@@ -698,7 +698,7 @@ def run_batch_tubes(args):
     line = {"metric": "batched MLUP/s (48 Becker tubes)", "value": cells * args.batch_steps / t / 1e6,
             "unit": "MLUP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "48 Becker tubes 128-2048 x 4 x 4 (M 1.5-5), seed 0", "cells": cells,
-                       "steps": args.batch_steps, "schedule": args.schedule},
+                       "steps": args.batch_steps, "schedule": args.schedule, "max_lanes": args.max_lanes},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_source": f"{src} hbm_gbs", "bytes_per_cell": 280}}
     print(json.dumps(line), flush=True)
@@ -1244,6 +1244,7 @@ def main():
                     help="leave the batched and served legs out of the default line")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "batch", "serve", "precision", "tgv-series",
                              "tgv-map", "batch-tubes", "capacity", "spectral", "slabs", "cases"])
+    ap.add_argument("--max-lanes", type=int, default=0, help="batch-tubes: streams of the table schedule (0 = 2)")
     ap.add_argument("--schedule", default="concurrent", choices=["concurrent", "table_const", "table"],
                     help="batch-tubes: concurrent single-domain sweeps, or one launch per step with "
                          "constant-table / device-memory records")

@@ -225,7 +225,7 @@ int64_t grlb_steps_done(const grlb_domain* d);
  *    launch per step and (storage, collision) group of the batched sweep, one 128-thread CTA per
  *    tile, their records in a constant table of 160 slots shared by the process (a batch that
  *    finds too few free slots runs as GRLB_SCHED_TABLE); with enough tiles they are split into
- *    two groups on two streams.  Large domains as under GRLB_SCHED_CONCURRENT.
+ *    groups of about equal tile counts on up to max_lanes streams.  Large domains as under GRLB_SCHED_CONCURRENT.
  *  GRLB_SCHED_TABLE: as GRLB_SCHED_TABLE_CONST with the records in device memory, staged in
  *    shared memory by a persistent kernel walking a tile table.
  * Under the two table schedules a CTA covers tile_x cells along x times 128/tile_x rows, a
@@ -242,6 +242,8 @@ typedef struct {
     int32_t use_graph;      /* table schedules: 1 = replay the table launches of two steps
                                from a CUDA graph                                            */
     int32_t schedule;       /* grlb_schedule                                                */
+    int32_t max_lanes;      /* GRLB_SCHED_TABLE_CONST: at most this many streams (1..8; 0 = 2)
+                               over which the small domains are split, one per 592 tiles    */
 } grlb_batch_config;
 
 grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_batch_config* cfg,

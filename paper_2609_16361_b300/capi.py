@@ -55,7 +55,7 @@ class grlb_diag(C.Structure):
 
 class grlb_batch_config(C.Structure):
     _fields_ = [("block_x", C.c_int32), ("solo_min_cells", C.c_int32), ("use_graph", C.c_int32),
-                ("schedule", C.c_int32)]
+                ("schedule", C.c_int32), ("max_lanes", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -275,9 +275,10 @@ def grlb_steps_done(h) -> int:
 SCHED_CONCURRENT, SCHED_TABLE_CONST, SCHED_TABLE = 0, 1, 2
 
 
-def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0, schedule=SCHED_CONCURRENT):
+def grlb_batch_create(handles, block_x=0, use_graph=1, solo_min_cells=0, schedule=SCHED_CONCURRENT,
+                      max_lanes=0):
     arr = (C.c_void_p * len(handles))(*[h.value for h in handles])
-    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, schedule)
+    cfg = grlb_batch_config(block_x, solo_min_cells, use_graph, schedule, max_lanes)
     b = C.c_void_p()
     check(lib().grlb_batch_create(arr, len(handles), C.byref(cfg), C.byref(b)))
     return b

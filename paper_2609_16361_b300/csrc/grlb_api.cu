@@ -720,14 +720,16 @@ struct grlb_batch {
     std::vector<int> small_idx;
     std::vector<DomainDev> h_recs;
     std::vector<grlb::BatchLaunch> launch;  // [lane * kGroups + group]
-    // the small domains split into nlanes groups of about equal tile counts (two when there are
-    // enough tiles), each stepped on its own stream (lane 0: `stream`, lane 1: lane_stream,
-    // forked from and joined back into `stream`) with its own graph: the domains are
-    // independent, so one lane's launches fill the other's wave ramp and tail
+    // the small domains split into nlanes groups of about equal tile counts (up to
+    // kTableLanes when there are enough tiles), each stepped on its own stream (lane 0:
+    // `stream`, lane l > 0: lane_stream[l - 1], forked from and joined back into `stream`) with
+    // its own graph: the domains are independent, so one lane's launches fill the others' wave
+    // ramp and tail
     int nlanes = 1;
-    cudaGraphExec_t lane_graph[2] = {nullptr, nullptr};
-    cudaStream_t lane_stream = nullptr;
-    cudaEvent_t lane_fork = nullptr, lane_done = nullptr;
+    cudaGraphExec_t lane_graph[grlb::kTableLanes] = {};
+    cudaStream_t lane_stream[grlb::kTableLanes - 1] = {};
+    cudaEvent_t lane_done[grlb::kTableLanes - 1] = {};
+    cudaEvent_t lane_fork = nullptr;
     std::vector<std::shared_ptr<void>> slot_waits;  // release events of the slots' last holders
     // large domains step on streams of their own, forked from and joined back into `stream`,
     // so that their launches overlap one another's tails and the table launches
@@ -838,9 +840,13 @@ void drop_lane_graphs(grlb_batch* b) {
     }
 }
 
-// Two lanes when the small domains have enough tiles for both to fill the device (at least
-// four waves of one CTA per SM each) and there are at least two of them.
-constexpr int64_t kLaneMinTiles = 4 * 2 * 148;
+// One lane per kLaneTiles tiles of the small domains (four waves of one CTA per SM each), at
+// most max_lanes (config; 0 = kDefaultLanes) and at most one per domain.  Measured on the
+// 48-tube class (0.79 / 0.85 / 0.83 / 0.79 of the copy bandwidth with 1 / 2 / 4 / 8 lanes): two
+// lanes fill each other's ramp and tail, more split the steps into launches too short to
+// reach full bandwidth themselves.
+constexpr int64_t kLaneTiles = 4 * 148;
+constexpr int kDefaultLanes = 2;
 
 grlb_status rebuild_launches(grlb_batch* b) {
     std::vector<size_t> small;
@@ -852,20 +858,22 @@ grlb_status rebuild_launches(grlb_batch* b) {
         tiles[i] = tiles_of(b, i);
         total += tiles[i];
     }
-    b->nlanes = (small.size() >= 2 && total >= kLaneMinTiles) ? 2 : 1;
-    // lane of each domain: largest first into the lane with fewer tiles
+    const int max_lanes = b->cfg.max_lanes > 0 ? std::min(b->cfg.max_lanes, grlb::kTableLanes) : kDefaultLanes;
+    b->nlanes = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)max_lanes, (int64_t)small.size(),
+                                                               total / kLaneTiles}));
+    // lane of each domain: largest first into the lane with the fewest tiles
     std::vector<int> lane_of(b->doms.size(), 0);
-    if (b->nlanes == 2) {
+    if (b->nlanes > 1) {
         std::vector<size_t> order = small;
         std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return tiles[a] > tiles[c]; });
-        int64_t load[2] = {0, 0};
+        std::vector<int64_t> load(b->nlanes, 0);
         for (size_t i : order) {
-            const int l = load[1] < load[0] ? 1 : 0;
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
             lane_of[i] = l;
             load[l] += tiles[i];
         }
     }
-    b->launch.assign(2 * kGroups, grlb::BatchLaunch{});
+    b->launch.assign(grlb::kTableLanes * kGroups, grlb::BatchLaunch{});
     for (grlb::BatchLaunch& L : b->launch) L.nd = 0;
     for (size_t i : small) {
         grlb::BatchLaunch& L = b->launch[lane_of[i] * kGroups + group_of(b->doms[i]->P)];
@@ -967,6 +975,10 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
         delete b;
         return fail(GRLB_EINVAL, "block_x must be 32, 64 or 128");
     }
+    if (b->cfg.max_lanes < 0 || b->cfg.max_lanes > grlb::kTableLanes) {
+        delete b;
+        return fail(GRLB_EINVAL, "max_lanes must be in [0, 8]");
+    }
     const int sched = b->cfg.schedule;
     if (sched != GRLB_SCHED_CONCURRENT && sched != GRLB_SCHED_TABLE_CONST && sched != GRLB_SCHED_TABLE) {
         delete b;
@@ -1038,9 +1050,11 @@ void grlb_batch_destroy(grlb_batch* b) {
     }
     give_slots(b->slot0, b->nsmall, b->stream);
     drop_lane_graphs(b);
-    if (b->lane_stream) cudaStreamDestroy(b->lane_stream);  // its pending work completes first
+    for (int l = 0; l < grlb::kTableLanes - 1; ++l) {  // pending work completes first
+        if (b->lane_stream[l]) cudaStreamDestroy(b->lane_stream[l]);
+        if (b->lane_done[l]) cudaEventDestroy(b->lane_done[l]);
+    }
     if (b->lane_fork) cudaEventDestroy(b->lane_fork);
-    if (b->lane_done) cudaEventDestroy(b->lane_done);
     // pending work on the side streams completes before their resources are released
     for (cudaStream_t s : b->aux) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->aux_done) cudaEventDestroy(e);
@@ -1157,28 +1171,26 @@ static grlb_status batch_table_steps(grlb_batch* b, int nsteps) {
                                 cudaMemcpyHostToDevice, b->stream));
     }
     const int nl = b->slot0 >= 0 ? b->nlanes : 1;
-    if (nl == 2) {
-        if (!b->lane_stream) {  // the lane stream and its two events exist together or not at all
+    if (nl > 1) {
+        if (!b->lane_fork) GRLB_CU(cudaEventCreateWithFlags(&b->lane_fork, cudaEventDisableTiming));
+        for (int l = 0; l + 1 < nl; ++l) {
+            if (b->lane_stream[l]) continue;  // a lane stream and its event exist together or not at all
             cudaStream_t ls = nullptr;
-            cudaEvent_t ev[2] = {nullptr, nullptr};
+            cudaEvent_t ev = nullptr;
             cudaError_t e = cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
             if (e != cudaSuccess) {
                 if (ls) cudaStreamDestroy(ls);
-                for (cudaEvent_t x : ev)
-                    if (x) cudaEventDestroy(x);
                 return cuda_fail(e, "batch lane stream");
             }
-            b->lane_stream = ls;
-            b->lane_fork = ev[0];
-            b->lane_done = ev[1];
+            b->lane_stream[l] = ls;
+            b->lane_done[l] = ev;
         }
         GRLB_CU(cudaEventRecord(b->lane_fork, b->stream));  // after the record upload
-        GRLB_CU(cudaStreamWaitEvent(b->lane_stream, b->lane_fork, 0));
+        for (int l = 0; l + 1 < nl; ++l) GRLB_CU(cudaStreamWaitEvent(b->lane_stream[l], b->lane_fork, 0));
     }
     for (int lane = 0; lane < nl; ++lane) {
-        cudaStream_t st = lane == 0 ? b->stream : b->lane_stream;
+        cudaStream_t st = lane == 0 ? b->stream : b->lane_stream[lane - 1];
         cudaGraphExec_t& G = b->slot0 >= 0 ? b->lane_graph[lane] : b->graph;
         int done = 0;
         if (b->cfg.use_graph && st != nullptr && nsteps >= 2) {
@@ -1201,9 +1213,9 @@ static grlb_status batch_table_steps(grlb_batch* b, int nsteps) {
         }
         for (; done < nsteps; ++done) GRLB_CU(enqueue_batch_step(b, done & 1, lane, st));
     }
-    if (nl == 2) {
-        GRLB_CU(cudaEventRecord(b->lane_done, b->lane_stream));
-        GRLB_CU(cudaStreamWaitEvent(b->stream, b->lane_done, 0));
+    for (int l = 0; l + 1 < nl; ++l) {
+        GRLB_CU(cudaEventRecord(b->lane_done[l], b->lane_stream[l]));
+        GRLB_CU(cudaStreamWaitEvent(b->stream, b->lane_done[l], 0));
     }
     for (size_t i = 0; i < b->doms.size(); ++i) {
         if (!b->active[i] || b->solo[i]) continue;

@@ -21,6 +21,7 @@ cudaError_t launch_batch_sweep(int storage, int coll, const DomainDev* doms, con
 // slot[i].  Tiles as in the tile-table sweep (tile_x cells x 128 / tile_x rows, or 128
 // consecutive cells when tile_x == 1).
 constexpr int kBatchSlots = 160;  // 160 x 336-byte records: 53.8 KB of the 64 KB constant bank
+constexpr int kTableLanes = 8;    // at most this many streams for the one-launch-per-step schedule
 struct BatchLaunch {
     int32_t nd;
     int32_t parity;

@@ -252,8 +252,8 @@ def test_table_schedules_agree():
 
 def test_two_lanes_give_each_domain_its_solo_batched_result():
     """Constant-table schedule: with enough tiles (here ~2000) the small domains are split into
-    two lanes stepped on two streams; every domain's result is still bitwise what it is batched
-    alone (one lane)."""
+    lanes stepped on their own streams (two by default, three with max_lanes 8, two with 2);
+    every domain's result is still bitwise what it is batched alone (one lane)."""
     om = inputs.becker_tied_omega(8.0)
     cases = [inputs.tgv3d(48, mach=0.8, re=100.0), inputs.tgv3d(44, mach=1.0, re=100.0),
              inputs.becker(2048, mach=2.5, cells_per_front=8, omega=om, cfl_max=0.1, ny=4, nz=4),
@@ -264,15 +264,21 @@ def test_two_lanes_give_each_domain_its_solo_batched_result():
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         doms.append(d)
-    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, solo_min_cells=10 ** 6,
-                               schedule=capi.SCHED_TABLE_CONST)
-    capi.grlb_batch_step(b, 5)
-    capi.grlb_batch_step(b, 8)
-    capi.grlb_batch_destroy(b)
-    for c, d in zip(cases, doms):
-        assert d.steps == 13
-        assert np.array_equal(capi.grlb_save(d.h)[32:], batched_alone(c, 13)), c.params.name
+    for max_lanes in (0, 8):
+        for d, c in zip(doms, cases):
+            d.init(c.rho, c.u, c.p)
+        b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, solo_min_cells=10 ** 6,
+                                   schedule=capi.SCHED_TABLE_CONST, max_lanes=max_lanes)
+        capi.grlb_batch_step(b, 5)
+        capi.grlb_batch_step(b, 8)
+        capi.grlb_batch_destroy(b)
+        for c, d in zip(cases, doms):
+            assert d.steps == 13
+            assert np.array_equal(capi.grlb_save(d.h)[32:], batched_alone(c, 13)), (c.params.name, max_lanes)
+    for d in doms:
         d.close()
+    with pytest.raises(capi.GrlbError):
+        capi.grlb_batch_create([capi.Domain(cases[0].params).h], max_lanes=9)
 
 
 def test_concurrent_schedule_with_many_domains_and_one_buffer():
