@@ -41,7 +41,7 @@ SWEEPS_PER_STEP = 50
 # collision readings: name -> (grlb_collision, kernel label)
 COLLISIONS = {"rlb": (1, "RLB"), "gated": (2, "RLB_GATED"), "bgk": (0, "BGK")}
 BYTES_PER_LUP = {0: 280, 1: 140, 2: 140}
-KERNEL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh",
+KERNEL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh", "paper_2609_16361_b300/csrc/grlb_check.cuh",
                   "paper_2609_16361_b300/csrc/grlb_kernels.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -76,7 +76,7 @@ def kernel_source_sha(sources=None):
 
 
 # the spectral post-processing's five kernels and the sweep header they include
-SPECTRAL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh",
+SPECTRAL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh", "paper_2609_16361_b300/csrc/grlb_check.cuh",
                     "paper_2609_16361_b300/csrc/grlb_spectral.cu"]
 
 

@@ -391,6 +391,42 @@ grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double* spectrum, 
  * Errors: GRLB_EINVAL for ctas or iters < 1 or NULL pointers; GRLB_ECUDA on launch failure. */
 grlb_status grlb_ffma_probe(int32_t ctas, int32_t iters, float* sink, void* stream, double* warp_instructions);
 
+/* ---- bounds-checked build ------------------------------------------------------------------
+ * A debugging aid with no counterpart in the paper, standing in for a memory checker.
+ * libgrlb_checked.so is this library compiled with GRLB_CHECKED.  In it every load and store of
+ * every kernel first tests its byte range against a device-side registry of live regions: each
+ * device allocation the library makes (live from its allocation to its release, in the order of
+ * the allocating / releasing stream), the caller's device buffers lent to one call (the init,
+ * halo, finiteness, allocation-free and probe calls: live while that call's kernels run) and a
+ * source field set with grlb_set_source_device (live until replaced, cleared or the domain is
+ * destroyed).  An access outside every live region is counted and not made (a load reads zero,
+ * a store goes to a sink).  The test is a call per access, which can change which multiplies and
+ * adds the compiler fuses, so results agree with the plain library's to rounding.  It costs a
+ * scan of the registry per access: use small domains.
+ *  grlb_checked_build  1 in the checked build, 0 in the plain one.
+ *  grlb_check_read     synchronises the device and fills *out (violations: accesses outside
+ *                      every live region; first_addr: the address of the first one, 0 if none;
+ *                      live_regions: regions registered and not yet released -- 0 once every
+ *                      domain, batch and staged buffer is gone; unmatched: releases of a region
+ *                      that was not live; overflow: registrations that found the registry
+ *                      (4096 regions) full).  reset != 0 zeroes every count but live_regions.
+ *  grlb_check_probe    makes [base, base + bytes) live on `stream`, tests the range
+ *                      [base + offset, base + offset + access_bytes) as a kernel access would
+ *                      (counting a violation when it is outside every live region), then
+ *                      releases the region.  Nothing at either address is read or written:
+ *                      base may be any value.  For testing the checker itself.
+ * In the plain build grlb_check_read and grlb_check_probe return GRLB_ESTATE. */
+typedef struct {
+    int64_t violations;
+    uint64_t first_addr;
+    int64_t live_regions;
+    int64_t unmatched;
+    int64_t overflow;
+} grlb_check_counts;
+int32_t grlb_checked_build(void);
+grlb_status grlb_check_read(grlb_check_counts* out, int32_t reset);
+grlb_status grlb_check_probe(const void* base, uint64_t bytes, int64_t offset, uint64_t access_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

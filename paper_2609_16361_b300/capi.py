@@ -53,6 +53,14 @@ class grlb_diag(C.Structure):
                     step=self.step, s=self.s, ncells=self.ncells)
 
 
+class grlb_check_counts(C.Structure):
+    _fields_ = [("violations", C.c_int64), ("first_addr", C.c_uint64), ("live_regions", C.c_int64),
+                ("unmatched", C.c_int64), ("overflow", C.c_int64)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 class grlb_batch_config(C.Structure):
     _fields_ = [("block_x", C.c_int32), ("solo_min_cells", C.c_int32), ("use_graph", C.c_int32),
                 ("schedule", C.c_int32), ("max_lanes", C.c_int32)]
@@ -71,6 +79,8 @@ def lib():
         from . import build as _build
         if LIB_PATH == _build.LIB and _build.needs_build():
             _build.build()
+        elif LIB_PATH == _build.LIB_CHECKED and _build.needs_build(checked=True):
+            _build.build(checked=True)
         if not os.path.exists(LIB_PATH):
             raise GrlbError(-3, f"CUDA library missing: {LIB_PATH}")
         L = C.CDLL(LIB_PATH)
@@ -112,6 +122,9 @@ def lib():
             "grlb_halo_exchange_z": ([vp, vp], i32),
             "grlb_halo_pack_z": ([vp, vp, vp], i32),
             "grlb_halo_unpack_z": ([vp, vp, vp], i32),
+            "grlb_checked_build": ([], C.c_int32),
+            "grlb_check_read": ([C.POINTER(grlb_check_counts), C.c_int32], i32),
+            "grlb_check_probe": ([vp, C.c_uint64, C.c_int64, C.c_uint64, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -132,7 +145,8 @@ def exported_symbols():
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
             "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe",
-            "grlb_set_init_mode", "grlb_halo_exchange_z", "grlb_halo_pack_z", "grlb_halo_unpack_z"]
+            "grlb_set_init_mode", "grlb_halo_exchange_z", "grlb_halo_pack_z", "grlb_halo_unpack_z",
+            "grlb_checked_build", "grlb_check_read", "grlb_check_probe"]
 
 
 def check(status):
@@ -407,3 +421,21 @@ class Domain:
     @property
     def steps(self):
         return grlb_steps_done(self.h)
+
+
+# ---- bounds-checked build (libgrlb_checked.so, selected with GRLB_LIB) -----------------------
+def grlb_checked_build() -> bool:
+    return bool(lib().grlb_checked_build())
+
+
+def grlb_check_read(reset=False) -> dict:
+    """Counts of the checked build's access tests (synchronises the device)."""
+    c = grlb_check_counts()
+    check(lib().grlb_check_read(C.byref(c), 1 if reset else 0))
+    return c.as_dict()
+
+
+def grlb_check_probe(base, nbytes, offset, access_bytes, stream=None):
+    """Test [base + offset, + access_bytes) against a region [base, base + nbytes) made live for
+    the probe alone; nothing at either address is accessed."""
+    check(lib().grlb_check_probe(base, nbytes, offset, access_bytes, stream))

@@ -273,10 +273,10 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     cudaStream_t s = d->stream;
     cudaError_t e = cudaSuccess;
     d->D.buf[0] = d->D.buf[1] = nullptr;
-    e = cudaMallocAsync(&d->D.buf[0], pb, s);
+    e = grlb::dev_alloc(&d->D.buf[0], pb, s);
     if (e == cudaSuccess) {
         if (p->streaming) d->D.buf[1] = d->D.buf[0];  // one buffer, updated in place
-        else e = cudaMallocAsync(&d->D.buf[1], pb, s);
+        else e = grlb::dev_alloc(&d->D.buf[1], pb, s);
     }
     // the last brick's cells past N are never written by a kernel: zero them once so that
     // checkpoints of equal states are equal bytes
@@ -284,10 +284,10 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     for (int b = 0; b < (p->streaming ? 1 : 2) && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(static_cast<char*>(d->D.buf[b]) + pb - tail, 0, tail, s);
     if (e == cudaSuccess && p->streaming && p->bc == GRLB_BC_X_DIRICHLET_EQ)
-        e = cudaMallocAsync(&d->D.outflow, outflow_bytes(*p), s);
+        e = grlb::dev_alloc(&d->D.outflow, outflow_bytes(*p), s);
     if (e == cudaSuccess)
-        e = cudaMallocAsync(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d->diag_dev, NDIAG * sizeof(double), s);
+        e = grlb::dev_alloc(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double), s);
+    if (e == cudaSuccess) e = grlb::dev_alloc(&d->diag_dev, NDIAG * sizeof(double), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         grlb_destroy(d);
@@ -304,13 +304,14 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
 void grlb_destroy(grlb_domain* d) {
     if (!d) return;
     cudaStream_t s = d->stream;
-    if (d->D.buf[0]) cudaFreeAsync(d->D.buf[0], s);
-    if (d->D.buf[1] && d->D.buf[1] != d->D.buf[0]) cudaFreeAsync(d->D.buf[1], s);
-    if (d->D.outflow) cudaFreeAsync(d->D.outflow, s);
-    if (d->partials) cudaFreeAsync(d->partials, s);
-    if (d->diag_dev) cudaFreeAsync(d->diag_dev, s);
+    if (d->D.src) grlb::chk_release(d->D.src, s);  // the caller's source field, lent since it was set
+    grlb::dev_free(d->D.buf[0], s);
+    if (d->D.buf[1] != d->D.buf[0]) grlb::dev_free(d->D.buf[1], s);
+    grlb::dev_free(d->D.outflow, s);
+    grlb::dev_free(d->partials, s);
+    grlb::dev_free(d->diag_dev, s);
     for (int i = 0; i < 2; ++i) {
-        if (d->stage[i]) cudaFreeAsync(d->stage[i], d->copy_stream);  // staged, never consumed
+        if (d->stage[i]) grlb::dev_free(d->stage[i], d->copy_stream);  // staged, never consumed
         if (d->staged[i]) cudaEventDestroy(d->staged[i]);
     }
     if (d->copy_stream) cudaStreamDestroy(d->copy_stream);
@@ -358,7 +359,7 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
     if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive: NULL argument");
     const size_t N = (size_t)d->D.plane;
     double* stage = nullptr;
-    GRLB_CU(cudaMallocAsync(&stage, 5 * N * sizeof(double), d->stream));
+    GRLB_CU(grlb::dev_alloc(&stage, 5 * N * sizeof(double), d->stream));
     cudaError_t e = cudaMemcpyAsync(stage, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(stage + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->stream);
@@ -366,7 +367,7 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
         d->D.cur = 0;
         e = launch_domain_init(d, stage, stage + N, stage + 4 * N);
     }
-    cudaError_t e2 = cudaFreeAsync(stage, d->stream);
+    cudaError_t e2 = grlb::dev_free(stage, d->stream);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(e, "grlb_init_primitive");
@@ -378,7 +379,13 @@ grlb_status grlb_init_primitive(grlb_domain* d, const double* rho, const double*
 grlb_status grlb_init_primitive_device(grlb_domain* d, const double* rho, const double* u, const double* p) {
     if (!d || !rho || !u || !p) return fail(GRLB_EINVAL, "grlb_init_primitive_device: NULL argument");
     d->D.cur = 0;
-    cudaError_t e = launch_domain_init(d, rho, u, p);
+    const size_t N = (size_t)d->D.plane;
+    cudaError_t e;
+    {
+        grlb::Lent lr(rho, N * sizeof(double), d->stream), lu(u, 3 * N * sizeof(double), d->stream),
+            lp(p, N * sizeof(double), d->stream);
+        e = launch_domain_init(d, rho, u, p);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "grlb_init_primitive_device");
     d->steps = 0;
     d->diag_step = -1;
@@ -408,14 +415,14 @@ grlb_status grlb_stage_primitive(grlb_domain* d, const double* rho, const double
     }
     retain_pool();
     const int slot = d->stage_head;
-    GRLB_CU(cudaMallocAsync(&d->stage[slot], 5 * N * sizeof(double), d->copy_stream));
+    GRLB_CU(grlb::dev_alloc(&d->stage[slot], 5 * N * sizeof(double), d->copy_stream));
     double* st = d->stage[slot];
     cudaError_t e = cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(st + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(st + 4 * N, p, N * sizeof(double), cudaMemcpyHostToDevice, d->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(d->staged[slot], d->copy_stream);
     if (e != cudaSuccess) {  // the slot stays empty; its buffer goes back to the pool
-        cudaFreeAsync(st, d->copy_stream);
+        grlb::dev_free(st, d->copy_stream);
         d->stage[slot] = nullptr;
         return cuda_fail(e, "grlb_stage_primitive");
     }
@@ -433,7 +440,7 @@ grlb_status grlb_init_from_stage(grlb_domain* d) {
     d->D.cur = 0;
     const double* st = d->stage[slot];
     GRLB_CU(launch_domain_init(d, st, st + N, st + 4 * N));
-    GRLB_CU(cudaFreeAsync(d->stage[slot], d->stream));  // released once the init has read it
+    GRLB_CU(grlb::dev_free(d->stage[slot], d->stream));  // released once the init has read it
     d->stage[slot] = nullptr;
     d->stage_count -= 1;
     d->steps = 0;
@@ -461,6 +468,8 @@ static grlb_status sweep_once(grlb_domain* d, bool diag) {
 grlb_status grlb_set_source_device(grlb_domain* d, const float* S) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     if (S && d->P.streaming) return fail(GRLB_EINVAL, "a source needs two-buffer streaming (streaming = 0)");
+    if (d->D.src) GRLB_CU(grlb::chk_release(d->D.src, d->stream));
+    if (S) GRLB_CU(grlb::chk_register(S, 5 * (size_t)d->D.plane * sizeof(float), d->stream));
     d->D.src = S;
     if (d->step_graph) {  // the captured sweeps carry the old source pointer
         cudaGraphExecDestroy(d->step_graph);
@@ -591,6 +600,7 @@ grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out) {
 grlb_status grlb_check_finite(grlb_domain* d, int32_t* flag) {
     if (!d || !flag) return fail(GRLB_EINVAL, "grlb_check_finite: NULL argument");
     const size_t bytes = pop_bytes((size_t)d->D.plane, d->P.storage);
+    grlb::Lent lf(flag, sizeof(int32_t), d->stream);
     GRLB_CU(grlb::launch_check_finite(d->D.buf[d->D.cur], (int64_t)bytes, d->P.storage, flag, d->stream));
     return GRLB_OK;
 }
@@ -599,12 +609,12 @@ grlb_status grlb_read_conserved(grlb_domain* d, double* out) {
     if (!d || !out) return fail(GRLB_EINVAL, "grlb_read_conserved: NULL argument");
     const size_t N = (size_t)d->D.plane;
     double* stage = nullptr;
-    GRLB_CU(cudaMallocAsync(&stage, 5 * N * sizeof(double), d->stream));
+    GRLB_CU(grlb::dev_alloc(&stage, 5 * N * sizeof(double), d->stream));
     const int gather = (d->P.streaming && (d->steps & 1)) ? 1 : 0;
     cudaError_t e = grlb::launch_conserved(d->D, d->P.storage, d->D.buf[d->D.cur], stage, d->s, d->rho_ref,
                                            d->E_ref, gather, d->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, stage, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, d->stream);
-    cudaError_t e2 = cudaFreeAsync(stage, d->stream);
+    cudaError_t e2 = grlb::dev_free(stage, d->stream);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(e, "grlb_read_conserved");
@@ -914,11 +924,11 @@ grlb_status rebuild_tiles(grlb_batch* b) {
         all.insert(all.end(), groups[g].begin(), groups[g].end());
     }
     b->group_off[kGroups] = (int)all.size();
-    if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
+    grlb::dev_free(b->d_tiles, b->stream);
     b->d_tiles = nullptr;
     b->ntiles = (int)all.size();
     if (b->ntiles > 0) {
-        GRLB_CU(cudaMallocAsync(&b->d_tiles, all.size() * sizeof(int4), b->stream));
+        GRLB_CU(grlb::dev_alloc(&b->d_tiles, all.size() * sizeof(int4), b->stream));
         GRLB_CU(cudaMemcpyAsync(b->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                 b->stream));
     }
@@ -1012,7 +1022,7 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
     b->h_recs.resize(b->nsmall);
     b->h_doms.resize(n);
     cudaError_t e = cudaSuccess;
-    if (b->slot0 < 0) e = cudaMallocAsync(&b->d_doms, n * sizeof(DomainDev), b->stream);
+    if (b->slot0 < 0) e = grlb::dev_alloc(&b->d_doms, n * sizeof(DomainDev), b->stream);
     // the batch stream must not run ahead of work already queued on the domains' streams
     if (e == cudaSuccess) e = order_after_domains(b);
     if (e != cudaSuccess) {
@@ -1040,8 +1050,8 @@ void grlb_batch_destroy(grlb_batch* b) {
         cudaEventDestroy(ev);
     }
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    if (b->d_doms) cudaFreeAsync(b->d_doms, b->stream);
-    if (b->d_tiles) cudaFreeAsync(b->d_tiles, b->stream);
+    grlb::dev_free(b->d_doms, b->stream);
+    grlb::dev_free(b->d_tiles, b->stream);
     // slots taken but never written (no step ran): their previous holders' release events have
     // not been waited for yet, so this batch's release must follow them too
     for (const auto& w : b->slot_waits) {
@@ -1270,6 +1280,9 @@ extern "C" grlb_status grlb_step_diag_noalloc(const grlb_params* p, const void* 
     st = noalloc_scratch(&scratch);
     if (st != GRLB_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t pb = pop_bytes((size_t)tmp.D.plane, p->storage);
+    grlb::Lent li(f_in, pb, s), lo(f_out, pb, s), ld(diag_out, NDIAG * sizeof(double), s),
+        lsc(scratch, sizeof(g_noalloc_partials), s);
     GRLB_CU(grlb::launch_sweep(tmp.D, p->storage, p->collision, 0, f_in, f_out, true, scratch, tmp.grid, tmp.block,
                                s));
     GRLB_CU(grlb::launch_diag_finalize(scratch, tmp.nblocks, diag_out, s));
@@ -1352,6 +1365,16 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     float2* tw = reinterpret_cast<float2*>(base + oTw);
     double* part = reinterpret_cast<double*>(base + oPart);
     unsigned long long* bins = reinterpret_cast<unsigned long long*>(base + oBins);
+    // the checked build registers each part of the scratch on its own, without the padding
+    const void* parts[5] = {U, mu, tw, part, bins};
+    const size_t part_bytes[5] = {4 * (size_t)N * sizeof(float2), (size_t)N * sizeof(float),
+                                  (size_t)n * sizeof(float2), (size_t)np * sizeof(double),
+                                  (size_t)std::max(nb, 1) * sizeof(unsigned long long)};
+    for (int i = 0; i < 5; ++i) grlb::chk_register(parts[i], part_bytes[i], st);
+    auto release_scratch = [&]() {
+        for (int i = 0; i < 5; ++i) grlb::chk_release(parts[i], st);
+        return cudaFreeAsync(base, st);
+    };
 
     std::vector<float2> htw(n);
     for (int j = 0; j < n; ++j) {
@@ -1385,7 +1408,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
             e = cudaMemcpyAsync(hpart.data(), part, 2 * plan.grid5 * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && nb > 0)
             e = cudaMemcpyAsync(hbins.data(), bins, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-        cudaError_t e2 = cudaFreeAsync(base, st);
+        cudaError_t e2 = release_scratch();
         if (e == cudaSuccess) e = e2;
         base = nullptr;
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1402,7 +1425,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
             for (int b = 0; b < nbins; ++b) spectrum[b] = b < nb ? (double)hbins[b] / fx_scale : 0.0;
         }
     }
-    if (base) cudaFreeAsync(base, st);
+    if (base) release_scratch();
     if (e != cudaSuccess) return cuda_fail(e, "grlb_spectral_diag");
     return GRLB_OK;
 }
@@ -1437,6 +1460,8 @@ extern "C" grlb_status grlb_halo_pack_z(grlb_domain* d, void* to_upper, void* to
     grlb_status st = check_slab(d, "grlb_halo_pack_z");
     if (st != GRLB_OK) return st;
     const grlb_params& a = d->P;
+    const size_t slice = 5 * (size_t)a.nx * a.ny * elem_bytes(a.storage);
+    grlb::Lent lu(to_upper, slice, d->stream), ll(to_lower, slice, d->stream);
     GRLB_CU(grlb::launch_halo_pack_z(d->D.buf[d->D.cur], to_upper, to_lower, a.nz, (int64_t)a.nx * a.ny,
                                      elem_bytes(a.storage), d->stream));
     return GRLB_OK;
@@ -1447,6 +1472,8 @@ extern "C" grlb_status grlb_halo_unpack_z(grlb_domain* d, const void* from_lower
     grlb_status st = check_slab(d, "grlb_halo_unpack_z");
     if (st != GRLB_OK) return st;
     const grlb_params& a = d->P;
+    const size_t slice = 5 * (size_t)a.nx * a.ny * elem_bytes(a.storage);
+    grlb::Lent ll(from_lower, slice, d->stream), lu(from_upper, slice, d->stream);
     GRLB_CU(grlb::launch_halo_unpack_z(d->D.buf[d->D.cur], from_lower, from_upper, a.nz, (int64_t)a.nx * a.ny,
                                        elem_bytes(a.storage), d->stream));
     return GRLB_OK;
@@ -1463,7 +1490,45 @@ extern "C" grlb_status grlb_ffma_probe(int32_t ctas, int32_t iters, float* sink,
                                        double* warp_instructions) {
     if (ctas < 1 || iters < 1 || !sink || !warp_instructions)
         return fail(GRLB_EINVAL, "grlb_ffma_probe: ctas and iters must be >= 1, pointers non-NULL");
+    grlb::Lent ls(sink, (size_t)ctas * 256 * sizeof(float), static_cast<cudaStream_t>(stream));
     GRLB_CU(grlb::launch_ffma_probe(sink, ctas, iters, static_cast<cudaStream_t>(stream)));
     *warp_instructions = (double)ctas * 8.0 * (double)iters * 128.0;
     return GRLB_OK;
+}
+
+// ---- bounds-checked build ---------------------------------------------------------------------
+extern "C" int32_t grlb_checked_build(void) { return grlb::kChecked ? 1 : 0; }
+
+extern "C" grlb_status grlb_check_read(grlb_check_counts* out, int32_t reset) {
+    if (!out) return fail(GRLB_EINVAL, "grlb_check_read: out is NULL");
+#ifdef GRLB_CHECKED
+    grlb::ChkCounts c{};
+    GRLB_CU(grlb::chk_read(&c, reset != 0));
+    out->violations = (int64_t)c.violations;
+    out->first_addr = c.first;
+    out->live_regions = c.live;
+    out->unmatched = (int64_t)c.unmatched;
+    out->overflow = (int64_t)c.overflow;
+    return GRLB_OK;
+#else
+    (void)reset;
+    return fail(GRLB_ESTATE, "grlb_check_read: not a bounds-checked build (GRLB_CHECKED)");
+#endif
+}
+
+extern "C" grlb_status grlb_check_probe(const void* base, uint64_t bytes, int64_t offset, uint64_t access_bytes,
+                                        void* stream) {
+#ifdef GRLB_CHECKED
+    if (bytes == 0 || access_bytes == 0 || access_bytes > 0xffffffffull)
+        return fail(GRLB_EINVAL, "grlb_check_probe: bytes and access_bytes must be positive (access < 4 GB)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char* at = static_cast<const char*>(base) + offset;
+    GRLB_CU(grlb::chk_register(base, bytes, s));
+    GRLB_CU(grlb::chk_probe(at, access_bytes, s));
+    GRLB_CU(grlb::chk_release(base, s));
+    return GRLB_OK;
+#else
+    (void)base; (void)bytes; (void)offset; (void)access_bytes; (void)stream;
+    return fail(GRLB_ESTATE, "grlb_check_probe: not a bounds-checked build (GRLB_CHECKED)");
+#endif
 }

@@ -19,6 +19,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "grlb_check.cuh"
+
 namespace grlb {
 
 constexpr int NF = 5;
@@ -100,29 +102,29 @@ template <> struct Store<S_F32> {
     // consecutive lines of every plane (measured 0.4% faster than a plain read-only load)
     static __device__ __forceinline__ float ld(const float* p) {
         float v;
-        asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(GRLB_CHK_SRC(p)));
         return v;
     }
-    static __device__ __forceinline__ float ld_plain(const float* p) { return *p; }
+    static __device__ __forceinline__ float ld_plain(const float* p) { return GRLB_LD(p); }
     // default write-back store (measured 0.8% faster than the evict-first .cs hint)
-    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ void st(float* p, float v) { GRLB_ST(p, v); }
 };
 template <> struct Store<S_F16> {
     static constexpr bool scaled = true;
     using T = __half;
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ float ld_plain(const __half* p) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(GRLB_LDG(p)); }
+    static __device__ __forceinline__ float ld_plain(const __half* p) { return __half2float(GRLB_LD(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { GRLB_ST(p, __float2half_rn(v)); }
 };
 template <> struct Store<S_BF16> {
     static constexpr bool scaled = false;
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
-        return __bfloat162float(__ldg(p));
+        return __bfloat162float(GRLB_LDG(p));
     }
-    static __device__ __forceinline__ float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(GRLB_LD(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
-        *p = __float2bfloat16_rn(v);
+        GRLB_ST(p, __float2bfloat16_rn(v));
     }
 };
 
@@ -151,7 +153,7 @@ __device__ __forceinline__ void add_source(const DomainDev& D, int32_t c, float 
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
-        float sk = __ldg(D.src + (int64_t)k * D.plane + c) * D.src_scale[r];
+        float sk = GRLB_LDG(D.src + (int64_t)k * D.plane + c) * D.src_scale[r];
         if (Store<S>::scaled) sk *= D.enc[k];
         o[k][0] += 0.25f * sk;
 #pragma unroll

@@ -25,10 +25,10 @@ __global__ void __launch_bounds__(256) halo_z_kernel(T* __restrict__ lower, T* _
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
         if (s < 5) {
             const int64_t q = (7 * s + 5) * kBrick;
-            upper[brick_at(c) + q] = lower[brick_at((int64_t)(nzl - 2) * nxy + c) + q];
+            GRLB_ST(upper + brick_at(c) + q, GRLB_LD(lower + brick_at((int64_t)(nzl - 2) * nxy + c) + q));
         } else {
             const int64_t q = (7 * (s - 5) + 6) * kBrick;
-            lower[brick_at((int64_t)(nzl - 1) * nxy + c) + q] = upper[brick_at(nxy + c) + q];
+            GRLB_ST(lower + brick_at((int64_t)(nzl - 1) * nxy + c) + q, GRLB_LD(upper + brick_at(nxy + c) + q));
         }
     }
 }
@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(256) halo_pack_kernel(const T* __restrict__ f,
                                                         T* __restrict__ to_lower, int nz, int64_t nxy) {
     const int s = blockIdx.y;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
-        if (s < 5) to_upper[s * nxy + c] = f[brick_at((int64_t)(nz - 2) * nxy + c) + (7 * s + 5) * kBrick];
-        else to_lower[(s - 5) * nxy + c] = f[brick_at(nxy + c) + (7 * (s - 5) + 6) * kBrick];
+        if (s < 5) GRLB_ST(to_upper + s * nxy + c, GRLB_LD(f + brick_at((int64_t)(nz - 2) * nxy + c) + (7 * s + 5) * kBrick));
+        else GRLB_ST(to_lower + (s - 5) * nxy + c, GRLB_LD(f + brick_at(nxy + c) + (7 * (s - 5) + 6) * kBrick));
     }
 }
 
@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256) halo_unpack_kernel(T* __restrict__ f, con
                                                           const T* __restrict__ from_upper, int nz, int64_t nxy) {
     const int s = blockIdx.y;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
-        if (s < 5) f[brick_at(c) + (7 * s + 5) * kBrick] = from_lower[s * nxy + c];
-        else f[brick_at((int64_t)(nz - 1) * nxy + c) + (7 * (s - 5) + 6) * kBrick] = from_upper[(s - 5) * nxy + c];
+        if (s < 5) GRLB_ST(f + brick_at(c) + (7 * s + 5) * kBrick, GRLB_LD(from_lower + s * nxy + c));
+        else GRLB_ST(f + brick_at((int64_t)(nz - 1) * nxy + c) + (7 * (s - 5) + 6) * kBrick, GRLB_LD(from_upper + (s - 5) * nxy + c));
     }
 }
 

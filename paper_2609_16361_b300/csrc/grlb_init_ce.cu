@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
     const int nx = D.nx, ny = D.ny, nz = D.nz;
     const float g1 = (float)C.gm1;
     const float Hp_ref = (float)(p_ref / C.gm1 + p_ref);
-    auto load = [&](int64_t i) { return lattice_prim(rho[i], u[i], u[N + i], u[2 * N + i], p[i], C.s); };
+    auto load = [&](int64_t i) {
+        return lattice_prim(GRLB_LD(rho + i), GRLB_LD(u + i), GRLB_LD(u + N + i), GRLB_LD(u + 2 * N + i), GRLB_LD(p + i), C.s);
+    };
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx);
         const int64_t r = c / nx;
@@ -124,11 +126,12 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
         }
 
         // equilibrium part: the plain initialisation's deviation arithmetic
-        const double rr = rho[c];
+        const double rr = GRLB_LD(rho + c);
         const float drho = (float)(rr - rho_ref);
-        const float dp = (float)(p[c] * C.s * C.s - p_ref);
+        const float dp = (float)(GRLB_LD(p + c) * C.s * C.s - p_ref);
         const float rf = (float)rr;
-        const float uv[3] = {(float)(u[c] * C.s), (float)(u[N + c] * C.s), (float)(u[2 * N + c] * C.s)};
+        const float uv[3] = {(float)(GRLB_LD(u + c) * C.s), (float)(GRLB_LD(u + N + c) * C.s),
+                             (float)(GRLB_LD(u + 2 * N + c) * C.s)};
         const float m[3] = {rf * uv[0], rf * uv[1], rf * uv[2]};
         const float ke = 0.5f * (m[0] * uv[0] + m[1] * uv[1] + m[2] * uv[2]);
         const float dEd = dp / g1 + ke;

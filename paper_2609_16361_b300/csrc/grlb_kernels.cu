@@ -203,7 +203,7 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
             const double x = sh[w][tid];
             acc = (tid == 8 || tid == 9) ? fmin(acc, x) : acc + x;
         }
-        out[tid] = acc;
+        GRLB_ST(out + tid, acc);
     }
 }
 
@@ -287,13 +287,13 @@ __global__ void __launch_bounds__(128) batch_sweep_kernel(const DomainDev* __res
     __shared__ DomainDev sD;
     int loaded = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[t];
+        const int4 tl = GRLB_LD(tiles + t);
         if (tl.x != loaded) {  // uniform across the CTA
             __syncthreads();
             const int nwords = sizeof(DomainDev) / 4;
             const uint32_t* src = reinterpret_cast<const uint32_t*>(doms + tl.x);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sD);
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = src[w];
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = GRLB_LD(src + w);
             __syncthreads();
             loaded = tl.x;
         }
@@ -420,7 +420,7 @@ __device__ __forceinline__ void reduce_records(const double* __restrict__ rec, i
     for (int64_t b = begin + threadIdx.x; b < end; b += 256) {
 #pragma unroll
         for (int f = 0; f < NDIAG; ++f) {
-            const double x = rec[b * NDIAG + f];
+            const double x = GRLB_LD(rec + (b * NDIAG + f));
             acc[f] = (f == 8 || f == 9) ? fmin(acc[f], x) : acc[f] + x;
         }
     }
@@ -437,7 +437,7 @@ __device__ __forceinline__ void reduce_records(const double* __restrict__ rec, i
         }
         __syncthreads();
     }
-    if (threadIdx.x < NDIAG) out[threadIdx.x] = sh[threadIdx.x][0];
+    if (threadIdx.x < NDIAG) GRLB_ST(out + threadIdx.x, sh[threadIdx.x][0]);
 }
 
 __global__ void __launch_bounds__(256) diag_stage1_kernel(const double* __restrict__ partials, int64_t nblocks,
@@ -468,11 +468,12 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
          c += (int64_t)gridDim.x * blockDim.x) {
         // the two differences against the reference state are taken in FP64, the rest in FP32
-        const double r = rho[c];
+        const double r = GRLB_LD(rho + c);
         const float drho = (float)(r - rho_ref);
-        const float dp = (float)(p[c] * s * s - p_ref);
+        const float dp = (float)(GRLB_LD(p + c) * s * s - p_ref);
         const float rf = (float)r;
-        const float uv[3] = {(float)(u[c] * s), (float)(u[N + c] * s), (float)(u[2 * N + c] * s)};
+        const float uv[3] = {(float)(GRLB_LD(u + c) * s), (float)(GRLB_LD(u + N + c) * s),
+                             (float)(GRLB_LD(u + 2 * N + c) * s)};
         const float m[3] = {rf * uv[0], rf * uv[1], rf * uv[2]};
         const float ke = 0.5f * (m[0] * uv[0] + m[1] * uv[1] + m[2] * uv[2]);
         const float dE = dp / g1 + ke;
@@ -540,7 +541,7 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
             if (k == 4) q += E_ref;
             if (k >= 1 && k <= 3) q /= s;
             if (k == 4) q /= s * s;
-            out[(int64_t)k * N + c] = q;
+            GRLB_ST(out + (int64_t)k * N + c, q);
         }
     }
 }
@@ -676,13 +677,13 @@ __global__ void __launch_bounds__(256) check_finite_kernel(const uint4* __restri
                                                            int32_t* __restrict__ flag) {
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint4 v = __ldg(buf + i);
+        const uint4 v = GRLB_LDG(buf + i);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             bad = bad || ((w[j] & mask_lo) == mask_lo) || ((w[j] & mask_hi) == mask_hi);
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) GRLB_ST(flag, 1);
 }
 
 cudaError_t launch_check_finite(const void* buf, int64_t bytes, int storage, int32_t* flag, cudaStream_t st) {

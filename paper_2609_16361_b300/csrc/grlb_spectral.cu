@@ -148,7 +148,7 @@ __device__ __forceinline__ void stockham_pass(float2* line, int q, const float2*
             const int step = k << (LG - LGNS - RB);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * step];
+                float2 w = GRLB_LD(tw + r * step);
                 if (INV) w.y = -w.y;
                 v[it * R + r] = cmul(v[it * R + r], w);
             }
@@ -183,7 +183,7 @@ __device__ __forceinline__ int opaque(int v) {
 }
 __device__ __forceinline__ float2 tw_load(const float2* p) {
     float2 v;
-    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(GRLB_CHK_SRC(p)));
     return v;
 }
 
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(192, 3) spectral_k1_kernel(const DomainDev D, 
             const int64_t c = c0 + w;
             float u0, u1, u2, mu;
             prep_cell<S>(D, fin, gather, P, c, u0, u1, u2, mu);
-            mu_out[c] = mu;
+            GRLB_ST(mu_out + c, mu);
             ke += (double)(0.5f * (u0 * u0 + u1 * u1 + u2 * u2));
             const int l = w >> LG, j = w & (n - 1);
             sm[sm_index(l, j, LS)] = make_float2(u0, 0.0f);
@@ -328,12 +328,12 @@ __global__ void __launch_bounds__(192, 3) spectral_k1_kernel(const DomainDev D, 
         for (int w = threadIdx.x; w < L * n; w += blockDim.x) {
             const int l = w >> LG, j = w & (n - 1);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) U[k * N + c0 + w] = sm[sm_index(k * L + l, j, LS)];
+            for (int k = 0; k < 3; ++k) GRLB_ST(U + k * N + c0 + w, sm[sm_index(k * L + l, j, LS)]);
         }
         __syncthreads();
     }
     const double tot = block_sum(ke, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+    if (threadIdx.x == 0) GRLB_ST(partials + blockIdx.x, tot);
 }
 
 // ---- K1 for n <= 256: prep + four-step forward along x ----------------------------------------
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(128) spectral_k1_row_kernel(const DomainDev D,
             const int64_t c = row + q + n2 * r;
             float u0, u1, u2, mu;
             prep_cell<S>(D, fin, gather, P, c, u0, u1, u2, mu);
-            mu_out[c] = mu;
+            GRLB_ST(mu_out + c, mu);
             fke += 0.5f * (u0 * u0 + u1 * u1 + u2 * u2);
             ur[0][r] = u0;
             ur[1][r] = u1;
@@ -400,12 +400,12 @@ __global__ void __launch_bounds__(128) spectral_k1_row_kernel(const DomainDev D,
 #pragma unroll
             for (int si = 0; si < SP; ++si)
 #pragma unroll
-                for (int t = 0; t < n2; ++t) U[k * N + row + (q * SP + si) + 16 * t] = w[si * n2 + t];
+                for (int t = 0; t < n2; ++t) GRLB_ST(U + k * N + row + (q * SP + si) + 16 * t, w[si * n2 + t]);
             __syncthreads();
         }
     }
     const double tot = block_sum(ke, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+    if (threadIdx.x == 0) GRLB_ST(partials + blockIdx.x, tot);
 }
 
 // ---- K2 / K4: FFT of several planes along y (cubes) -------------------------------------------
@@ -429,13 +429,13 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_fft_y_kernel(fl
     const int64_t inc = (int64_t)jstep * nx;
     float2 tmp[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) tmp[e] = src[e * inc];
+    for (int e = 0; e < 16; ++e) tmp[e] = GRLB_LD(src + e * inc);
 #pragma unroll
     for (int e = 0; e < 16; ++e) sm[sm_index(l, j0 + e * jstep, LS)] = tmp[e];
     __syncthreads();
     cta_fft<LG, INV>(sm, tw);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) src[e * inc] = sm[sm_index(l, j0 + e * jstep, LS)];
+    for (int e = 0; e < 16; ++e) GRLB_ST(src + e * inc, sm[sm_index(l, j0 + e * jstep, LS)]);
 }
 
 // ---- K2 / K4 for cubes of n <= 256: four-step transforms along y -------------------------------
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(128) spectral_fft_y4_kernel(float2* __restrict
     if (!INV) {
         float2 v[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = line[(int64_t)(q + n2 * r) * nx];
+        for (int r = 0; r < 16; ++r) v[r] = GRLB_LD(line + (int64_t)(q + n2 * r) * nx);
         dft_reg<16, false>(v);
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
@@ -483,13 +483,13 @@ __global__ void __launch_bounds__(128) spectral_fft_y4_kernel(float2* __restrict
 #pragma unroll
         for (int si = 0; si < SP; ++si)
 #pragma unroll
-            for (int t = 0; t < n2; ++t) line[(int64_t)(q * SP + si + 16 * t) * nx] = w[si * n2 + t];
+            for (int t = 0; t < n2; ++t) GRLB_ST(line + (int64_t)(q * SP + si + 16 * t) * nx, w[si * n2 + t]);
     } else {
         float2 w[16];
 #pragma unroll
         for (int si = 0; si < SP; ++si)
 #pragma unroll
-            for (int t = 0; t < n2; ++t) w[si * n2 + t] = line[(int64_t)(q * SP + si + 16 * t) * nx];
+            for (int t = 0; t < n2; ++t) w[si * n2 + t] = GRLB_LD(line + (int64_t)(q * SP + si + 16 * t) * nx);
         if constexpr (n2 > 1) {
 #pragma unroll
             for (int si = 0; si < SP; ++si) dft_reg<n2, true>(w + si * n2);
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(128) spectral_fft_y4_kernel(float2* __restrict
         for (int s = 0; s < 16; ++s) x[s] = sm[q * RI + s * L + l];
         dft_reg<16, true>(x);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) line[(int64_t)(q + n2 * r) * nx] = x[r];
+        for (int r = 0; r < 16; ++r) GRLB_ST(line + (int64_t)(q + n2 * r) * nx, x[r]);
     }
 }
 
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k3_kernel(float
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) tmp[k * 4 + e] = col[k * N + e * inc];
+            for (int e = 0; e < 4; ++e) tmp[k * 4 + e] = GRLB_LD(col + k * N + e * inc);
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -611,12 +611,12 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k3_kernel(float
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) col[k * N + e * inc] = sm[sm_index(k * L + l_ld, j0 + e * jstep, LS)];
+            for (int e = 0; e < 4; ++e) GRLB_ST(col + k * N + e * inc, sm[sm_index(k * L + l_ld, j0 + e * jstep, LS)]);
         __syncthreads();
     }
     __syncthreads();
     for (int b = threadIdx.x; b < P.nbins; b += blockDim.x)
-        if (sbins[b]) atomicAdd(&bins[b], sbins[b]);
+        if (sbins[b]) GRLB_ATOMIC_ADD(bins + b, sbins[b]);
 }
 
 // ---- K3 for cubes of n <= 256: four-step transforms along z ------------------------------------
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
             const int qk = opaque(q);
             float2 v[16];
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = col[k * N + (int64_t)(qk + n2 * r) * S3];
+            for (int r = 0; r < 16; ++r) v[r] = GRLB_LD(col + k * N + (int64_t)(qk + n2 * r) * S3);
             dft_reg<16, false>(v);
 #pragma unroll
             for (int s = 1; s < 16; ++s)
@@ -755,13 +755,13 @@ __global__ void __launch_bounds__(128) spectral_k3_cube_kernel(float2* __restric
             for (int s = 0; s < 16; ++s) x[s] = sm[qo * RI + s * L + l];
             dft_reg<16, true>(x);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) col[o * N + (int64_t)(qo + n2 * r) * S3] = x[r];
+            for (int r = 0; r < 16; ++r) GRLB_ST(col + o * N + (int64_t)(qo + n2 * r) * S3, x[r]);
             __syncthreads();
         }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < P.nbins; b += blockDim.x)
-        if (sbins[b]) atomicAdd(&bins[b], sbins[b]);
+        if (sbins[b]) GRLB_ATOMIC_ADD(bins + b, sbins[b]);
 }
 
 // ---- K5: inverse x + dissipation -------------------------------------------------------------
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k5_kernel(const
 #pragma unroll
         for (int e = 0; e < 4; ++e)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) tmp[4 * e + k] = U[k * N + c0 + threadIdx.x + e * 256];
+            for (int k = 0; k < 4; ++k) tmp[4 * e + k] = GRLB_LD(U + k * N + c0 + threadIdx.x + e * 256);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int w = threadIdx.x + e * 256;
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k5_kernel(const
             const int l = w >> LG, j = w & (n - 1);
             const float wx = sm[sm_index(l, j, LS)].x, wy = sm[sm_index(L + l, j, LS)].x;
             const float wz = sm[sm_index(2 * L + l, j, LS)].x, th = sm[sm_index(3 * L + l, j, LS)].x;
-            const float m = mu[c0 + w];
+            const float m = GRLB_LD(mu + c0 + w);
             es += (double)(m * (wx * wx + wy * wy + wz * wz));
             ed += (double)((4.0f / 3.0f) * m * th * th);
         }
@@ -810,8 +810,8 @@ __global__ void __launch_bounds__(256, LG >= 9 ? 2 : 3) spectral_k5_kernel(const
     const double s1 = block_sum(es, red);
     const double s2 = block_sum(ed, red);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = s1;
-        partials[2 * blockIdx.x + 1] = s2;
+        GRLB_ST(partials + 2 * blockIdx.x, s1);
+        GRLB_ST(partials + 2 * blockIdx.x + 1, s2);
     }
 }
 
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(128) spectral_k5_row_kernel(const float2* __re
 #pragma unroll
             for (int si = 0; si < SP; ++si)
 #pragma unroll
-                for (int t = 0; t < n2; ++t) w[si * n2 + t] = U[o * N + row + (q * SP + si) + 16 * t];
+                for (int t = 0; t < n2; ++t) w[si * n2 + t] = GRLB_LD(U + o * N + row + (q * SP + si) + 16 * t);
             if constexpr (n2 > 1) {
 #pragma unroll
                 for (int si = 0; si < SP; ++si) dft_reg<n2, true>(w + si * n2);
@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(128) spectral_k5_row_kernel(const float2* __re
         float fs = 0.0f, fd = 0.0f;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-            const float m = mu[row + q + n2 * e];
+            const float m = GRLB_LD(mu + row + q + n2 * e);
             fs += m * wsq[e];
             fd += (4.0f / 3.0f) * m * th[e] * th[e];
         }
@@ -892,8 +892,8 @@ __global__ void __launch_bounds__(128) spectral_k5_row_kernel(const float2* __re
     const double s1 = block_sum(es, red);
     const double s2 = block_sum(ed, red);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = s1;
-        partials[2 * blockIdx.x + 1] = s2;
+        GRLB_ST(partials + 2 * blockIdx.x, s1);
+        GRLB_ST(partials + 2 * blockIdx.x + 1, s2);
     }
 }
 
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(256) ffma_probe_kernel(float* __restrict__ sin
         }
     }
     const float s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
-    if (s == 0.0f) sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (s == 0.0f) GRLB_ST(sink + (int64_t)blockIdx.x * blockDim.x + threadIdx.x, s);
 }
 
 // ---- launchers ----------------------------------------------------------------------------

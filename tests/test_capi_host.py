@@ -34,6 +34,24 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert b"sm_103a" in capi.lib().grlb_version()
 
 
+def test_checked_build_loads_and_exports_the_same_symbols():
+    """libgrlb_checked.so (GRLB_CHECKED, relocatable device code) builds, loads beside the plain
+    library and exports every declared entry point; only it reports itself as checked, and the
+    plain library refuses the checker's calls with GRLB_ESTATE."""
+    from paper_2609_16361_b300 import build
+    path = build.build(checked=True)
+    Lc = C.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(Lc, n), f"{n} missing from libgrlb_checked.so"
+    Lc.grlb_checked_build.restype = C.c_int32
+    assert Lc.grlb_checked_build() == 1
+    assert capi.lib().grlb_checked_build() == 0
+    c = capi.grlb_check_counts()
+    assert capi.lib().grlb_check_read(C.byref(c), 0) == -6
+    assert b"not a bounds-checked build" in capi.lib().grlb_last_error()
+    assert capi.lib().grlb_check_probe(None, 16, 0, 4, None) == -6
+
+
 def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "lay.c"
     src.write_text(r'''
@@ -41,9 +59,9 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "grlb.h"
 int main(void){
- printf("%zu %zu %zu %zu %zu %zu\n", sizeof(grlb_params), offsetof(grlb_params, T_S),
+ printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(grlb_params), offsetof(grlb_params, T_S),
         offsetof(grlb_params, right_prim), sizeof(grlb_diag), offsetof(grlb_diag, n_floor),
-        sizeof(grlb_batch_config));
+        sizeof(grlb_batch_config), sizeof(grlb_check_counts), offsetof(grlb_check_counts, overflow));
  return 0;}
 ''')
     exe = tmp_path / "lay"
@@ -51,7 +69,8 @@ int main(void){
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [C.sizeof(capi.grlb_params), capi.grlb_params.T_S.offset,
                     capi.grlb_params.right_prim.offset, C.sizeof(capi.grlb_diag),
-                    capi.grlb_diag.n_floor.offset, C.sizeof(capi.grlb_batch_config)]
+                    capi.grlb_diag.n_floor.offset, C.sizeof(capi.grlb_batch_config),
+                    C.sizeof(capi.grlb_check_counts), capi.grlb_check_counts.overflow.offset]
 
 
 def test_parameter_validation_without_device():
