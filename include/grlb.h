@@ -193,6 +193,20 @@ grlb_status grlb_read_conserved(grlb_domain* d, double* out);
 /* Primitive fields in physical units (no floors): rho[N], u[3*N], p[N], T[N]; any pointer
  * may be NULL to skip that field. */
 grlb_status grlb_read_primitive(grlb_domain* d, double* rho, double* u, double* p, double* T);
+/* Point probes: the 35 populations of listed cells without reading the whole state.  The state
+ * of a domain is the post-collision population set f*_{k,i}(x) of its cells (Alg. 1 step 9
+ * before streaming: what a two-buffer sweep writes at x), whatever the streaming pattern
+ * (grlb_params.streaming) keeps where.
+ *  cells  host array of n cell indices x + nx (y + ny z), each in [0, N); n >= 0 (0: no-op).
+ *  f_out  host array of 35 n doubles, row-major by population: f_out[q n + j] = f*_q of
+ *         cells[j], q = 7 k + i (field k = rho, m_x, m_y, m_z, E; link i = 0, +x, -x, +y, -y,
+ *         +z, -z), in lattice units with the reference equilibrium added back, so that
+ *         sum_i f_out[(7 k + i) n + j] is conserved field k of the cell in lattice units
+ *         (rho; m s; E s^2 with s = dt/dx).
+ * Synchronises the domain's stream.  Errors: GRLB_EINVAL for a NULL argument, n < 0 or a cell
+ * outside [0, N) (checked before anything is enqueued); GRLB_ENOMEM / GRLB_ECUDA from the
+ * staging allocation or the copies. */
+grlb_status grlb_read_cells(grlb_domain* d, const int64_t* cells, int64_t n, double* f_out);
 
 /* Raw checkpoint: stored populations + step counter.  grlb_save with buf == NULL sets
  * *bytes to the size needed; otherwise *bytes must be at least that size.  grlb_load

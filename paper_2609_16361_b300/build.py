@@ -20,7 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgrlb.so")
 LIB_CHECKED = os.path.join(HERE, "libgrlb_checked.so")
-SOURCES = ["grlb_kernels.cu", "grlb_spectral.cu", "grlb_init_ce.cu", "grlb_halo.cu", "grlb_check.cu", "grlb_api.cu"]
+SOURCES = ["grlb_kernels.cu", "grlb_spectral.cu", "grlb_init_ce.cu", "grlb_halo.cu", "grlb_cells.cu", "grlb_check.cu",
+           "grlb_api.cu"]
 HEADERS = ["grlb_device.cuh", "grlb_kernels.h", "grlb_check.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -104,6 +104,7 @@ def lib():
             "grlb_check_finite": ([vp, vp], i32),
             "grlb_read_conserved": ([vp, dp], i32),
             "grlb_read_primitive": ([vp, dp, dp, dp, dp], i32),
+            "grlb_read_cells": ([vp, C.POINTER(C.c_int64), i64, dp], i32),
             "grlb_save": ([vp, vp, C.POINTER(sz)], i32),
             "grlb_load": ([vp, vp, sz], i32),
             "grlb_steps_done": ([vp], i64),
@@ -140,7 +141,7 @@ def exported_symbols():
             "grlb_init_primitive_device", "grlb_stage_primitive", "grlb_init_from_stage",
             "grlb_set_source_device", "grlb_step",
             "grlb_step_diag", "grlb_diag_read", "grlb_check_finite", "grlb_read_conserved",
-            "grlb_read_primitive",
+            "grlb_read_primitive", "grlb_read_cells",
             "grlb_save", "grlb_load", "grlb_steps_done", "grlb_batch_create",
             "grlb_batch_destroy", "grlb_batch_set_stream", "grlb_batch_set_active",
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
@@ -266,6 +267,14 @@ def grlb_read_primitive(h, N):
     rho, u, p, T = np.empty(N), np.empty((3, N)), np.empty(N), np.empty(N)
     check(lib().grlb_read_primitive(h, _dp(rho), _dp(u), _dp(p), _dp(T)))
     return rho, u, p, T
+
+
+def grlb_read_cells(h, cells) -> np.ndarray:
+    """Populations f*_q (lattice units) of the listed cells: array (35, len(cells))."""
+    cells = np.ascontiguousarray(cells, np.int64).ravel()
+    out = np.empty((35, cells.size))
+    check(lib().grlb_read_cells(h, cells.ctypes.data_as(C.POINTER(C.c_int64)), cells.size, _dp(out)))
+    return out
 
 
 def grlb_save(h) -> np.ndarray:

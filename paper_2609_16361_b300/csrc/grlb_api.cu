@@ -621,6 +621,46 @@ grlb_status grlb_read_conserved(grlb_domain* d, double* out) {
     return GRLB_OK;
 }
 
+grlb_status grlb_read_cells(grlb_domain* d, const int64_t* cells, int64_t n, double* f_out) {
+    if (!d) return fail(GRLB_EINVAL, "domain is NULL");
+    if (n < 0) return fail(GRLB_EINVAL, "grlb_read_cells: n must be >= 0");
+    if (n == 0) return GRLB_OK;
+    if (!cells || !f_out) return fail(GRLB_EINVAL, "grlb_read_cells: NULL argument");
+    const int64_t N = d->D.plane;
+    for (int64_t j = 0; j < n; ++j)
+        if (cells[j] < 0 || cells[j] >= N)
+            return fail(GRLB_EINVAL, "grlb_read_cells: cell " + std::to_string(cells[j]) + " (entry " +
+                                         std::to_string(j) + ") outside [0, " + std::to_string(N) + ")");
+    // decoding: f = stored x dec[k] + w_i (Q_ref,k + c_i . J_ref,k / cs^2), J_ref,m_j = p_ref e_j
+    grlb::CellDecode dec;
+    const double Qref[5] = {d->rho_ref, 0.0, 0.0, 0.0, d->E_ref};
+    const int cx[7] = {0, 1, -1, 0, 0, 0, 0}, cy[7] = {0, 0, 0, 1, -1, 0, 0}, cz[7] = {0, 0, 0, 0, 0, 1, -1};
+    for (int k = 0; k < 5; ++k) {
+        dec.dec[k] = (double)d->D.dec[k];
+        for (int i = 0; i < 7; ++i) {
+            const double w = i == 0 ? 0.25 : 0.125;
+            const int c = k == 1 ? cx[i] : k == 2 ? cy[i] : k == 3 ? cz[i] : 0;
+            dec.shift[7 * k + i] = w * (Qref[k] + 4.0 * c * d->p_ref);
+        }
+    }
+    const int layout = !d->P.streaming ? 0 : (d->steps & 1) ? 2 : 1;
+    cudaStream_t s = d->stream;
+    char* stage = nullptr;
+    const size_t cb = (size_t)n * sizeof(int64_t), ob = (size_t)n * grlb::NP * sizeof(double);
+    GRLB_CU(grlb::dev_alloc(&stage, cb + ob, s));
+    int64_t* dcells = reinterpret_cast<int64_t*>(stage);
+    double* dout = reinterpret_cast<double*>(stage + cb);
+    cudaError_t e = cudaMemcpyAsync(dcells, cells, cb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = grlb::launch_read_cells(d->D, d->P.storage, d->D.buf[d->D.cur], dcells, n, layout, dec, dout, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f_out, dout, ob, cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = grlb::dev_free(stage, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "grlb_read_cells");
+    return GRLB_OK;
+}
+
 grlb_status grlb_read_primitive(grlb_domain* d, double* rho, double* u, double* p, double* T) {
     if (!d) return fail(GRLB_EINVAL, "domain is NULL");
     const size_t N = (size_t)d->D.plane;

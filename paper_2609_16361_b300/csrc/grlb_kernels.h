@@ -82,6 +82,16 @@ cudaError_t launch_halo_pack_z(const void* f, void* to_upper, void* to_lower, in
                                cudaStream_t st);
 cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
                                  size_t elem, cudaStream_t st);
+// Populations of listed cells (grlb_cells.cu): out[q n + j] = f_q(cells[j]) in FP64 lattice
+// units, f = stored x dec[k] + shift[q].  layout 0: slot q of the cell (two buffers); 1: slot
+// opp(i) of the cell (one buffer, even steps done); 2: slot q of the neighbour x + c_i or the
+// outflow record (one buffer, odd steps done).  cells[j] must lie in [0, N).
+struct CellDecode {
+    double dec[5];
+    double shift[35];
+};
+cudaError_t launch_read_cells(const DomainDev& D, int storage, const void* buf, const int64_t* cells, int64_t n,
+                              int layout, const CellDecode& dec, double* out, cudaStream_t st);
 // Writes *flag = 1 (device-accessible) if any stored value of the buffer (bytes, a multiple of
 // 16) is non-finite; never writes 0.
 cudaError_t launch_check_finite(const void* buf, int64_t bytes, int storage, int32_t* flag, cudaStream_t st);

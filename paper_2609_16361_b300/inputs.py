@@ -143,6 +143,33 @@ def tgv3d(n: int, mach: float = 1.25, re: float = 1600.0, pr: float = 0.71,
     return Case(prm, _flat(rho), np.stack([_flat(ux), _flat(uy), _flat(uz)]), _flat(p), meta)
 
 
+def tgv3d_device(n: int, device="cuda", **kw):
+    """tgv3d(n, **kw) with its fields built on the device, one z-plane at a time, as torch FP64
+    tensors (rho (N,), u (3, N), p (N,)): for domains whose n^3 host arrays would not fit the
+    host.  Returns (params, rho, u, p); the same formulas as tgv3d."""
+    import torch
+    c = tgv3d(n, nxyz=(n, n, 1), **kw)  # the n^3 case's parameters, one plane of fields
+    prm = c.params.replace(nz=n)
+    m = c.meta
+    N = n * n * n
+    f64 = dict(dtype=torch.float64, device=device)
+    rho = torch.empty(N, **f64)
+    u = torch.empty((3, N), **f64)
+    p = torch.empty(N, **f64)
+    x = (torch.arange(n, **f64) + 0.0) * prm.dx
+    X, Y = x[None, :], x[:, None]
+    for z in range(n):
+        Z = torch.tensor(z * prm.dx, **f64)
+        sl = slice(z * n * n, (z + 1) * n * n)
+        u[0, sl] = (m["V0"] * torch.sin(X) * torch.cos(Y) * torch.cos(Z)).reshape(-1)
+        u[1, sl] = (-m["V0"] * torch.cos(X) * torch.sin(Y) * torch.cos(Z)).reshape(-1)
+        u[2, sl] = 0.0
+        pz = m["p0"] + m["rho0"] * m["V0"] ** 2 / 16.0 * (torch.cos(2 * X) + torch.cos(2 * Y)) * (torch.cos(2 * Z) + 2.0)
+        p[sl] = pz.reshape(-1)
+        rho[sl] = p[sl] / m["T0"]
+    return prm, rho, u, p
+
+
 def sod(nx: int = 400, t_end: float = 0.2, steps: int = 1000, storage: int = STORE_F32,
         mu: float = 1e-6, omega: float = 1.40) -> Case:
     """Sod tube on [0, 1], diaphragm between cells nx/2 - 1 and nx/2 (x = 0.5).

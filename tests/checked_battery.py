@@ -261,6 +261,19 @@ def sc_spectral(dg):
         d.close()
 
 
+def sc_read_cells(dg):
+    """Point probes in the three layouts (two buffers; one buffer after even and after odd
+    steps, with the outflow record of a tube)."""
+    for case in (inputs.random_smooth(40, 21, 7, seed=3), inputs.sod(64)):
+        for streaming, steps in ((0, 3), (1, 2), (1, 3)):
+            dg.part(f"cells {case.params.name} aa{streaming} n{steps}")
+            d = capi.Domain(case.params.replace(streaming=streaming))
+            d.init(case.rho, case.u, case.p)
+            d.step(steps)
+            dg.add(capi.grlb_read_cells(d.h, np.arange(case.params.ncells)))
+            d.close()
+
+
 def sc_ffma(dg):
     import torch
     sink = torch.zeros(4 * 256, dtype=torch.float32, device="cuda")
@@ -271,7 +284,7 @@ def sc_ffma(dg):
 
 SCENARIOS = [sc_sweeps, sc_one_buffer, sc_tubes, sc_ce_init, sc_source, sc_staging_and_checkpoint,
              sc_init_device, sc_batches, sc_serve, sc_slabs, sc_check_finite, sc_noalloc, sc_spectral,
-             sc_ffma]
+             sc_read_cells, sc_ffma]
 
 
 def probe_checker():

@@ -86,6 +86,9 @@ def test_parameter_validation_without_device():
     h = C.c_void_p()
     st = capi.lib().grlb_create(C.byref(capi.to_params(good.replace(nx=0))), None, C.byref(h))
     assert st == -1 and b"nx" in capi.lib().grlb_last_error()
+    cells = (C.c_int64 * 1)(0)
+    out = (C.c_double * 35)()
+    assert capi.lib().grlb_read_cells(None, cells, 1, out) == -1
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (10, 7, 3), (129, 1, 1), (40, 21, 7)])

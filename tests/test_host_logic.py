@@ -156,3 +156,15 @@ def test_bf16_rounding_helper_matches_torch():
     x = np.concatenate([x, [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 0.0]])
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
     assert np.array_equal(bf16_round(x), ref)
+
+
+def test_device_taylor_green_fields_equal_the_host_generator():
+    """inputs.tgv3d_device (fields built plane by plane as torch tensors, here on the CPU)
+    gives tgv3d's parameters and, bit for bit, its fields."""
+    torch = pytest.importorskip("torch")
+    for n, kw in ((8, {}), (12, dict(mach=0.8, storage=inputs.STORE_F16))):
+        c = inputs.tgv3d(n, **kw)
+        prm, rho, u, p = inputs.tgv3d_device(n, device="cpu", **kw)
+        assert prm == c.params
+        assert np.array_equal(rho.numpy(), c.rho) and np.array_equal(u.numpy(), c.u)
+        assert np.array_equal(p.numpy(), c.p)
