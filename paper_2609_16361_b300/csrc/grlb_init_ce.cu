@@ -13,9 +13,11 @@
 // central differences (phi(x + e_a) - phi(x - e_a)) / 2 in lattice units of Q_k, u and T, with
 // periodic wrap or the Dirichlet ghost state beyond a tube's ends; Phi^diff is 0 (rho),
 // -tau_visc (momentum) and -tau_visc u + q (energy) with tau_visc = mu (grad u + grad u^T -
-// 2/3 div u I), q = -kappa grad T at the local temperature.  A_k is formed in FP64; the
-// equilibrium part repeats the FP32 deviation arithmetic of the plain initialisation, so a
-// uniform field gives bitwise the plain initial state.
+// 2/3 div u I), q = -kappa grad T at the local temperature.  A_k is formed in FP32 from
+// differences of the FP64 inputs (B300's FP64 units are a small fraction of its FP32 ones: the
+// same arithmetic in FP64 took 11.2 ms at 256^3); the equilibrium part repeats the FP32
+// deviation arithmetic of the plain initialisation, so a uniform field gives bitwise the plain
+// initial state.
 #include <cuda_runtime.h>
 
 #include "grlb_device.cuh"
@@ -25,27 +27,18 @@ namespace grlb {
 
 namespace {
 
-struct Prim {
+struct Prim {  // physical units, as in the input fields
     double r, u[3], p;
 };
 
-__device__ __forceinline__ Prim lattice_prim(double r, double ux, double uy, double uz, double p, double s) {
+__device__ __forceinline__ Prim prim(double r, double ux, double uy, double uz, double p) {
     Prim q;
     q.r = r;
-    q.u[0] = ux * s;
-    q.u[1] = uy * s;
-    q.u[2] = uz * s;
-    q.p = p * s * s;
+    q.u[0] = ux;
+    q.u[1] = uy;
+    q.u[2] = uz;
+    q.p = p;
     return q;
-}
-
-__device__ __forceinline__ void conserved_of(const Prim& q, double gm1, double Q[5], double& T) {
-    Q[0] = q.r;
-    Q[1] = q.r * q.u[0];
-    Q[2] = q.r * q.u[1];
-    Q[3] = q.r * q.u[2];
-    Q[4] = q.p / gm1 + 0.5 * q.r * (q.u[0] * q.u[0] + q.u[1] * q.u[1] + q.u[2] * q.u[2]);
-    T = q.p / q.r;
 }
 
 }  // namespace
@@ -62,8 +55,9 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
     const float g1 = (float)C.gm1;
     const float Hp_ref = (float)(p_ref / C.gm1 + p_ref);
     auto load = [&](int64_t i) {
-        return lattice_prim(GRLB_LD(rho + i), GRLB_LD(u + i), GRLB_LD(u + N + i), GRLB_LD(u + 2 * N + i), GRLB_LD(p + i), C.s);
+        return prim(GRLB_LD(rho + i), GRLB_LD(u + i), GRLB_LD(u + N + i), GRLB_LD(u + 2 * N + i), GRLB_LD(p + i));
     };
+    const float sl = (float)C.s, sl2 = (float)(C.s * C.s);  // lattice scaling of u and p
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx);
         const int64_t r = c / nx;
@@ -71,11 +65,11 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
         // neighbours along +-x, +-y, +-z: [2a] = +e_a, [2a + 1] = -e_a
         Prim nb[6];
         if (C.bc == 1 && x == nx - 1)
-            nb[0] = lattice_prim(C.ghostR[0], C.ghostR[1], C.ghostR[2], C.ghostR[3], C.ghostR[4], C.s);
+            nb[0] = prim(C.ghostR[0], C.ghostR[1], C.ghostR[2], C.ghostR[3], C.ghostR[4]);
         else
             nb[0] = load(c - x + (x == nx - 1 ? 0 : x + 1));
         if (C.bc == 1 && x == 0)
-            nb[1] = lattice_prim(C.ghostL[0], C.ghostL[1], C.ghostL[2], C.ghostL[3], C.ghostL[4], C.s);
+            nb[1] = prim(C.ghostL[0], C.ghostL[1], C.ghostL[2], C.ghostL[3], C.ghostL[4]);
         else
             nb[1] = load(c - x + (x == 0 ? nx - 1 : x - 1));
         nb[2] = load(c + (int64_t)((y == ny - 1) ? -(ny - 1) : 1) * nx);
@@ -86,43 +80,62 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
         const int ext[3] = {nx, ny, nz};
 
         const Prim q0 = load(c);
-        double Q0[5], T0;
-        conserved_of(q0, C.gm1, Q0, T0);
-        double gQ[5][3], gu[3][3], gT[3];
+        // Differences of neighbouring states without cancellation: the primitive differences
+        // are taken in FP64 (the inputs' precision), everything else in FP32 through the
+        // product rule on pairs, e.g. r+ u+ - r- u- = rb du + ub dr with the pair means rb, ub
+        // (exact identities), so each gradient carries FP32 rounding of itself, not of the
+        // states it is the difference of.  Lattice units: u s, p s^2.
+        float gQ[5][3], gu[3][3], gT[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double Qp[5], Qm[5], Tp, Tm;
-            conserved_of(nb[2 * a], C.gm1, Qp, Tp);
-            conserved_of(nb[2 * a + 1], C.gm1, Qm, Tm);
-            const double h = ext[a] > 1 ? 0.5 : 0.0;
+            const Prim& P = nb[2 * a];
+            const Prim& M = nb[2 * a + 1];
+            const float h = ext[a] > 1 ? 0.5f : 0.0f;
+            const float rP = (float)P.r, rM = (float)M.r;
+            const float dr = (float)(P.r - M.r), dp = (float)(P.p - M.p) * sl2;
+            const float rb = 0.5f * (rP + rM), pb = 0.5f * ((float)P.p + (float)M.p) * sl2;
+            float du[3], ub[3], du2 = 0.0f, u2b = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) gQ[k][a] = h * (Qp[k] - Qm[k]);
+            for (int j = 0; j < 3; ++j) {
+                const float uP = (float)P.u[j] * sl, uM = (float)M.u[j] * sl;
+                du[j] = (float)(P.u[j] - M.u[j]) * sl;
+                ub[j] = 0.5f * (uP + uM);
+                du2 += 2.0f * ub[j] * du[j];                                   // d |u|^2
+                u2b += 0.5f * (uP * uP + uM * uM);
+            }
+            gQ[0][a] = h * dr;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) gu[j][a] = h * (nb[2 * a].u[j] - nb[2 * a + 1].u[j]);
-            gT[a] = h * (Tp - Tm);
+            for (int j = 0; j < 3; ++j) {
+                gQ[1 + j][a] = h * (rb * du[j] + ub[j] * dr);                  // d (r u_j)
+                gu[j][a] = h * du[j];
+            }
+            gQ[4][a] = h * (dp / g1 + 0.5f * (rb * du2 + u2b * dr));           // d (p/(g-1) + r|u|^2/2)
+            gT[a] = h * (rb * dp - pb * dr) / (rP * rM);                       // d (p / r)
         }
-        double fac = 1.0;
+        const float T0 = (float)q0.p * sl2 / (float)q0.r;
+        float fac = 1.0f;
         if (C.sutherland) {
-            const double t = T0 * C.inv_T_ref;
-            fac = (1.0 + C.T_S) * t * sqrt(t) / (t + C.T_S);
+            const float t = T0 * (float)C.inv_T_ref, ts = (float)C.T_S;
+            fac = (1.0f + ts) * t * sqrtf(t) / (t + ts);
         }
-        const double mu = C.mu * fac, kap = C.kap * fac;
-        const double th = gu[0][0] + gu[1][1] + gu[2][2];
-        double tv[3][3];
+        const float mu = (float)C.mu * fac, kap = (float)C.kap * fac;
+        const float th = gu[0][0] + gu[1][1] + gu[2][2];
+        float tv[3][3];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                tv[j][a] = mu * (gu[j][a] + gu[a][j] - (j == a ? 2.0 / 3.0 * th : 0.0));
+                tv[j][a] = mu * (gu[j][a] + gu[a][j] - (j == a ? (2.0f / 3.0f) * th : 0.0f));
+        const float u0[3] = {(float)q0.u[0] * sl, (float)q0.u[1] * sl, (float)q0.u[2] * sl};
         float A[5][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double qa = -kap * gT[a];
-            const double dE = -(tv[a][0] * q0.u[0] + tv[a][1] * q0.u[1] + tv[a][2] * q0.u[2]) + qa;
-            A[0][a] = (float)(-(C.tau[0] - 1.0) * 0.25 * gQ[0][a]);
+            const float qa = -kap * gT[a];
+            const float dE = -(tv[a][0] * u0[0] + tv[a][1] * u0[1] + tv[a][2] * u0[2]) + qa;
+            A[0][a] = -((float)C.tau[0] - 1.0f) * 0.25f * gQ[0][a];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) A[1 + j][a] = (float)(-tv[j][a] - (C.tau[1 + j] - 1.0) * 0.25 * gQ[1 + j][a]);
-            A[4][a] = (float)(dE - (C.tau[4] - 1.0) * 0.25 * gQ[4][a]);
+            for (int j = 0; j < 3; ++j) A[1 + j][a] = -tv[j][a] - ((float)C.tau[1 + j] - 1.0f) * 0.25f * gQ[1 + j][a];
+            A[4][a] = dE - ((float)C.tau[4] - 1.0f) * 0.25f * gQ[4][a];
         }
 
         // equilibrium part: the plain initialisation's deviation arithmetic
