@@ -74,3 +74,31 @@ def decode_populations(raw, prm, nplanes=35, cells=None):
             shift = WI[i] * (Qref[k] + 4.0 * CI[i] @ Jref)
             f[7 * k + i] = d[7 * k + i] * dec[k] + shift
     return f
+
+
+def oracle_update_cells(prm, pre_of, cells):
+    """The oracle's post-collision populations (35, n) of `cells` from the pre-step state:
+    population i of cell x is pulled from f*_i of x - c_i (periodic wrap), or, past the ends of
+    an X_DIRICHLET_EQ tube, taken from the equilibrium of the ghost state.  pre_of(cells) returns
+    the pre-step populations (35, len(cells)) of any cells, e.g. the library's point probes.
+    Also returns the oracle's sensor value chi per cell."""
+    import oracle
+    P = oracle.lattice_params(prm)
+    nx, ny, nz = prm.nx, prm.ny, prm.nz
+    cells = np.asarray(cells, np.int64)
+    x, y, z = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    src = [((x - CI[i][0]) % nx + nx * ((y - CI[i][1]) % ny + ny * ((z - CI[i][2]) % nz))) for i in range(7)]
+    planes = [pre_of(src[i]) for i in range(7)]
+    if prm.bc == 1:
+        gl = oracle.equilibrium_state(P, list(P.left))
+        gr = oracle.equilibrium_state(P, list(P.right))
+        for k in range(5):
+            planes[1][7 * k + 1, x == 0] = gl[7 * k + 1]       # +x population entering at x = 0
+            planes[2][7 * k + 2, x == nx - 1] = gr[7 * k + 2]  # -x population entering at nx - 1
+    out = np.zeros((35, cells.size))
+    chi = np.zeros(cells.size)
+    for n in range(cells.size):
+        fhat = np.array([planes[i][7 * k + i, n] for k in range(5) for i in range(7)])
+        out[:, n], info = oracle.cell(P, fhat)
+        chi[n] = info.chi
+    return out, chi

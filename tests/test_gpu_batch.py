@@ -304,3 +304,43 @@ def test_concurrent_schedule_with_many_domains_and_one_buffer():
         _, raw = solo(c, 39)
         assert np.array_equal(capi.grlb_save(d.h)[32:], raw), c.params.name
         d.close()
+
+
+@pytest.mark.parametrize("schedule", [capi.SCHED_CONCURRENT, capi.SCHED_TABLE_CONST])
+def test_full_batched_configuration_sampled_cells(schedule):
+    """The 64-domain batched configuration (inputs.batched_mix(0): 48 Becker tubes of 128-2048 x
+    4 x 4 cells, shock Mach 1.5-5, and 16 Taylor-Green boxes of 32^3-96^3), batched as the
+    batched leg of the benchmark runs it (concurrent single-domain sweeps with graph replays) and
+    with the constant-record table kernel: after 20 batched steps, one batched step of sampled
+    cells of every domain -- both tube ends of a row and 40 random cells each -- against the
+    oracle's update of the probed pre-step populations (ghost equilibria past the tube ends),
+    within 2e-6 of each field's largest population as at 256^3; the sensor fires in some of
+    them."""
+    from tests.common import oracle_update_cells
+    cases = inputs.batched_mix(0)
+    doms = [capi.Domain(c.params) for c in cases]
+    for d, c in zip(doms, cases):
+        d.init(c.rho, c.u, c.p)
+    b = capi.grlb_batch_create([d.h for d in doms], use_graph=1, schedule=schedule)
+    capi.grlb_batch_step(b, 20)
+    rng = np.random.default_rng(5)
+    picks, wants, fired = [], [], 0
+    for d, c in zip(doms, cases):
+        prm = c.params
+        N = prm.ncells
+        cells = np.unique(np.concatenate([rng.integers(0, N, 40), [0, prm.nx - 1, N - 1]])).astype(np.int64)
+        want, chi = oracle_update_cells(prm, lambda cs: capi.grlb_read_cells(d.h, cs), cells)
+        picks.append(cells)
+        wants.append(want)
+        fired += int((chi > 0).sum())
+    capi.grlb_batch_step(b, 1)
+    capi.grlb_batch_destroy(b)
+    for d, c, cells, want in zip(doms, cases, picks, wants):
+        got = capi.grlb_read_cells(d.h, cells)
+        assert d.steps == 21
+        for k in range(5):
+            blk = slice(7 * k, 7 * k + 7)
+            scale = max(np.abs(want[blk]).max(), 1e-12)
+            assert np.abs(got[blk] - want[blk]).max() / scale < 2e-6, (c.params.name, k)
+        d.close()
+    assert fired > 0

@@ -12,9 +12,8 @@ same cells from the probed pre-step populations of their pull sources."""
 import numpy as np
 import pytest
 
-import oracle
 from paper_2609_16361_b300 import capi, inputs
-from tests.common import CI, decode_populations
+from tests.common import CI, decode_populations, oracle_update_cells
 from tests.test_gpu_storage import spacing
 
 pytestmark = pytest.mark.gpu
@@ -82,21 +81,6 @@ def test_probe_sums_are_the_conserved_fields(streaming):
     d.close()
 
 
-def oracle_update(prm, pre_of, cells):
-    """The oracle's post-collision populations of `cells` from the probed pre-step state:
-    population i of cell x is pulled from f*_i of x - c_i."""
-    P = oracle.lattice_params(prm)
-    nx, ny, nz = prm.nx, prm.ny, prm.nz
-    x, y, z = cells % nx, (cells // nx) % ny, cells // (nx * ny)
-    src = [((x - CI[i][0]) % nx + nx * ((y - CI[i][1]) % ny + ny * ((z - CI[i][2]) % nz))) for i in range(7)]
-    planes = [pre_of(src[i]) for i in range(7)]
-    out = np.zeros((35, cells.size))
-    for n in range(cells.size):
-        fhat = np.array([planes[i][7 * k + i, n] for k in range(5) for i in range(7)])
-        out[:, n], _ = oracle.cell(P, fhat)
-    return out
-
-
 def stored_values(f, prm):
     """FP64 populations -> the 16-bit stored deviations they decode from (exact inverse of the
     decoding up to FP64 rounding), as (35, n) float64."""
@@ -140,7 +124,7 @@ def test_capacity_sizes_sampled_cells(n, storage):
     rng = np.random.default_rng(11)
     edges = [0, 1, n - 1, n, n * n - 1, n * n, N - n, N - 128, N - 1]
     cells = np.unique(np.concatenate([rng.integers(0, N, 2000), edges])).astype(np.int64)
-    want = oracle_update(prm, lambda cs: capi.grlb_read_cells(d.h, cs), cells)
+    want, _ = oracle_update_cells(prm, lambda cs: capi.grlb_read_cells(d.h, cs), cells)
     d.step(1)
     got = capi.grlb_read_cells(d.h, cells)
     d.close()

@@ -168,3 +168,20 @@ def test_device_taylor_green_fields_equal_the_host_generator():
         assert prm == c.params
         assert np.array_equal(rho.numpy(), c.rho) and np.array_equal(u.numpy(), c.u)
         assert np.array_equal(p.numpy(), c.p)
+
+
+def test_per_cell_oracle_update_equals_the_oracle_sweep():
+    """The per-cell update the sampled-cell parity tests use (tests.common.oracle_update_cells:
+    pull sources by periodic wrap, ghost equilibria past the ends of a Dirichlet tube) gives
+    bit for bit the oracle's own sweep, for every cell of two tubes and a periodic box."""
+    import oracle
+    from tests.common import oracle_update_cells
+    for c in (inputs.sod(64), inputs.becker(128, ny=4, nz=4), inputs.random_smooth(12, 5, 4, seed=2)):
+        o = oracle.Oracle(c.params)
+        o.init_primitive(c.rho, c.u, c.p)
+        o.step(3)
+        pre = o.f.copy()
+        o.step(1)
+        cells = np.arange(c.params.ncells)
+        want, _ = oracle_update_cells(c.params, lambda cs: pre[:, cs], cells)
+        assert np.array_equal(want, o.f[:, cells]), c.params.name
