@@ -24,6 +24,7 @@ same workload (one oracle sweep of 256 x 256 x 16 cells per step).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -41,6 +42,8 @@ SWEEPS_PER_STEP = 50
 # collision readings: name -> (grlb_collision, kernel label)
 COLLISIONS = {"rlb": (1, "RLB"), "gated": (2, "RLB_GATED"), "bgk": (0, "BGK")}
 BYTES_PER_LUP = {0: 280, 1: 140, 2: 140}
+# moment storage (regularized collision): 20 FP32 values per cell read and written
+BYTES_PER_LUP_MOMENTS = 160
 KERNEL_SOURCES = ["paper_2609_16361_b300/csrc/grlb_device.cuh", "paper_2609_16361_b300/csrc/grlb_check.cuh",
                   "paper_2609_16361_b300/csrc/grlb_kernels.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -252,6 +255,12 @@ def run_ours(args):
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
     coll, coll_label = COLLISIONS[args.collision]
     case = inputs.tgv3d(n, storage=storage, collision=coll)
+    moments = args.state == "moments"
+    if moments:
+        if storage != 0 or args.collision != "rlb":
+            print(json.dumps({"error": "--state moments needs --storage f32 --collision rlb"}), flush=True)
+            return 1
+        case = dataclasses.replace(case, params=case.params.replace(streaming=2))
     N = case.params.ncells
     dev = torch.device("cuda", local)
     rho_d = torch.from_numpy(case.rho).to(dev)
@@ -345,18 +354,19 @@ def run_ours(args):
     e2e_lups = job_mlups(ws, N, SWEEPS_PER_STEP * e2e_steps, te) * 1e6
 
     peak, peak_src = measured_peaks()
-    bpl = BYTES_PER_LUP[storage]
+    bpl = BYTES_PER_LUP_MOMENTS if moments else BYTES_PER_LUP[storage]
+    skey = "_moments" if moments else ""
     achieved = bpl * N / (sweep_med / 1e3) / 1e9
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         t = json.load(open(TRAFFIC_FILE))
-        rec = t.get(f"tgv{n}_{args.storage}" + ("" if args.collision == "rlb" else f"_{args.collision}"))
+        rec = t.get(f"tgv{n}_{args.storage}" + ("" if args.collision == "rlb" else f"_{args.collision}") + skey)
         if rec and rec.get("source_sha") == kernel_source_sha():
             traffic = rec.get("dram_bytes_per_launch")
 
     issue = None
     rate = ffma_issue_rate(stream)
-    ipc = instructions_per_cell(args.storage)
+    ipc = instructions_per_cell(args.storage + skey)
     if ipc is not None:
         ach = ipc * N / (sweep_med / 1e3)
         issue = {"bound": "issue", "achieved": ach, "peak": rate, "unit": "warp-inst/s",
@@ -379,14 +389,16 @@ def run_ours(args):
                        "mach": 1.25, "re": 1600, "sweeps_per_step": SWEEPS_PER_STEP,
                        "step": "init kernel + 49 sweeps + 1 diagnostic sweep (FP64 reductions)",
                        "parallelism": f"replicas{ws}",
-                       "l2": "inputs larger than L2 (4.7 GB populations), no flush"},
+                       "state": ("moments: Q_k, J*_k of the regularized outgoing set, 20 FP32 per cell"
+                                 if moments else "populations: 35 per cell"),
+                       "l2": f"inputs larger than L2 ({bpl * N / 1e9:.1f} GB of state), no flush"},
             "e2e": {"value": e2e_lups / 1e6, "unit": "MLUP/s",
                     "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 8 * 13},
             # per step: init + 49 plain sweeps + diagnostic sweep + 2 finalize stages
             "gpu_launches": args.steps * (SWEEPS_PER_STEP + 3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"sweep_kernel<{args.storage},{coll_label}> (plain sweep)",
+                         "kernel": f"sweep_kernel<{args.storage},{coll_label}{',moments' if moments else ''}> (plain sweep)",
                          "bytes_per_launch": bpl * N, "launch_ms_median": sweep_med,
                          "peak_source": f"{peak_src} hbm_gbs"},
             "issue_ceiling": issue,
@@ -1237,6 +1249,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--state", default="populations", choices=["populations", "moments"],
+                    help="tgv: keep the state as 35 populations or as the 20 moments of the "
+                         "regularized outgoing set (FP32, --collision rlb)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parallelism", default="replicas", choices=["replicas", "zslab"],
                     help="N > 1: independent replica domains, or one domain split along z over the ranks")

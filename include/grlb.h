@@ -74,8 +74,16 @@ typedef struct {
     int32_t streaming;          /* 0: two population buffers (pull); 1: one buffer updated in
                                    place by the AA pattern (half the memory, same traffic, the
                                    same collisions: results agree with 0 to FP32 rounding);
-                                   sources need 0, batches 0 for domains they run in the
-                                   batched kernel (below solo_min_cells)                     */
+                                   2: two buffers of moments -- the regularized collision's
+                                   outgoing set of field k is w_i (Q_k + c_i . J*_k / cs^2),
+                                   so the state is kept as (Q_k, J*_k), 20 values per cell
+                                   instead of 35, and the pull rebuilds each population with
+                                   the collide's own FP32 operations: results bitwise those of
+                                   0 (FP32 storage and GRLB_COLL_RLB_SENSOR only; 160 instead
+                                   of 280 bytes per cell update); sources need 0, batches 0
+                                   for domains they run in the batched kernel (below
+                                   solo_min_cells; moment domains always run their own sweep)
+                                   */
     double T_S;                 /* Sutherland constant relative to T_ref (0.4042)           */
     double omega_rho, omega_mom, omega_E; /* per-field relaxation 1/tau_LB, in (0, 2]       */
     double omega_min;           /* sensor floor rate (Listing 2)                            */
@@ -210,8 +218,11 @@ grlb_status grlb_read_cells(grlb_domain* d, const int64_t* cells, int64_t n, dou
 
 /* Raw checkpoint: stored populations + step counter.  grlb_save with buf == NULL sets
  * *bytes to the size needed; otherwise *bytes must be at least that size.  grlb_load
- * requires a buffer written by grlb_save of a domain with the same params.
- * Format: a 32-byte header, then the population buffer as the library keeps it in device
+ * requires a buffer written by grlb_save of a domain with the same cells, storage and
+ * streaming (the header's last 32-bit field records grlb_params.streaming).  Moment storage
+ * (streaming 2) saves its moment buffer: bricks of 128 cells, each holding 20 rows 4 k + m
+ * (m = 0: Q_k, 1..3: J*_k,x..z, deviations from the reference state), 128 FP32 values each.
+ * Otherwise the format is a 32-byte header, then the population buffer as the library keeps it in device
  * memory -- the cell-brick layout: cells in storage order (x fastest) are grouped into
  * ceil(N / 128) bricks of 128 cells; a brick holds its 35 population rows q = 7k + i (field k
  * = rho, m_x, m_y, m_z, E; link i = 0, +x, -x, +y, -y, +z, -z) one after the other, 128
@@ -234,7 +245,7 @@ int64_t grlb_steps_done(const grlb_domain* d);
  *    domains are dealt, largest first, over up to 32 side streams forked from and joined back
  *    into the batch stream, so that the kernels of different domains run concurrently and fill
  *    one another's waves.  Results are bitwise those of grlb_step.  Domains may use one-buffer
- *    streaming.
+ *    streaming or moment storage.
  *  GRLB_SCHED_TABLE_CONST: the small domains (below solo_min_cells) advance together in one
  *    launch per step and (storage, collision) group of the batched sweep, one 128-thread CTA per
  *    tile, their records in a constant table of 160 slots shared by the process (a batch that

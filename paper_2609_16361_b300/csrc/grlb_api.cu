@@ -40,10 +40,19 @@ grlb_status cuda_fail(cudaError_t e, const char* what) {
 size_t elem_bytes(int storage) { return storage == GRLB_STORE_F32 ? 4 : 2; }
 // one population buffer: N cells in cell bricks (whole bricks of 35 x 128 elements)
 size_t pop_bytes(size_t N, int storage) { return (size_t)grlb::brick_elems((int64_t)N) * elem_bytes(storage); }
+// streaming = 1: one population buffer (AA pattern); 2: two buffers of moments (FP32, regularized
+// collision: 20 values per cell instead of 35)
+bool one_buffer(const grlb_params& p) { return p.streaming == 1; }
+bool moment_storage(const grlb_params& p) { return p.streaming == 2; }
+// one state buffer of N cells
+size_t state_bytes(size_t N, const grlb_params& p) {
+    if (moment_storage(p)) return (size_t)grlb::brick_elems_m((int64_t)N) * sizeof(float);
+    return pop_bytes(N, p.storage);
+}
 
 // One-buffer Dirichlet domains keep the populations that leave through the ends in an odd step.
 size_t outflow_bytes(const grlb_params& p) {
-    return (p.streaming && p.bc == GRLB_BC_X_DIRICHLET_EQ) ? 10 * (size_t)p.ny * p.nz * elem_bytes(p.storage) : 0;
+    return (one_buffer(p) && p.bc == GRLB_BC_X_DIRICHLET_EQ) ? 10 * (size_t)p.ny * p.nz * elem_bytes(p.storage) : 0;
 }
 
 // Power-of-two storage scale for the 16-bit modes: deviations of field k are divided by a
@@ -117,7 +126,9 @@ static grlb_status validate(const grlb_params* p) {
         p->collision != GRLB_COLL_RLB_GATED)
         return fail(GRLB_EINVAL, "bad collision");
     if (p->storage < GRLB_STORE_F32 || p->storage > GRLB_STORE_BF16) return fail(GRLB_EINVAL, "bad storage");
-    if (p->streaming != 0 && p->streaming != 1) return fail(GRLB_EINVAL, "streaming must be 0 or 1");
+    if (p->streaming < 0 || p->streaming > 2) return fail(GRLB_EINVAL, "streaming must be 0, 1 or 2");
+    if (p->streaming == 2 && (p->storage != GRLB_STORE_F32 || p->collision != GRLB_COLL_RLB_SENSOR))
+        return fail(GRLB_EINVAL, "moment storage (streaming = 2) needs FP32 storage and the regularized collision");
     if (!(p->dx > 0) || !(p->dt > 0)) return fail(GRLB_EINVAL, "dx, dt must be > 0");
     if (!(p->gamma > 1)) return fail(GRLB_EINVAL, "gamma must be > 1");
     if (!(p->mu_ref >= 0) || !(p->prandtl > 0) || !(p->T_ref > 0) || !(p->T_S >= 0))
@@ -216,14 +227,17 @@ static void fill_domain_dev(grlb_domain* d) {
 
 // CTA of 128 threads = bx cells along x times by rows.  bx in {128, 64, 32} is the width that
 // pads the row least (idle lanes cost throughput: nx = 130 on 128-wide tiles leaves half the
-// lanes of every row idle), the wider one on ties.
+// lanes of every row idle), the wider one on ties -- the narrower one for moment storage, whose
+// sweep reads every cell's moments from up to 7 threads: with 4 rows per CTA the +-y sources
+// are mostly L1 hits (256^3: 0.518 ms on 32 x 4 tiles, 0.522 on 64 x 2, 0.532 on 128 x 1).
 static void choose_launch(grlb_domain* d) {
     const int nx = d->P.nx;
+    const bool narrow = moment_storage(d->P);
     int bx = 128;
     long best = -1;
     for (int w = 128; w >= 32; w /= 2) {
         const long padded = (long)((nx + w - 1) / w) * w;
-        if (best < 0 || padded < best) {
+        if (best < 0 || padded < best || (narrow && padded == best)) {
             best = padded;
             bx = w;
         }
@@ -250,8 +264,8 @@ size_t grlb_bytes_for(const grlb_params* p) {
     tmp.P = *p;
     choose_launch(&tmp);
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    const size_t nbuf = p->streaming ? 1 : 2;
-    return nbuf * pop_bytes(N, p->storage) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+    const size_t nbuf = one_buffer(*p) ? 1 : 2;
+    return nbuf * state_bytes(N, *p) + (size_t)(tmp.nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
            NDIAG * 8 + outflow_bytes(*p);
 }
 
@@ -268,22 +282,22 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
     fill_domain_dev(d);
     choose_launch(d);
     const size_t N = (size_t)d->D.plane;
-    const size_t pb = pop_bytes(N, p->storage);
+    const size_t pb = state_bytes(N, *p);
     retain_pool();
     cudaStream_t s = d->stream;
     cudaError_t e = cudaSuccess;
     d->D.buf[0] = d->D.buf[1] = nullptr;
     e = grlb::dev_alloc(&d->D.buf[0], pb, s);
     if (e == cudaSuccess) {
-        if (p->streaming) d->D.buf[1] = d->D.buf[0];  // one buffer, updated in place
+        if (one_buffer(*p)) d->D.buf[1] = d->D.buf[0];  // one buffer, updated in place
         else e = grlb::dev_alloc(&d->D.buf[1], pb, s);
     }
     // the last brick's cells past N are never written by a kernel: zero them once so that
     // checkpoints of equal states are equal bytes
-    const size_t tail = grlb::NP * grlb::kBrick * elem_bytes(p->storage);
-    for (int b = 0; b < (p->streaming ? 1 : 2) && e == cudaSuccess; ++b)
+    const size_t tail = (moment_storage(*p) ? grlb::NM : grlb::NP) * grlb::kBrick * elem_bytes(p->storage);
+    for (int b = 0; b < (one_buffer(*p) ? 1 : 2) && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(static_cast<char*>(d->D.buf[b]) + pb - tail, 0, tail, s);
-    if (e == cudaSuccess && p->streaming && p->bc == GRLB_BC_X_DIRICHLET_EQ)
+    if (e == cudaSuccess && one_buffer(*p) && p->bc == GRLB_BC_X_DIRICHLET_EQ)
         e = grlb::dev_alloc(&d->D.outflow, outflow_bytes(*p), s);
     if (e == cudaSuccess)
         e = grlb::dev_alloc(&d->partials, (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * sizeof(double), s);
@@ -294,7 +308,7 @@ grlb_status grlb_create(const grlb_params* p, void* stream, grlb_domain** out) {
         return fail(e == cudaErrorMemoryAllocation ? GRLB_ENOMEM : GRLB_ECUDA,
                     std::string("grlb_create: ") + cudaGetErrorString(e));
     }
-    d->bytes = (p->streaming ? 1 : 2) * pb + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
+    d->bytes = (one_buffer(*p) ? 1 : 2) * pb + (size_t)(d->nblocks + grlb::kDiagStageRecords) * NDIAG * 8 +
                NDIAG * 8 + outflow_bytes(*p);
     *out = d;
     return GRLB_OK;
@@ -451,16 +465,16 @@ grlb_status grlb_init_from_stage(grlb_domain* d) {
 static grlb_status sweep_once(grlb_domain* d, bool diag) {
     const int c = d->D.cur;
     cudaError_t e;
-    if (d->P.streaming) {
+    if (one_buffer(d->P)) {
         const int pattern = (d->steps % 2 == 0) ? 1 : 2;
         e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, pattern, d->D.buf[0], d->D.buf[0], diag,
                                d->partials, d->grid, d->block, d->stream);
-    } else {
-        e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, 0, d->D.buf[c], d->D.buf[c ^ 1], diag,
-                               d->partials, d->grid, d->block, d->stream);
+    } else {  // pull from one buffer into the other: populations (pattern 0) or moments (3)
+        e = grlb::launch_sweep(d->D, d->P.storage, d->P.collision, moment_storage(d->P) ? 3 : 0, d->D.buf[c],
+                               d->D.buf[c ^ 1], diag, d->partials, d->grid, d->block, d->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
-    if (!d->P.streaming) d->D.cur = c ^ 1;
+    if (!one_buffer(d->P)) d->D.cur = c ^ 1;
     d->steps += 1;
     return GRLB_OK;
 }
@@ -517,7 +531,7 @@ static grlb_status capture_step_graph(grlb_domain* d) {
 // The captured sweeps read buf[graph_cur] first; a one-buffer domain's sweeps also depend on
 // the step parity (the AA pattern alternates), a two-buffer domain's do not.
 static bool at_graph_start(const grlb_domain* d) {
-    if (d->P.streaming) return (int)(d->steps & 1) == d->graph_parity;
+    if (one_buffer(d->P)) return (int)(d->steps & 1) == d->graph_parity;
     return d->D.cur == d->graph_cur;
 }
 
@@ -599,7 +613,7 @@ grlb_status grlb_diag_read(grlb_domain* d, grlb_diag* out) {
 
 grlb_status grlb_check_finite(grlb_domain* d, int32_t* flag) {
     if (!d || !flag) return fail(GRLB_EINVAL, "grlb_check_finite: NULL argument");
-    const size_t bytes = pop_bytes((size_t)d->D.plane, d->P.storage);
+    const size_t bytes = state_bytes((size_t)d->D.plane, d->P);
     grlb::Lent lf(flag, sizeof(int32_t), d->stream);
     GRLB_CU(grlb::launch_check_finite(d->D.buf[d->D.cur], (int64_t)bytes, d->P.storage, flag, d->stream));
     return GRLB_OK;
@@ -610,7 +624,7 @@ grlb_status grlb_read_conserved(grlb_domain* d, double* out) {
     const size_t N = (size_t)d->D.plane;
     double* stage = nullptr;
     GRLB_CU(grlb::dev_alloc(&stage, 5 * N * sizeof(double), d->stream));
-    const int gather = (d->P.streaming && (d->steps & 1)) ? 1 : 0;
+    const int gather = moment_storage(d->P) ? 2 : (one_buffer(d->P) && (d->steps & 1)) ? 1 : 0;
     cudaError_t e = grlb::launch_conserved(d->D, d->P.storage, d->D.buf[d->D.cur], stage, d->s, d->rho_ref,
                                            d->E_ref, gather, d->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, stage, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, d->stream);
@@ -643,7 +657,7 @@ grlb_status grlb_read_cells(grlb_domain* d, const int64_t* cells, int64_t n, dou
             dec.shift[7 * k + i] = w * (Qref[k] + 4.0 * c * d->p_ref);
         }
     }
-    const int layout = !d->P.streaming ? 0 : (d->steps & 1) ? 2 : 1;
+    const int layout = moment_storage(d->P) ? 3 : !one_buffer(d->P) ? 0 : (d->steps & 1) ? 2 : 1;
     cudaStream_t s = d->stream;
     char* stage = nullptr;
     const size_t cb = (size_t)n * sizeof(int64_t), ob = (size_t)n * grlb::NP * sizeof(double);
@@ -690,14 +704,14 @@ struct SaveHeader {
     uint64_t magic;
     int64_t steps;
     int64_t N;
-    int32_t storage, pad;
+    int32_t storage, layout;  // layout: grlb_params.streaming of the saving domain
 };
 const uint64_t kMagic = 0x3242524c47ULL;  // "GLRB2": cell-brick population layout
 }  // namespace
 
 grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
     if (!d || !bytes) return fail(GRLB_EINVAL, "grlb_save: NULL argument");
-    const size_t pop = pop_bytes((size_t)d->D.plane, d->P.storage);
+    const size_t pop = state_bytes((size_t)d->D.plane, d->P);
     const size_t ob = outflow_bytes(d->P);
     const size_t need = sizeof(SaveHeader) + pop + ob;
     if (!buf) {
@@ -705,7 +719,7 @@ grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
         return GRLB_OK;
     }
     if (*bytes < need) return fail(GRLB_EINVAL, "grlb_save: buffer too small");
-    SaveHeader h{kMagic, d->steps, d->D.plane, d->P.storage, 0};
+    SaveHeader h{kMagic, d->steps, d->D.plane, d->P.storage, d->P.streaming};
     std::memcpy(buf, &h, sizeof h);
     GRLB_CU(cudaMemcpyAsync(static_cast<char*>(buf) + sizeof h, d->D.buf[d->D.cur], pop, cudaMemcpyDeviceToHost,
                             d->stream));
@@ -719,13 +733,13 @@ grlb_status grlb_save(grlb_domain* d, void* buf, size_t* bytes) {
 
 grlb_status grlb_load(grlb_domain* d, const void* buf, size_t bytes) {
     if (!d || !buf) return fail(GRLB_EINVAL, "grlb_load: NULL argument");
-    const size_t pop = pop_bytes((size_t)d->D.plane, d->P.storage);
+    const size_t pop = state_bytes((size_t)d->D.plane, d->P);
     const size_t ob = outflow_bytes(d->P);
     if (bytes < sizeof(SaveHeader) + pop + ob) return fail(GRLB_EINVAL, "grlb_load: buffer too small");
     SaveHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != kMagic || h.N != d->D.plane || h.storage != d->P.storage)
-        return fail(GRLB_EINVAL, "grlb_load: checkpoint does not match this domain");
+    if (h.magic != kMagic || h.N != d->D.plane || h.storage != d->P.storage || h.layout != d->P.streaming)
+        return fail(GRLB_EINVAL, "grlb_load: checkpoint does not match this domain (cells, storage or layout)");
     d->D.cur = 0;
     GRLB_CU(cudaMemcpyAsync(d->D.buf[0], static_cast<const char*>(buf) + sizeof h, pop, cudaMemcpyHostToDevice,
                             d->stream));
@@ -1040,9 +1054,13 @@ grlb_status grlb_batch_create(grlb_domain* const* domains, int n, const grlb_bat
             return fail(GRLB_EINVAL, "NULL domain in batch");
         }
         const int64_t thr = b->cfg.solo_min_cells == 0 ? 262144 : b->cfg.solo_min_cells;
-        const int solo = sched == GRLB_SCHED_CONCURRENT || (thr > 0 && domains[i]->D.plane >= thr) ? 1 : 0;
+        // moment-storage domains always run their own sweep (the table kernels pull populations)
+        const int solo = sched == GRLB_SCHED_CONCURRENT || moment_storage(domains[i]->P) ||
+                                 (thr > 0 && domains[i]->D.plane >= thr)
+                             ? 1
+                             : 0;
         // the batched kernel runs two-buffer domains without a source; a domain advanced on its
-        // own (solo) may use one-buffer streaming
+        // own (solo) may use one-buffer streaming or moment storage
         if (domains[i]->D.src || (domains[i]->P.streaming && !solo)) {
             delete b;
             return fail(GRLB_EINVAL, "batched domains need two-buffer streaming (unless at least solo_min_cells "
@@ -1423,7 +1441,7 @@ extern "C" grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double*
     }
     std::vector<double> hpart(np);
     std::vector<unsigned long long> hbins(std::max(nb, 1));
-    const int gather = (P.streaming && (d->steps & 1)) ? 1 : 0;
+    const int gather = moment_storage(P) ? 2 : (one_buffer(P) && (d->steps & 1)) ? 1 : 0;
     double ke_sum = 0.0;
     cudaError_t e = cudaMemcpyAsync(tw, htw.data(), htw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, std::max(nb, 1) * sizeof(unsigned long long), st);

@@ -6,7 +6,8 @@
 //   one buffer, even steps done:   slot opp(i) of x (the AA-even write, and the initial state);
 //   one buffer, odd steps done:    slot i of x + c_i (the AA-odd push), or, for the +x / -x
 //                                  populations leaving an X_DIRICHLET_EQ tube, the outflow
-//                                  record [side][k][y + ny z].
+//                                  record [side][k][y + ny z];
+//   moments:                       rebuilt from the cell's own Q_k, J*_k (mom_at layout).
 // One thread per (population row, listed cell): out[q n + j] = f_q(cells[j]) in FP64 lattice
 // units, the stored deviation decoded and the reference equilibrium added back.
 #include <cuda_runtime.h>
@@ -33,6 +34,15 @@ __global__ void __launch_bounds__(256) read_cells_kernel(const __grid_constant__
         const int64_t nx = D.nx, ny = D.ny, nz = D.nz;
         const int64_t x = c % nx, r = c / nx, y = r % ny, z = r / ny;
         const T* src;
+        if (layout == 3) {  // moments: f*_q rebuilt from the cell's own Q_k, J*_k
+            const T* m = buf + mom_at(c) + (int64_t)(4 * k) * kBrick;
+            const float mq = Store<S>::ld(m);
+            const float v = i == 0 ? 0.25f * mq
+                                   : fmaf(((i & 1) ? 0.5f : -0.5f), Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick),
+                                          mq * 0.125f);
+            GRLB_ST(out + t, (double)v * dec.dec[k] + dec.shift[q]);
+            continue;
+        }
         if (layout == 0) {
             src = buf + brick_at(c) + (int64_t)q * kBrick;
         } else if (layout == 1) {

@@ -53,6 +53,22 @@ __host__ __device__ __forceinline__ int64_t brick_elems(int64_t N) {
     return (N + kBrick - 1) / kBrick * (int64_t)(NP * kBrick);
 }
 static_assert(kBrick == 128, "brick_at_u32 shifts by log2(kBrick)");
+// Moment storage (regularized collision): the outgoing set of field k is w_i (Q_k + c_i . J*_k /
+// cs^2), so a cell's state is the 4 numbers (Q_k, J*_k) per field: bricks of kBrick cells with
+// NM = 20 rows r = 4 k + m (m = 0: Q_k deviation, 1..3: J*_k,x..z), so value m of field k of
+// cell c is element mom_at(c) + (4 k + m) kBrick.  A pull reads Q_k and one component of J*_k
+// of each source: scalar loads of whole 128-byte row segments per warp, no unused components.
+constexpr int NM = 4 * NF;
+__host__ __device__ __forceinline__ int64_t mom_at(int64_t c) {
+    const uint64_t u = (uint64_t)c;
+    return (int64_t)((u / kBrick) * (uint64_t)(NM * kBrick) + (u % kBrick));
+}
+__device__ __forceinline__ int64_t mom_at_u32(uint32_t c) {
+    return (int64_t)(c >> 7) * (NM * kBrick) + (c & (kBrick - 1));
+}
+__host__ __device__ __forceinline__ int64_t brick_elems_m(int64_t N) {  // floats of one buffer
+    return (N + kBrick - 1) / kBrick * (int64_t)(NM * kBrick);
+}
 
 enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
 // C_GATED: BGK where the sensor is off (chi = 0), the regularized collision with omega_h where
@@ -180,29 +196,33 @@ __device__ __forceinline__ void field_moments(const DomainDev& D, int k, float d
     }
 }
 
-template <int S, int COLL, bool DIAG>
+template <int S, int COLL, bool DIAG, bool MOM = false>
 __device__ __forceinline__ void collide_moments(const DomainDev& D, const float (&dQ)[NF],
                                                 const float (&dJ)[NF][3], const float (&d)[NF][NQ],
                                                 float (&o)[NF][NQ], CellDiag* cd);
 
 // In: d[k][i] = pulled stored values (deviations, x enc[k] when scaled).  Out: o[k][i] = the
 // values to store (post-collision deviations in the same units).
-template <int S, int COLL, bool DIAG>
+// MOM: the outgoing set as moments, o[k][0] = Q_k, o[k][1..3] = J*_k (regularized collision
+// only: its outgoing set is w_i (Q_k + c_i . J*_k / cs^2), population i being
+// fmaf(+-1/2, J*_k,a, Q_k / 8) for the links along axis a and Q_k / 4 at rest).
+template <int S, int COLL, bool DIAG, bool MOM = false>
 __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF][NQ],
                                         float (&o)[NF][NQ], CellDiag* cd) {
     float dQ[NF], dJ[NF][3];
 #pragma unroll
     for (int k = 0; k < NF; ++k)
         field_moments<S>(D, k, d[k][0], d[k][1], d[k][2], d[k][3], d[k][4], d[k][5], d[k][6], dQ[k], dJ[k]);
-    collide_moments<S, COLL, DIAG>(D, dQ, dJ, d, o, cd);
+    collide_moments<S, COLL, DIAG, MOM>(D, dQ, dJ, d, o, cd);
 }
 
 // Everything after the moments: primitives and floors, reconstruction, sensor, closures,
 // equilibrium and collision.  The regularized collision needs only (dQ, dJ); BGK also reads d.
-template <int S, int COLL, bool DIAG>
+template <int S, int COLL, bool DIAG, bool MOM>
 __device__ __forceinline__ void collide_moments(const DomainDev& D, const float (&dQ)[NF],
                                                 const float (&dJ)[NF][3], const float (&d)[NF][NQ],
                                                 float (&o)[NF][NQ], CellDiag* cd) {
+    static_assert(!MOM || (COLL == C_RLB && S == S_F32), "moment storage: FP32, regularized collision");
     constexpr bool SC = Store<S>::scaled;
     const float gm1 = D.gm1;
     // primitives with positivity floors (Alg. 1); Q_k themselves stay unfloored
@@ -365,6 +385,13 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
             float js[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) js[c] = Pd[k][c] + onem * (nA[k][c] - Fd[k][c]);
+            if (MOM) {
+                o[k][0] = dQ[k];
+                o[k][1] = js[0];
+                o[k][2] = js[1];
+                o[k][3] = js[2];
+                continue;
+            }
             const float q1 = dQ[k] * cq1;
             o[k][0] = dQ[k] * cq0;
             o[k][1] = fmaf(cj, js[0], q1);

@@ -56,7 +56,12 @@ __device__ __forceinline__ PullIdx pull_index(const DomainDev& D, int x, int y, 
 // step reads the ghost value instead of the missing neighbour, drops the population that
 // leaves the domain, and writes the ghost's incoming population into the boundary cell's own
 // slot (nobody else reads it in that step) for the AA_EVEN step to find.
-enum Pattern { PULL = 0, AA_ODD = 1, AA_EVEN = 2 };
+// MOM: two buffers of moments (brick_at_m layout, regularized collision): the pull rebuilds
+// f*_i(x - c_i) from the source cell's Q_k and J*_k with the collide's own operations, so the
+// sweep computes bit for bit what PULL computes on the populations those moments stand for,
+// reading 20 values per cell (each used by up to 7 cells, the reuse caught by L1 / L2) and
+// writing 20 instead of 35.
+enum Pattern { PULL = 0, AA_ODD = 1, AA_EVEN = 2, MOM = 3 };
 
 template <int S, int PAT>
 __device__ __forceinline__ float ld_pop(const typename Store<S>::T* p) {
@@ -81,37 +86,69 @@ __device__ __forceinline__ PullAt pull_at(const PullIdx& P) {
     return A;
 }
 
+// element offsets (moment storage) of the cell and its 6 pull sources
+__device__ __forceinline__ PullAt pull_at_m(const PullIdx& P) {
+    PullAt A;
+    A.c = mom_at_u32((uint32_t)P.c);
+    A.xm = mom_at_u32((uint32_t)P.xm);
+    A.xp = mom_at_u32((uint32_t)P.xp);
+    A.ym = mom_at_u32((uint32_t)P.ym);
+    A.yp = mom_at_u32((uint32_t)P.yp);
+    A.zm = mom_at_u32((uint32_t)P.zm);
+    A.zp = mom_at_u32((uint32_t)P.zp);
+    return A;
+}
+
+// Population i of the outgoing set (Q, J) of a field: Q / 4 at rest, fmaf(+-1/2, J_a, Q / 8)
+// along axis a (the regularized collide's own operations).
+__device__ __forceinline__ float mom_pop(float q, float j, float sign) { return fmaf(sign * 0.5f, j, q * 0.125f); }
+
 template <int S, int PAT>
 __device__ __forceinline__ void load_cell(const DomainDev& D, const typename Store<S>::T* fin,
                                           const PullIdx& P, const PullAt& A, float (&d)[NF][NQ]) {
     using St = Store<S>;
     using T = typename St::T;
-    const T* bc = fin + A.c;
-    const T* bxm = fin + A.xm;
-    const T* bxp = fin + A.xp;
-    const T* bym = fin + A.ym;
-    const T* byp = fin + A.yp;
-    const T* bzm = fin + A.zm;
-    const T* bzp = fin + A.zp;
+    if constexpr (PAT == MOM) {
+        static_assert(S == S_F32, "moment storage is FP32");
 #pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        const int q = 7 * k * kBrick;
-        const float gl = D.ghostL_st[k], gr = D.ghostR_st[k];  // stored units
-        if (PAT == AA_EVEN) {
+        for (int k = 0; k < NF; ++k) {
+            const int q = 4 * k * kBrick;
+            d[k][0] = 0.25f * St::ld(fin + A.c + q);
+            d[k][1] = P.gl ? D.ghostL_st[k] : mom_pop(St::ld(fin + A.xm + q), St::ld(fin + A.xm + q + kBrick), 1.0f);
+            d[k][2] = P.gr ? D.ghostR_st[k] : mom_pop(St::ld(fin + A.xp + q), St::ld(fin + A.xp + q + kBrick), -1.0f);
+            d[k][3] = mom_pop(St::ld(fin + A.ym + q), St::ld(fin + A.ym + q + 2 * kBrick), 1.0f);
+            d[k][4] = mom_pop(St::ld(fin + A.yp + q), St::ld(fin + A.yp + q + 2 * kBrick), -1.0f);
+            d[k][5] = mom_pop(St::ld(fin + A.zm + q), St::ld(fin + A.zm + q + 3 * kBrick), 1.0f);
+            d[k][6] = mom_pop(St::ld(fin + A.zp + q), St::ld(fin + A.zp + q + 3 * kBrick), -1.0f);
+        }
+    } else {
+        const T* bc = fin + A.c;
+        const T* bxm = fin + A.xm;
+        const T* bxp = fin + A.xp;
+        const T* bym = fin + A.ym;
+        const T* byp = fin + A.yp;
+        const T* bzm = fin + A.zm;
+        const T* bzp = fin + A.zp;
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) d[k][i] = ld_pop<S, PAT>(bc + q + i * kBrick);
-        } else {
-            // PULL reads row i of the neighbour; AA_ODD reads row opp(i) of it
-            const int o1 = PAT == PULL ? 1 : 2, o2 = PAT == PULL ? 2 : 1;
-            const int o3 = PAT == PULL ? 3 : 4, o4 = PAT == PULL ? 4 : 3;
-            const int o5 = PAT == PULL ? 5 : 6, o6 = PAT == PULL ? 6 : 5;
-            d[k][0] = ld_pop<S, PAT>(bc + q);
-            d[k][1] = P.gl ? gl : ld_pop<S, PAT>(bxm + q + o1 * kBrick);
-            d[k][2] = P.gr ? gr : ld_pop<S, PAT>(bxp + q + o2 * kBrick);
-            d[k][3] = ld_pop<S, PAT>(bym + q + o3 * kBrick);
-            d[k][4] = ld_pop<S, PAT>(byp + q + o4 * kBrick);
-            d[k][5] = ld_pop<S, PAT>(bzm + q + o5 * kBrick);
-            d[k][6] = ld_pop<S, PAT>(bzp + q + o6 * kBrick);
+        for (int k = 0; k < NF; ++k) {
+            const int q = 7 * k * kBrick;
+            const float gl = D.ghostL_st[k], gr = D.ghostR_st[k];  // stored units
+            if (PAT == AA_EVEN) {
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) d[k][i] = ld_pop<S, PAT>(bc + q + i * kBrick);
+            } else {
+                // PULL reads row i of the neighbour; AA_ODD reads row opp(i) of it
+                const int o1 = PAT == PULL ? 1 : 2, o2 = PAT == PULL ? 2 : 1;
+                const int o3 = PAT == PULL ? 3 : 4, o4 = PAT == PULL ? 4 : 3;
+                const int o5 = PAT == PULL ? 5 : 6, o6 = PAT == PULL ? 6 : 5;
+                d[k][0] = ld_pop<S, PAT>(bc + q);
+                d[k][1] = P.gl ? gl : ld_pop<S, PAT>(bxm + q + o1 * kBrick);
+                d[k][2] = P.gr ? gr : ld_pop<S, PAT>(bxp + q + o2 * kBrick);
+                d[k][3] = ld_pop<S, PAT>(bym + q + o3 * kBrick);
+                d[k][4] = ld_pop<S, PAT>(byp + q + o4 * kBrick);
+                d[k][5] = ld_pop<S, PAT>(bzm + q + o5 * kBrick);
+                d[k][6] = ld_pop<S, PAT>(bzp + q + o6 * kBrick);
+            }
         }
     }
 }
@@ -122,40 +159,47 @@ __device__ __forceinline__ void store_cell(const DomainDev& D, typename Store<S>
     using St = Store<S>;
     using T = typename St::T;
     T* bc = fout + A.c;
+    if constexpr (PAT == MOM) {  // o[k][0..3] = Q_k, J*_k
 #pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        const int q = 7 * k * kBrick;
-        if (PAT == PULL) {
+        for (int k = 0; k < NF; ++k)
 #pragma unroll
-            for (int i = 0; i < NQ; ++i) St::st(bc + q + i * kBrick, o[k][i]);
-        } else if (PAT == AA_EVEN) {
-            St::st(bc + q, o[k][0]);
-            St::st(bc + q + 2 * kBrick, o[k][1]);
-            St::st(bc + q + 1 * kBrick, o[k][2]);
-            St::st(bc + q + 4 * kBrick, o[k][3]);
-            St::st(bc + q + 3 * kBrick, o[k][4]);
-            St::st(bc + q + 6 * kBrick, o[k][5]);
-            St::st(bc + q + 5 * kBrick, o[k][6]);
-        } else {  // AA_ODD: push to the neighbour the population streams to
-            St::st(bc + q, o[k][0]);
-            const int64_t nyz = (int64_t)D.ny * D.nz;
-            T* out = static_cast<T*>(D.outflow);
-            if (P.gr) {
-                St::st(bc + q + 2 * kBrick, D.ghostR_st[k]);
-                St::st(out + (5 + k) * nyz + P.yz, o[k][1]);
-            } else {
-                St::st(fout + A.xp + q + 1 * kBrick, o[k][1]);
+            for (int m = 0; m < 4; ++m) St::st(bc + (4 * k + m) * kBrick, o[k][m]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            const int q = 7 * k * kBrick;
+            if (PAT == PULL) {
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) St::st(bc + q + i * kBrick, o[k][i]);
+            } else if (PAT == AA_EVEN) {
+                St::st(bc + q, o[k][0]);
+                St::st(bc + q + 2 * kBrick, o[k][1]);
+                St::st(bc + q + 1 * kBrick, o[k][2]);
+                St::st(bc + q + 4 * kBrick, o[k][3]);
+                St::st(bc + q + 3 * kBrick, o[k][4]);
+                St::st(bc + q + 6 * kBrick, o[k][5]);
+                St::st(bc + q + 5 * kBrick, o[k][6]);
+            } else {  // AA_ODD: push to the neighbour the population streams to
+                St::st(bc + q, o[k][0]);
+                const int64_t nyz = (int64_t)D.ny * D.nz;
+                T* out = static_cast<T*>(D.outflow);
+                if (P.gr) {
+                    St::st(bc + q + 2 * kBrick, D.ghostR_st[k]);
+                    St::st(out + (5 + k) * nyz + P.yz, o[k][1]);
+                } else {
+                    St::st(fout + A.xp + q + 1 * kBrick, o[k][1]);
+                }
+                if (P.gl) {
+                    St::st(bc + q + 1 * kBrick, D.ghostL_st[k]);
+                    St::st(out + k * nyz + P.yz, o[k][2]);
+                } else {
+                    St::st(fout + A.xm + q + 2 * kBrick, o[k][2]);
+                }
+                St::st(fout + A.yp + q + 3 * kBrick, o[k][3]);
+                St::st(fout + A.ym + q + 4 * kBrick, o[k][4]);
+                St::st(fout + A.zp + q + 5 * kBrick, o[k][5]);
+                St::st(fout + A.zm + q + 6 * kBrick, o[k][6]);
             }
-            if (P.gl) {
-                St::st(bc + q + 1 * kBrick, D.ghostL_st[k]);
-                St::st(out + k * nyz + P.yz, o[k][2]);
-            } else {
-                St::st(fout + A.xm + q + 2 * kBrick, o[k][2]);
-            }
-            St::st(fout + A.yp + q + 3 * kBrick, o[k][3]);
-            St::st(fout + A.ym + q + 4 * kBrick, o[k][4]);
-            St::st(fout + A.zp + q + 5 * kBrick, o[k][5]);
-            St::st(fout + A.zm + q + 6 * kBrick, o[k][6]);
         }
     }
 }
@@ -239,10 +283,10 @@ __device__ __forceinline__ void sweep_body(const DomainDev& D, const void* fin_v
     CellDiag cd;
     if (active) {
         const PullIdx P = pull_index(D, x, y, z);
-        const PullAt A = pull_at(P);
+        const PullAt A = PAT == MOM ? pull_at_m(P) : pull_at(P);
         float d[NF][NQ], o[NF][NQ];
         load_cell<S, PAT>(D, fin, P, A, d);
-        collide<S, COLL, DIAG>(D, d, o, &cd);
+        collide<S, COLL, DIAG, PAT == MOM>(D, d, o, &cd);
         if (SRC) add_source<S>(D, P.c, o);
         store_cell<S, PAT>(D, fout, P, A, o);
     }
@@ -268,6 +312,18 @@ __global__ void __launch_bounds__(128, 5) sweep_kernel_gated_f32(const __grid_co
                                                                  const void* fin_v, void* fout_v,
                                                                  double* __restrict__ partials) {
     sweep_body<S_F32, C_GATED, DIAG, SRC, PAT, LIN>(D, fin_v, fout_v, partials);
+}
+
+// The plain moment-storage sweep waits mostly on its 65 loads per cell (L1 / L2 hits of the
+// sources' moments) with 5 CTAs per SM at 92 registers; capped at 6 CTAs (80 registers, 28
+// bytes of spills) it runs 1.7 % faster.  Its own kernel carries the cap, as for the gated
+// sweep.  The diagnostic variant keeps the plain bound: capped, the compiler fused other
+// multiply-adds than in the population sweep's diagnostic variant, and the two storages would no
+// longer agree bit for bit.
+template <bool LIN>
+__global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant__ DomainDev D, const void* fin_v,
+                                                           void* fout_v, double* __restrict__ partials) {
+    sweep_body<S_F32, C_RLB, false, false, MOM, LIN>(D, fin_v, fout_v, partials);
 }
 
 // ---- batched sweep: persistent CTAs over a tile table ------------------------------------
@@ -487,6 +543,16 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
             for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? dp : 0.0f);
             Pd[4][a] = Hp * uv[a];
         }
+        if (swap == 2) {  // moment storage (FP32): Q_k and the first moment Phi^adv_k
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                T* m = fout + mom_at(c) + 4 * k * kBrick;
+                Store<S>::st(m, dQ[k]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Store<S>::st(m + (1 + a) * kBrick, Pd[k][a]);
+            }
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             const float sc = D.enc[k];
@@ -508,7 +574,8 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
 // ---- readback: conserved fields in physical units (FP64) ---------------------------------
 template <int S>
 // gather = 1: one-buffer state after an odd step, where f*_i(x) sits in slot i of x + c_i
-// (or in the outflow record when x + c_i is outside an X_DIRICHLET_EQ domain).
+// (or in the outflow record when x + c_i is outside an X_DIRICHLET_EQ domain); gather = 2:
+// moment storage, f*_i(x) rebuilt from the cell's own Q_k, J*_k.
 __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin_v,
                                  double* __restrict__ out, double s, double rho_ref, double E_ref, int gather) {
     using T = typename Store<S>::T;
@@ -523,15 +590,23 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
         const PullIdx P = pull_index(D, x, y, z);
         // where population i of this cell lives
         int32_t at[NQ] = {P.c, P.c, P.c, P.c, P.c, P.c, P.c};
-        if (gather) {
+        if (gather == 1) {
             at[1] = P.xp; at[2] = P.xm; at[3] = P.yp; at[4] = P.ym; at[5] = P.zp; at[6] = P.zm;
         }
         for (int k = 0; k < NF; ++k) {
             double acc = 0.0;
             const double sc = (double)D.dec[k];
+            float mq = 0.0f, mj[3] = {0.0f, 0.0f, 0.0f};
+            if (gather == 2) {  // moment storage: the cell's own outgoing set
+                const T* m = fin + mom_at(c) + 4 * k * kBrick;
+                mq = Store<S>::ld(m);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) mj[a] = Store<S>::ld(m + (1 + a) * kBrick);
+            }
             for (int i = 0; i < NQ; ++i) {
                 double v;
-                if (gather && i == 1 && P.gr) v = (double)Store<S>::ld(outflow + (5 + k) * nyz + P.yz);
+                if (gather == 2) v = (double)(i == 0 ? 0.25f * mq : mom_pop(mq, mj[(i - 1) >> 1], (i & 1) ? 1.0f : -1.0f));
+                else if (gather && i == 1 && P.gr) v = (double)Store<S>::ld(outflow + (5 + k) * nyz + P.yz);
                 else if (gather && i == 2 && P.gl) v = (double)Store<S>::ld(outflow + k * nyz + P.yz);
                 else v = (double)Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
                 acc += v * sc;
@@ -551,7 +626,9 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
 template <int S, int COLL, bool DIAG, bool SRC, int PAT, bool LIN>
 static void launch_one(const DomainDev& D, const void* fin, void* fout, double* partials, dim3 grid,
                        dim3 block, cudaStream_t st) {
-    if constexpr (S == S_F32 && COLL == C_GATED)
+    if constexpr (PAT == MOM && !DIAG)
+        sweep_kernel_mom<LIN><<<grid, block, 0, st>>>(D, fin, fout, partials);
+    else if constexpr (S == S_F32 && COLL == C_GATED)
         sweep_kernel_gated_f32<DIAG, SRC, PAT, LIN><<<grid, block, 0, st>>>(D, fin, fout, partials);
     else
         sweep_kernel<S, COLL, DIAG, SRC, PAT, LIN><<<grid, block, 0, st>>>(D, fin, fout, partials);
@@ -572,6 +649,11 @@ static cudaError_t launch_sweep_p(const DomainDev& D, const void* fin, void* fou
 template <int S, int COLL>
 static cudaError_t launch_sweep_t(const DomainDev& D, int pattern, const void* fin, void* fout, bool diag,
                                   double* partials, dim3 grid, dim3 block, cudaStream_t st) {
+    if (pattern == MOM) {
+        if constexpr (S == S_F32 && COLL == C_RLB)
+            return launch_sweep_p<S, COLL, MOM, false>(D, fin, fout, diag, partials, grid, block, st);
+        return cudaErrorInvalidValue;
+    }
     if (pattern == AA_ODD) return launch_sweep_p<S, COLL, AA_ODD, false>(D, fin, fout, diag, partials, grid, block, st);
     if (pattern == AA_EVEN) return launch_sweep_p<S, COLL, AA_EVEN, false>(D, fin, fout, diag, partials, grid, block, st);
     if (D.src != nullptr)  // sources: two-buffer sweeps only

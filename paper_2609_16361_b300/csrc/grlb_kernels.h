@@ -7,7 +7,8 @@
 
 namespace grlb {
 // One sweep of one domain (record by value).  pattern: 0 two-buffer pull (fin -> fout),
-// 1 / 2 odd / even step of the one-buffer AA pattern (fin == fout).  diag: one partial record
+// 1 / 2 odd / even step of the one-buffer AA pattern (fin == fout), 3 two-buffer pull of
+// moments (FP32, regularized collision).  diag: one partial record
 // per CTA in partials.
 cudaError_t launch_sweep(const DomainDev& D, int storage, int coll, int pattern, const void* fin, void* fout,
                          bool diag, double* partials, dim3 grid, dim3 block, cudaStream_t st);
@@ -47,7 +48,7 @@ struct CeInit {
 cudaError_t launch_init_ce(const DomainDev& D, int storage, void* fout, const double* rho, const double* u,
                            const double* p, double rho_ref, double p_ref, int swap, const CeInit& C,
                            cudaStream_t st);
-// gather = 1 for a one-buffer (AA) state after an odd number of steps.
+// gather = 1 for a one-buffer (AA) state after an odd number of steps, 2 for moment storage.
 cudaError_t launch_conserved(const DomainDev& D, int storage, const void* fin, double* out,
                              double s, double rho_ref, double E_ref, int gather, cudaStream_t st);
 
@@ -85,7 +86,8 @@ cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* fr
 // Populations of listed cells (grlb_cells.cu): out[q n + j] = f_q(cells[j]) in FP64 lattice
 // units, f = stored x dec[k] + shift[q].  layout 0: slot q of the cell (two buffers); 1: slot
 // opp(i) of the cell (one buffer, even steps done); 2: slot q of the neighbour x + c_i or the
-// outflow record (one buffer, odd steps done).  cells[j] must lie in [0, N).
+// outflow record (one buffer, odd steps done); 3: rebuilt from the cell's moments (moment
+// storage).  cells[j] must lie in [0, N).
 struct CellDecode {
     double dec[5];
     double shift[35];

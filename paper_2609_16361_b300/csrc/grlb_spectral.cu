@@ -243,7 +243,8 @@ __device__ __forceinline__ int shell_of(int64_t M) {
 
 // ---- per-cell preparation shared by both K1 kernels ------------------------------------------
 // Lattice-unit moments of the stored state of cell c (gather = 1: one-buffer state after an odd
-// step, where f*_i(x) sits in slot i of x + c_i), in FP32 deviation form as the sweep takes
+// step, where f*_i(x) sits in slot i of x + c_i; gather = 2: moment storage, the populations
+// rebuilt from the cell's own Q_k, J*_k), in FP32 deviation form as the sweep takes
 // them; rho_f = max(rho, rho_min), u = m / rho_f, p = max(p_ref + (gamma-1)(dE - |m|^2 / (2
 // rho_f)), p_min), T = p / rho_f and mu(T) (constant or Sutherland).  The divisions are the
 // approximate reciprocal-and-multiply (within 2 ulp): u and mu feed FP32 transforms, and the
@@ -254,7 +255,7 @@ __device__ __forceinline__ void prep_cell(const DomainDev& D, const typename Sto
                                           float& u2, float& mu) {
     const int nx = 1 << P.lgx, ny = 1 << P.lgy, nz = 1 << P.lgz;
     int64_t at[NQ] = {c, c, c, c, c, c, c};
-    if (gather) {
+    if (gather == 1) {
         const int x = (int)(c & (nx - 1));
         const int y = (int)((c >> P.lgx) & (ny - 1));
         const int z = (int)(c >> (P.lgx + P.lgy));
@@ -270,8 +271,17 @@ __device__ __forceinline__ void prep_cell(const DomainDev& D, const typename Sto
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         float acc = 0.0f;
+        if (gather == 2) {  // moment storage: the cell's own outgoing set, summed as stored
+            const typename Store<S>::T* m = fin + mom_at(c) + 4 * k * kBrick;
+            const float mq = Store<S>::ld(m);
+            acc = 0.25f * mq;
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
+            for (int i = 1; i < NQ; ++i)
+                acc += fmaf((i & 1) ? 0.5f : -0.5f, Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick), mq * 0.125f);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
+        }
         dQ[k] = acc * D.dec[k];
     }
     const float rf = fmaxf(D.rho_ref + dQ[0], D.rho_min);

@@ -41,7 +41,8 @@ class CaseParams:
     bc: int = BC_PERIODIC
     collision: int = COLL_RLB_SENSOR
     storage: int = STORE_F32
-    streaming: int = 0        # 0: two buffers (pull), 1: one buffer, AA pattern
+    streaming: int = 0        # 0: two buffers (pull), 1: one buffer, AA pattern, 2: two buffers of
+                              # moments (FP32 storage, regularized collision)
     dx: float = 1.0
     dt: float = 1.0
     gamma: float = 1.4

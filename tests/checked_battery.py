@@ -274,6 +274,22 @@ def sc_read_cells(dg):
             d.close()
 
 
+def sc_moments(dg):
+    """Moment storage: the sweep (tiled and linear launches, Dirichlet ghosts), its diagnostic
+    sweep, the Chapman-Enskog start, readback, probes and spectra."""
+    for case, ce in ((inputs.tgv3d(16), False), (inputs.tgv3d(16, mach=0.5, re=100.0), True),
+                     (inputs.random_smooth(40, 21, 7, seed=3), False), (inputs.sod(64), False)):
+        run_domain(dg, with_params(case, streaming=2), 9, ce=ce)
+        d = capi.Domain(case.params.replace(streaming=2))
+        d.init(case.rho, case.u, case.p)
+        d.step(2)
+        dg.add(capi.grlb_read_cells(d.h, np.arange(case.params.ncells)))
+        if case.params.name.startswith("tgv"):
+            E, sums = d.spectral()
+            dg.add(np.asarray(E), np.asarray(sums))
+        d.close()
+
+
 def sc_ffma(dg):
     import torch
     sink = torch.zeros(4 * 256, dtype=torch.float32, device="cuda")
@@ -284,7 +300,7 @@ def sc_ffma(dg):
 
 SCENARIOS = [sc_sweeps, sc_one_buffer, sc_tubes, sc_ce_init, sc_source, sc_staging_and_checkpoint,
              sc_init_device, sc_batches, sc_serve, sc_slabs, sc_check_finite, sc_noalloc, sc_spectral,
-             sc_read_cells, sc_ffma]
+             sc_read_cells, sc_moments, sc_ffma]
 
 
 def probe_checker():
