@@ -521,7 +521,8 @@ def batched_leg(args, steps=200):
     st = stream.cuda_stream
     cases = inputs.batched_mix(0)
     cells = sum(c.params.ncells for c in cases)
-    doms = [capi.Domain(c.params, stream=st) for c in cases]
+    moments = args.state != "populations"  # every domain of the mix is FP32, regularized
+    doms = [capi.Domain(c.params.replace(streaming=2 if moments else 0), stream=st) for c in cases]
     for d, c in zip(doms, cases):
         d.init(c.rho, c.u, c.p)
     b = capi.grlb_batch_create([d.h for d in doms], use_graph=1)
@@ -553,7 +554,8 @@ def batched_leg(args, steps=200):
     return {"metric": "batched MLUP/s", "value": mb, "unit": "MLUP/s",
             "sequential_plain_mlups": mp, "vs_sequential_plain": mb / mp,
             "workload": "64 uneven domains (48 Becker 128-2048 x 4 x 4, 16 Taylor-Green 32^3-96^3 "
-                        "Re 100), seed 0", "cells": cells, "steps": steps}
+                        "Re 100), seed 0", "cells": cells, "steps": steps,
+            "state": "moments" if moments else "populations"}
 
 
 def served_leg(args, n_requests=40, rate=20.0):
@@ -562,9 +564,10 @@ def served_leg(args, n_requests=40, rate=20.0):
     in, first out, one domain at a time through grlb_step."""
     from paper_2609_16361_b300 import inputs, serve
     trace = inputs.serving_trace(0, n_requests=n_requests, rate=rate)
-    res = serve.Server(hbm_budget=150e9, chunk=200).run(trace, realtime=True)
+    moments = args.state != "populations"  # FP32 requests as moments, FP16 ones as populations
+    res = serve.Server(hbm_budget=150e9, chunk=200, moments=moments).run(trace, realtime=True)
     sb = serve.summarize(res)
-    sp = serve.summarize(serve.serial_plain(trace, realtime=True))
+    sp = serve.summarize(serve.serial_plain(trace, realtime=True, moments=moments))
     keep = ("solves_per_s", "p50_latency_s", "p99_latency_s", "mean_latency_s", "mlups", "failed")
     return {"metric": "served solves/s", "value": sb["solves_per_s"], "unit": "solves/s",
             **{k: sb[k] for k in keep if k != "solves_per_s"},
@@ -572,7 +575,8 @@ def served_leg(args, n_requests=40, rate=20.0):
             "vs_serial_plain": sb["solves_per_s"] / sp["solves_per_s"],
             "p99_vs_serial_plain": sb["p99_latency_s"] / sp["p99_latency_s"],
             "workload": f"Poisson {rate:g}/s, {n_requests} requests (Sod / Becker tubes, Taylor-Green "
-                        "64^3-192^3 Re 100, FP32 or FP16, 500-5000 steps), seed 0, 150 GB budget"}
+                        "64^3-192^3 Re 100, FP32 or FP16, 500-5000 steps), seed 0, 150 GB budget",
+            "state": "FP32 requests as moments" if moments else "populations"}
 
 
 # ----------------------------------------------------------------------------------------
@@ -1254,9 +1258,10 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--state", default="auto", choices=["auto", "populations", "moments"],
-                    help="tgv: keep the state as 35 populations or as the 20 moments of the "
-                         "regularized outgoing set (FP32, --collision rlb; bitwise the same "
-                         "results); auto: moments where they apply")
+                    help="tgv (and the batched / served legs of its line): keep the state as 35 "
+                         "populations or as the 20 moments of the regularized outgoing set (FP32, "
+                         "--collision rlb; bitwise the same results); auto: moments where they "
+                         "apply")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parallelism", default="replicas", choices=["replicas", "zslab"],
                     help="N > 1: independent replica domains, or one domain split along z over the ranks")

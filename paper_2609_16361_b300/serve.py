@@ -15,6 +15,9 @@ released, which may admit waiting requests.
 
 With one_buffer_large, large requests keep one population buffer (AA pattern: half their
 memory, the same traffic and collisions); small ones stay two-buffer for the batched kernel.
+With moments, FP32 requests of the regularized collision keep their state as the 20 moments of
+each cell's outgoing set (160 instead of 280 bytes per cell update, bitwise the same run); they
+advance by their own sweeps in every schedule.
 
 A domain's result does not depend on which other domains share its launches, so every
 request's result is bitwise the same alone and in the mix.
@@ -37,6 +40,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import autotune, capi
+from . import inputs as _inputs
 
 
 @dataclass
@@ -73,7 +77,7 @@ class Server:
     def __init__(self, hbm_budget: float = 150e9, max_resident: int = 512, chunk: int = 200,
                  use_graph: bool = True, tile_table: dict | None = None, stream=None,
                  keep_fields: bool = False, large_cells: int = 262144, srpt: bool = True,
-                 one_buffer_large: bool = False, check_finite: bool = True):
+                 one_buffer_large: bool = False, check_finite: bool = True, moments: bool = False):
         import torch
         self.budget = float(hbm_budget)
         self.max_resident = max_resident
@@ -91,6 +95,7 @@ class Server:
         # traffic; small ones run in the batched kernel, which needs two buffers
         self.one_buffer_large = one_buffer_large
         self.check_finite = check_finite  # scan every advanced request after each chunk
+        self.moments = moments  # FP32 regularized requests keep their state as moments
         self.evicted = 0
 
     def run(self, trace, realtime: bool = True, lookahead: int = 12):
@@ -191,7 +196,7 @@ class Server:
                 # admission: FIFO while the head fits in the budget and a slot is free
                 while waiting and len(resident) < self.max_resident:
                     r = waiting[0]
-                    prm = request_params(r, self.large_cells, self.one_buffer_large)
+                    prm = request_params(r, self.large_cells, self.one_buffer_large, self.moments)
                     need = capi.grlb_bytes_for(prm)
                     if need == 0:
                         raise capi.GrlbError(-1, f"request {r.rid}: invalid parameters")
@@ -281,15 +286,20 @@ class Server:
         return [results[r.rid] for r in sorted(trace, key=lambda r: r.rid)]
 
 
-def request_params(r, large_cells: int, one_buffer_large: bool):
-    """Domain parameters of a request: one population buffer for large requests if asked."""
-    if one_buffer_large and r.case.params.ncells >= large_cells:
-        return r.case.params.replace(streaming=1)
-    return r.case.params
+def request_params(r, large_cells: int, one_buffer_large: bool, moments: bool = False):
+    """Domain parameters of a request: with `moments`, FP32 requests of the regularized
+    collision keep their state as moments (streaming 2: 20 values per cell, bitwise the same
+    run); otherwise one population buffer for large requests if asked."""
+    prm = r.case.params
+    if moments and prm.storage == _inputs.STORE_F32 and prm.collision == _inputs.COLL_RLB_SENSOR:
+        return prm.replace(streaming=2)
+    if one_buffer_large and prm.ncells >= large_cells:
+        return prm.replace(streaming=1)
+    return prm
 
 
 def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = False,
-                 one_buffer_large: bool = False, large_cells: int = 262144):
+                 one_buffer_large: bool = False, large_cells: int = 262144, moments: bool = False):
     """Baseline: first-in first-out, one domain at a time through grlb_step on `stream` (no
     batching; grlb_step replays a small domain's sweeps from a CUDA graph of 8 launches); the
     same buffer choice per request as the server's."""
@@ -305,7 +315,7 @@ def serial_plain(trace, realtime: bool = True, stream=None, keep_fields: bool = 
                 time.sleep(wait)
         res = Result(r.rid, r.kind, r.steps, r.case.params.ncells, r.arrival if realtime else 0.0,
                      admitted=time.perf_counter() - t0)
-        dom = capi.Domain(request_params(r, large_cells, one_buffer_large), stream=st)
+        dom = capi.Domain(request_params(r, large_cells, one_buffer_large, moments), stream=st)
         dom.init(r.case.rho, r.case.u, r.case.p)
         dom.step(r.steps)
         _finish(res, dom, t0, keep_fields)

@@ -95,3 +95,17 @@ def test_served_results_match_the_oracle():
         R = run_oracle(r.case, r.steps).conserved()
         ok, err = oracle_gate(r.case, x.fields, R)
         assert ok, (r.rid, r.kind, r.storage, err)
+
+
+def test_served_moment_requests_equal_their_population_runs():
+    """With moments, the FP32 requests keep their state as moments: every result bitwise the
+    population server's (and the serial baseline's in the same state)."""
+    trace = small_trace(n=8, seed=5)
+    assert any(r.storage == inputs.STORE_F32 for r in trace)
+    a = serve.Server(chunk=16, keep_fields=True).run(trace, realtime=False)
+    b = serve.Server(chunk=16, keep_fields=True, moments=True).run(trace, realtime=False)
+    c = serve.serial_plain(trace, realtime=False, keep_fields=True, moments=True)
+    for r, x, y, z in zip(trace, a, b, c):
+        assert x.status == y.status == "ok"
+        assert x.digest == y.digest, (r.rid, r.kind, r.storage)
+        assert np.all(rel_linf(z.fields, y.fields) <= (1e-6 if r.storage == inputs.STORE_F32 else 1e-2))
