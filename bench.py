@@ -441,7 +441,11 @@ def run_zslab(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
-    part = decomp.slab_case(inputs.tgv3d(n), 0, n)   # this rank's period, ghost planes wrapped
+    moments = args.state != "populations"
+    whole = inputs.tgv3d(n)
+    if moments:
+        whole = dataclasses.replace(whole, params=whole.params.replace(streaming=2))
+    part = decomp.slab_case(whole, 0, n)   # this rank's period, ghost planes wrapped
     stream = torch.cuda.Stream()
     r = decomp.SlabRank(None, rank, ws, stream=stream, part=part)
     dev = torch.device("cuda", local)
@@ -483,7 +487,8 @@ def run_zslab(args):
                            "parallelism": f"zslab{ws}", "sweeps_per_step": SWEEPS_PER_STEP,
                            "step": "init kernel + 50 x (ghost pack, NCCL send/recv to both z "
                                    "neighbours, unpack, sweep)",
-                           "halo_bytes_per_sweep_per_rank": 2 * 5 * n * n * 4,
+                           "halo_bytes_per_sweep_per_rank": 2 * (10 if moments else 5) * n * n * 4,
+                           "state": "moments" if moments else "populations",
                            "l2": "inputs larger than L2, no flush"},
                 "gpu_launches": args.steps * (1 + 3 * SWEEPS_PER_STEP),
                 "clocks": clk.summary(), "finite_after_run": finite}

@@ -355,8 +355,11 @@ grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init);
  * pulls.  The interior cells then evolve bitwise as in the undivided domain (same kernel, same
  * inputs); ghost-plane cells carry no meaning and enter the slab's own diagnostics, so interior
  * totals are taken from the readback.  Enqueued on the slabs' common stream.
- * Errors: GRLB_EINVAL for NULL domains, slabs that differ in nx, ny or storage, one-buffer
- * streaming, non-periodic slabs, nz < 3, or different streams; GRLB_ECUDA on launch failure. */
+ * Moment storage (streaming 2) exchanges Q_k and J*_k,z of the same planes (what a pull from a
+ * ghost plane reads of it); both slabs must keep the same kind of state.
+ * Errors: GRLB_EINVAL for NULL domains, slabs that differ in nx, ny, storage or streaming,
+ * one-buffer streaming, non-periodic slabs, nz < 3, or different streams; GRLB_ECUDA on launch
+ * failure. */
 grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upper);
 
 /* The same exchange between slabs on different devices (one slab per rank of a multi-device
@@ -369,7 +372,10 @@ grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upper);
  *  grlb_halo_unpack_z: ghost plane z = 0 (+z populations) <- from_lower (the lower neighbour's
  *                      to_upper), ghost plane z = nz - 1 (-z populations) <- from_upper.
  * All buffers are device memory of the domain's device, 5 nx ny elements each, owned by the
- * caller; both calls only enqueue on the domain's stream.  A slab that is its own neighbour (one
+ * caller; both calls only enqueue on the domain's stream.  Moment storage (streaming 2): a pull
+ * from a ghost plane reads Q_k and J*_k,z of the ghost cell, so the slices hold those: 10 nx ny
+ * FP32 values per buffer, slice 2 k + h = Q_k (h = 0) or J*_k,z (h = 1) of field k;
+ * grlb_halo_exchange_z copies the same rows (both slabs must store moments).  A slab that is its own neighbour (one
  * rank, periodic) unpacks its own packed slices: the slab then evolves as the periodic domain.
  * Errors: GRLB_EINVAL for NULL arguments, one-buffer streaming, a non-periodic domain or
  * nz < 3; GRLB_ECUDA on launch failure. */

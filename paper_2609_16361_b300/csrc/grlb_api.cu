@@ -1494,20 +1494,29 @@ extern "C" grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upp
     const grlb_params& b = upper->P;
     if (a.nx != b.nx || a.ny != b.ny || a.storage != b.storage)
         return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs differ in nx, ny or storage");
-    if (a.streaming || b.streaming) return fail(GRLB_EINVAL, "grlb_halo_exchange_z: two-buffer streaming only");
+    if (one_buffer(a) || a.streaming != b.streaming)
+        return fail(GRLB_EINVAL, "grlb_halo_exchange_z: two-buffer slabs of one kind (populations or moments)");
     if (a.bc != GRLB_BC_PERIODIC || b.bc != GRLB_BC_PERIODIC)
         return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs are periodic domains");
     if (a.nz < 3 || b.nz < 3) return fail(GRLB_EINVAL, "grlb_halo_exchange_z: a slab needs nz >= 3 (2 ghost planes)");
     if (lower->stream != upper->stream)
         return fail(GRLB_EINVAL, "grlb_halo_exchange_z: slabs must share one stream");
-    GRLB_CU(grlb::launch_halo_z(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], a.nz, (int64_t)a.nx * a.ny,
-                                elem_bytes(a.storage), lower->stream));
+    if (moment_storage(a))
+        GRLB_CU(grlb::launch_halo_z_mom(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], a.nz,
+                                        (int64_t)a.nx * a.ny, lower->stream));
+    else
+        GRLB_CU(grlb::launch_halo_z(lower->D.buf[lower->D.cur], upper->D.buf[upper->D.cur], a.nz,
+                                    (int64_t)a.nx * a.ny, elem_bytes(a.storage), lower->stream));
     return GRLB_OK;
 }
 
+// values per cell of one exchanged slab face: the population along z of each field, or Q_k and
+// J*_k,z of each field (moment storage)
+static int halo_slices(const grlb_params& p) { return moment_storage(p) ? 10 : 5; }
+
 static grlb_status check_slab(const grlb_domain* d, const char* who) {
     const grlb_params& a = d->P;
-    if (a.streaming) return fail(GRLB_EINVAL, std::string(who) + ": two-buffer streaming only");
+    if (one_buffer(a)) return fail(GRLB_EINVAL, std::string(who) + ": two-buffer streaming only");
     if (a.bc != GRLB_BC_PERIODIC) return fail(GRLB_EINVAL, std::string(who) + ": slabs are periodic domains");
     if (a.nz < 3) return fail(GRLB_EINVAL, std::string(who) + ": a slab needs nz >= 3 (2 ghost planes)");
     return GRLB_OK;
@@ -1518,10 +1527,14 @@ extern "C" grlb_status grlb_halo_pack_z(grlb_domain* d, void* to_upper, void* to
     grlb_status st = check_slab(d, "grlb_halo_pack_z");
     if (st != GRLB_OK) return st;
     const grlb_params& a = d->P;
-    const size_t slice = 5 * (size_t)a.nx * a.ny * elem_bytes(a.storage);
+    const size_t slice = halo_slices(a) * (size_t)a.nx * a.ny * elem_bytes(a.storage);
     grlb::Lent lu(to_upper, slice, d->stream), ll(to_lower, slice, d->stream);
-    GRLB_CU(grlb::launch_halo_pack_z(d->D.buf[d->D.cur], to_upper, to_lower, a.nz, (int64_t)a.nx * a.ny,
-                                     elem_bytes(a.storage), d->stream));
+    if (moment_storage(a))
+        GRLB_CU(grlb::launch_halo_pack_z_mom(d->D.buf[d->D.cur], to_upper, to_lower, a.nz, (int64_t)a.nx * a.ny,
+                                             d->stream));
+    else
+        GRLB_CU(grlb::launch_halo_pack_z(d->D.buf[d->D.cur], to_upper, to_lower, a.nz, (int64_t)a.nx * a.ny,
+                                         elem_bytes(a.storage), d->stream));
     return GRLB_OK;
 }
 
@@ -1530,10 +1543,14 @@ extern "C" grlb_status grlb_halo_unpack_z(grlb_domain* d, const void* from_lower
     grlb_status st = check_slab(d, "grlb_halo_unpack_z");
     if (st != GRLB_OK) return st;
     const grlb_params& a = d->P;
-    const size_t slice = 5 * (size_t)a.nx * a.ny * elem_bytes(a.storage);
+    const size_t slice = halo_slices(a) * (size_t)a.nx * a.ny * elem_bytes(a.storage);
     grlb::Lent ll(from_lower, slice, d->stream), lu(from_upper, slice, d->stream);
-    GRLB_CU(grlb::launch_halo_unpack_z(d->D.buf[d->D.cur], from_lower, from_upper, a.nz, (int64_t)a.nx * a.ny,
-                                       elem_bytes(a.storage), d->stream));
+    if (moment_storage(a))
+        GRLB_CU(grlb::launch_halo_unpack_z_mom(d->D.buf[d->D.cur], from_lower, from_upper, a.nz,
+                                               (int64_t)a.nx * a.ny, d->stream));
+    else
+        GRLB_CU(grlb::launch_halo_unpack_z(d->D.buf[d->D.cur], from_lower, from_upper, a.nz, (int64_t)a.nx * a.ny,
+                                           elem_bytes(a.storage), d->stream));
     return GRLB_OK;
 }
 

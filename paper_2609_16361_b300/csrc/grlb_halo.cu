@@ -99,4 +99,67 @@ cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* fr
     return cudaGetLastError();
 }
 
+// ---- moment storage ------------------------------------------------------------------------
+// A pull from a ghost plane reads Q_k and J*_k,z of the ghost cell (the +z population from plane
+// 0, the -z one from plane nz - 1), so the exchange carries those two of the four moment rows
+// per field: slice 2 k + h holds row 4 k (h = 0, Q_k) or 4 k + 3 (h = 1, J*_k,z), 10 slices of
+// nx ny values per direction.
+__device__ __forceinline__ int mom_halo_row(int slice) { return 4 * (slice >> 1) + ((slice & 1) ? 3 : 0); }
+
+__global__ void __launch_bounds__(256) halo_z_mom_kernel(float* __restrict__ lower, float* __restrict__ upper,
+                                                         int nzl, int64_t nxy) {
+    const int s = blockIdx.y % 10, row = mom_halo_row(s);
+    const bool up = blockIdx.y < 10;  // lower top interior -> upper ghost plane 0
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
+        if (up) GRLB_ST(upper + mom_at(c) + row * kBrick, GRLB_LD(lower + mom_at((int64_t)(nzl - 2) * nxy + c) + row * kBrick));
+        else GRLB_ST(lower + mom_at((int64_t)(nzl - 1) * nxy + c) + row * kBrick, GRLB_LD(upper + mom_at(nxy + c) + row * kBrick));
+    }
+}
+
+__global__ void __launch_bounds__(256) halo_pack_mom_kernel(const float* __restrict__ f, float* __restrict__ to_upper,
+                                                            float* __restrict__ to_lower, int nz, int64_t nxy) {
+    const int s = blockIdx.y % 10, row = mom_halo_row(s);
+    const bool up = blockIdx.y < 10;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
+        if (up) GRLB_ST(to_upper + s * nxy + c, GRLB_LD(f + mom_at((int64_t)(nz - 2) * nxy + c) + row * kBrick));
+        else GRLB_ST(to_lower + s * nxy + c, GRLB_LD(f + mom_at(nxy + c) + row * kBrick));
+    }
+}
+
+__global__ void __launch_bounds__(256) halo_unpack_mom_kernel(float* __restrict__ f, const float* __restrict__ from_lower,
+                                                              const float* __restrict__ from_upper, int nz, int64_t nxy) {
+    const int s = blockIdx.y % 10, row = mom_halo_row(s);
+    const bool low = blockIdx.y < 10;  // from the lower neighbour into ghost plane 0
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nxy; c += (int64_t)gridDim.x * blockDim.x) {
+        if (low) GRLB_ST(f + mom_at(c) + row * kBrick, GRLB_LD(from_lower + s * nxy + c));
+        else GRLB_ST(f + mom_at((int64_t)(nz - 1) * nxy + c) + row * kBrick, GRLB_LD(from_upper + s * nxy + c));
+    }
+}
+
+static dim3 halo_grid(int64_t nxy, int slices) {
+    int64_t blocks = (nxy + 255) / 256;
+    if (blocks > 148 * 4) blocks = 148 * 4;
+    return dim3((unsigned)blocks, slices);
+}
+
+cudaError_t launch_halo_z_mom(void* lower, void* upper, int nzl, int64_t nxy, cudaStream_t st) {
+    halo_z_mom_kernel<<<halo_grid(nxy, 20), 256, 0, st>>>(static_cast<float*>(lower), static_cast<float*>(upper), nzl,
+                                                          nxy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_pack_z_mom(const void* f, void* to_upper, void* to_lower, int nz, int64_t nxy,
+                                   cudaStream_t st) {
+    halo_pack_mom_kernel<<<halo_grid(nxy, 20), 256, 0, st>>>(static_cast<const float*>(f), static_cast<float*>(to_upper),
+                                                             static_cast<float*>(to_lower), nz, nxy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_unpack_z_mom(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
+                                     cudaStream_t st) {
+    halo_unpack_mom_kernel<<<halo_grid(nxy, 20), 256, 0, st>>>(static_cast<float*>(f), static_cast<const float*>(from_lower),
+                                                               static_cast<const float*>(from_upper), nz, nxy);
+    return cudaGetLastError();
+}
+
 }  // namespace grlb

@@ -83,6 +83,13 @@ cudaError_t launch_halo_pack_z(const void* f, void* to_upper, void* to_lower, in
                                cudaStream_t st);
 cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
                                  size_t elem, cudaStream_t st);
+// The same for moment storage: per direction 10 slices of nx ny FP32 values, slice 2 k + h = row
+// 4 k (h = 0: Q_k) or 4 k + 3 (h = 1: J*_k,z) of the moment bricks.
+cudaError_t launch_halo_z_mom(void* lower, void* upper, int nzl, int64_t nxy, cudaStream_t st);
+cudaError_t launch_halo_pack_z_mom(const void* f, void* to_upper, void* to_lower, int nz, int64_t nxy,
+                                   cudaStream_t st);
+cudaError_t launch_halo_unpack_z_mom(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
+                                     cudaStream_t st);
 // Populations of listed cells (grlb_cells.cu): out[q n + j] = f_q(cells[j]) in FP64 lattice
 // units, f = stored x dec[k] + shift[q].  layout 0: slot q of the cell (two buffers); 1: slot
 // opp(i) of the cell (one buffer, even steps done); 2: slot q of the neighbour x + c_i or the

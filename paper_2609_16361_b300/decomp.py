@@ -90,6 +90,18 @@ def exchange_planes(f_lower: np.ndarray, f_upper: np.ndarray, nxy: int):
     put_top_ghost(f_lower, nxy, bottom_slice(f_upper, nxy))
 
 
+def slab_params(prm):
+    """A slab keeps two buffers: of moments when the case stores moments (streaming 2), else
+    of populations."""
+    return prm.replace(streaming=2 if prm.streaming == 2 else 0)
+
+
+def halo_values(prm) -> int:
+    """Values per cell of one exchanged slab face: the population along z of each field, or
+    Q_k and J*_k,z of each field for moment storage."""
+    return 10 if prm.streaming == 2 else 5
+
+
 class SlabSet:
     """A periodic domain as z-slabs on the current CUDA device, stepped with the ghost exchange
     of the C ABI before every step (two-buffer streaming)."""
@@ -102,7 +114,7 @@ class SlabSet:
         if len(self.sizes) < 2 or sum(self.sizes) != case.params.nz:
             raise ValueError("slab sizes must add up to nz, at least two slabs")
         self.parts = [slab_case(case, z0, n) for z0, n in zip(slab_starts(self.sizes), self.sizes)]
-        self.doms = [capi.Domain(p.params.replace(streaming=0), stream=stream) for p in self.parts]
+        self.doms = [capi.Domain(slab_params(p.params), stream=stream) for p in self.parts]
 
     def init(self, ce_init: bool | None = None):
         for d, p in zip(self.doms, self.parts):
@@ -180,10 +192,10 @@ class SlabRank:
             self.z0 = part.meta.get("z0", 0)
         prm = self.part.params
         self.stream = stream or torch.cuda.Stream()
-        self.dom = capi.Domain(self.part.params.replace(streaming=0), stream=self.stream.cuda_stream)
+        self.dom = capi.Domain(slab_params(self.part.params), stream=self.stream.cuda_stream)
         nxy = prm.nx * prm.ny
         dtype = torch.float32 if prm.storage == inputs.STORE_F32 else torch.int16  # raw 16-bit values
-        self.top = torch.empty((5, nxy), dtype=dtype, device="cuda")
+        self.top = torch.empty((halo_values(prm), nxy), dtype=dtype, device="cuda")
         self.bottom = torch.empty_like(self.top)
         self.nx, self.ny = prm.nx, prm.ny
 

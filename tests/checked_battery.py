@@ -214,6 +214,17 @@ def sc_slabs(dg):
     r.step(3)
     dg.add(r.conserved_interior())
     r.close()
+    mc = with_params(inputs.tgv3d(16), streaming=2)   # moment slabs: Q_k, J*_k,z exchanged
+    s = decomp.SlabSet(mc, [7, 9])
+    s.init()
+    s.step(3)
+    dg.add(s.conserved())
+    s.close()
+    r = decomp.SlabRank(mc, 0, 1)
+    r.init()
+    r.step(3)
+    dg.add(r.conserved_interior())
+    r.close()
 
 
 def sc_check_finite(dg):

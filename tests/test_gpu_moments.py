@@ -8,8 +8,8 @@ re-encoding: the moment-storage run must equal the population run bit for bit --
 (through the point probes), conserved fields, diagnostics, spectra, checkpoints -- for periodic
 boxes, ragged linear launches, Dirichlet tubes, the Chapman-Enskog start, batches and the
 staged upload; and it must refuse what it cannot represent (BGK and gated cells keep parts of
-the populations outside the moments; 16-bit storage; sources; the z-slab exchange, which moves
-population slices)."""
+the populations outside the moments; 16-bit storage; sources; the allocation-free sweep).  The
+z-slab exchange of moment slabs is tested in test_gpu_slabs.py."""
 import numpy as np
 import pytest
 
@@ -158,8 +158,6 @@ def test_what_moments_cannot_hold_is_refused():
     S = torch.zeros((5, base.ncells), dtype=torch.float32, device="cuda")
     with pytest.raises(capi.GrlbError):
         capi.grlb_set_source_device(d.h, S.data_ptr())
-    with pytest.raises(capi.GrlbError):
-        capi.grlb_halo_pack_z(d.h, S.data_ptr(), S.data_ptr())
     with pytest.raises(capi.GrlbError):
         capi.grlb_step_diag_noalloc(base, S.data_ptr(), S.data_ptr(), S.data_ptr(), None)
     d.close()

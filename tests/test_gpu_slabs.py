@@ -4,6 +4,8 @@ Chapman-Enskog start; interior totals add up to the whole domain's.  The multi-d
 (grlb_halo_pack_z / grlb_halo_unpack_z around a transfer of device buffers) gives the same:
 one rank whose ring closes on itself (decomp.SlabRank, world 1), and slabs that swap their packed
 slices through device buffers as ranks on different devices would."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -103,3 +105,33 @@ def test_packed_slices_between_slabs_equal_the_undivided_run():
         capi.grlb_halo_pack_z(capi.Domain(inputs.sod(64).params).h, 1, 2)
     for d in doms:
         d.close()
+
+
+def test_moment_slabs_bitwise_equal_the_undivided_moment_run():
+    """Moment storage: the exchange carries Q_k and J*_k,z of the boundary planes (on one device
+    and through packed buffers, one rank closing the ring on itself); the interior is bitwise
+    the undivided moment run, which is bitwise the population run."""
+    c = inputs.tgv3d(32)
+    mc = dataclasses.replace(c, params=c.params.replace(streaming=2))
+    want = whole_run(c, 30)
+    d = capi.Domain(mc.params)
+    d.init(c.rho, c.u, c.p)
+    d.step(30)
+    assert np.array_equal(d.conserved(), want)
+    d.close()
+    s = decomp.SlabSet(mc, [12, 20])
+    s.init()
+    s.step(30)
+    assert np.array_equal(s.conserved(), want)
+    s.close()
+    r = decomp.SlabRank(mc, 0, 1)
+    assert tuple(r.top.shape) == (10, 32 * 32)
+    r.init()
+    r.step(30)
+    assert np.array_equal(r.conserved_interior(), want)
+    r.close()
+    a, b = capi.Domain(c.params), capi.Domain(mc.params.replace(nz=32))
+    with pytest.raises(capi.GrlbError):  # slabs of different kinds
+        capi.grlb_halo_exchange_z(a.h, b.h)
+    a.close()
+    b.close()
