@@ -289,6 +289,7 @@ def sc_moments(dg):
     """Moment storage: the sweep (tiled and linear launches, Dirichlet ghosts), its diagnostic
     sweep, the Chapman-Enskog start, readback, probes and spectra."""
     for case, ce in ((inputs.tgv3d(16), False), (inputs.tgv3d(16, mach=0.5, re=100.0), True),
+                     (inputs.tgv3d(32), False),   # tiled: the column-marching sweep
                      (inputs.random_smooth(40, 21, 7, seed=3), False), (inputs.sod(64), False)):
         run_domain(dg, with_params(case, streaming=2), 9, ce=ce)
         d = capi.Domain(case.params.replace(streaming=2))
