@@ -221,7 +221,8 @@ grlb_status grlb_read_cells(grlb_domain* d, const int64_t* cells, int64_t n, dou
  * requires a buffer written by grlb_save of a domain with the same cells, storage and
  * streaming (the header's last 32-bit field records grlb_params.streaming).  Moment storage
  * (streaming 2) saves its moment buffer: bricks of 128 cells, each holding 20 rows 4 k + m
- * (m = 0: Q_k, 1..3: J*_k,x..z, deviations from the reference state), 128 FP32 values each.
+ * (m = 0: Q_k / 8, the share w_1 Q_k of each moving population; 1..3: J*_k,x..z; deviations
+ * from the reference state), 128 FP32 values each.
  * Otherwise the format is a 32-byte header, then the population buffer as the library keeps it in device
  * memory -- the cell-brick layout: cells in storage order (x fastest) are grouped into
  * ceil(N / 128) bricks of 128 cells; a brick holds its 35 population rows q = 7k + i (field k
@@ -355,7 +356,7 @@ grlb_status grlb_set_init_mode(grlb_domain* d, int32_t ce_init);
  * pulls.  The interior cells then evolve bitwise as in the undivided domain (same kernel, same
  * inputs); ghost-plane cells carry no meaning and enter the slab's own diagnostics, so interior
  * totals are taken from the readback.  Enqueued on the slabs' common stream.
- * Moment storage (streaming 2) exchanges Q_k and J*_k,z of the same planes (what a pull from a
+ * Moment storage (streaming 2) exchanges Q_k / 8 and J*_k,z of the same planes (what a pull from a
  * ghost plane reads of it); both slabs must keep the same kind of state.
  * Errors: GRLB_EINVAL for NULL domains, slabs that differ in nx, ny, storage or streaming,
  * one-buffer streaming, non-periodic slabs, nz < 3, or different streams; GRLB_ECUDA on launch
@@ -373,8 +374,8 @@ grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upper);
  *                      to_upper), ghost plane z = nz - 1 (-z populations) <- from_upper.
  * All buffers are device memory of the domain's device, 5 nx ny elements each, owned by the
  * caller; both calls only enqueue on the domain's stream.  Moment storage (streaming 2): a pull
- * from a ghost plane reads Q_k and J*_k,z of the ghost cell, so the slices hold those: 10 nx ny
- * FP32 values per buffer, slice 2 k + h = Q_k (h = 0) or J*_k,z (h = 1) of field k;
+ * from a ghost plane reads Q_k / 8 and J*_k,z of the ghost cell, so the slices hold those: 10 nx ny
+ * FP32 values per buffer, slice 2 k + h = Q_k / 8 (h = 0) or J*_k,z (h = 1) of field k;
  * grlb_halo_exchange_z copies the same rows (both slabs must store moments).  A slab that is its own neighbour (one
  * rank, periodic) unpacks its own packed slices: the slab then evolves as the periodic domain.
  * Errors: GRLB_EINVAL for NULL arguments, one-buffer streaming, a non-periodic domain or

@@ -7,7 +7,7 @@
 //   one buffer, odd steps done:    slot i of x + c_i (the AA-odd push), or, for the +x / -x
 //                                  populations leaving an X_DIRICHLET_EQ tube, the outflow
 //                                  record [side][k][y + ny z];
-//   moments:                       rebuilt from the cell's own Q_k, J*_k (mom_at layout).
+//   moments:                       rebuilt from the cell's own w_1 Q_k, J*_k (mom_at layout).
 // One thread per (population row, listed cell): out[q n + j] = f_q(cells[j]) in FP64 lattice
 // units, the stored deviation decoded and the reference equilibrium added back.
 #include <cuda_runtime.h>
@@ -37,9 +37,8 @@ __global__ void __launch_bounds__(256) read_cells_kernel(const __grid_constant__
         if (layout == 3) {  // moments: f*_q rebuilt from the cell's own Q_k, J*_k
             const T* m = buf + mom_at(c) + (int64_t)(4 * k) * kBrick;
             const float mq = Store<S>::ld(m);
-            const float v = i == 0 ? 0.25f * mq
-                                   : fmaf(((i & 1) ? 0.5f : -0.5f), Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick),
-                                          mq * 0.125f);
+            const float v = i == 0 ? 2.0f * mq  // mq = w_1 Q_k
+                                   : fmaf(((i & 1) ? 0.5f : -0.5f), Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick), mq);
             GRLB_ST(out + t, (double)v * dec.dec[k] + dec.shift[q]);
             continue;
         }

@@ -55,8 +55,9 @@ __host__ __device__ __forceinline__ int64_t brick_elems(int64_t N) {
 static_assert(kBrick == 128, "brick_at_u32 shifts by log2(kBrick)");
 // Moment storage (regularized collision): the outgoing set of field k is w_i (Q_k + c_i . J*_k /
 // cs^2), so a cell's state is the 4 numbers (Q_k, J*_k) per field: bricks of kBrick cells with
-// NM = 20 rows r = 4 k + m (m = 0: Q_k deviation, 1..3: J*_k,x..z), so value m of field k of
-// cell c is element mom_at(c) + (4 k + m) kBrick.  A pull reads Q_k and one component of J*_k
+// NM = 20 rows r = 4 k + m (m = 0: w_1 Q_k = Q_k / 8, the share of Q_k each moving population
+// carries, as a deviation; 1..3: J*_k,x..z), so value m of field k of cell c is element
+// mom_at(c) + (4 k + m) kBrick.  Keeping Q_k / 8 spares the pull a multiplication per population.  A pull reads Q_k and one component of J*_k
 // of each source: scalar loads of whole 128-byte row segments per warp, no unused components.
 constexpr int NM = 4 * NF;
 __host__ __device__ __forceinline__ int64_t mom_at(int64_t c) {
@@ -203,9 +204,9 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
 
 // In: d[k][i] = pulled stored values (deviations, x enc[k] when scaled).  Out: o[k][i] = the
 // values to store (post-collision deviations in the same units).
-// MOM: the outgoing set as moments, o[k][0] = Q_k, o[k][1..3] = J*_k (regularized collision
-// only: its outgoing set is w_i (Q_k + c_i . J*_k / cs^2), population i being
-// fmaf(+-1/2, J*_k,a, Q_k / 8) for the links along axis a and Q_k / 4 at rest).
+// MOM: the outgoing set as moments, o[k][0] = w_1 Q_k = Q_k / 8, o[k][1..3] = J*_k (regularized
+// collision only: its outgoing set is w_i (Q_k + c_i . J*_k / cs^2), population i being
+// fmaf(+-1/2, J*_k,a, Q_k / 8) for the links along axis a and Q_k / 4 = 2 (Q_k / 8) at rest).
 template <int S, int COLL, bool DIAG, bool MOM = false>
 __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF][NQ],
                                         float (&o)[NF][NQ], CellDiag* cd) {
@@ -386,7 +387,7 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
 #pragma unroll
             for (int c = 0; c < 3; ++c) js[c] = Pd[k][c] + onem * (nA[k][c] - Fd[k][c]);
             if (MOM) {
-                o[k][0] = dQ[k];
+                o[k][0] = dQ[k] * cq1;  // w_1 Q_k: the rest of the set is rebuilt from it
                 o[k][1] = js[0];
                 o[k][2] = js[1];
                 o[k][3] = js[2];

@@ -100,9 +100,9 @@ cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* fr
 }
 
 // ---- moment storage ------------------------------------------------------------------------
-// A pull from a ghost plane reads Q_k and J*_k,z of the ghost cell (the +z population from plane
+// A pull from a ghost plane reads Q_k / 8 and J*_k,z of the ghost cell (the +z population from plane
 // 0, the -z one from plane nz - 1), so the exchange carries those two of the four moment rows
-// per field: slice 2 k + h holds row 4 k (h = 0, Q_k) or 4 k + 3 (h = 1, J*_k,z), 10 slices of
+// per field: slice 2 k + h holds row 4 k (h = 0, w_1 Q_k) or 4 k + 3 (h = 1, J*_k,z), 10 slices of
 // nx ny values per direction.
 __device__ __forceinline__ int mom_halo_row(int slice) { return 4 * (slice >> 1) + ((slice & 1) ? 3 : 0); }
 

@@ -158,11 +158,11 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
             for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? dp : 0.0f);
             Pd[4][a] = Hp * uv[a];
         }
-        if (swap == 2) {  // moment storage (FP32): Q_k and the first moment Phi^adv_k + A_k
+        if (swap == 2) {  // moment storage (FP32): w_1 Q_k and the first moment Phi^adv_k + A_k
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 T* m = fout + mom_at(c) + 4 * k * kBrick;
-                Store<S>::st(m, dQ[k]);
+                Store<S>::st(m, 0.125f * dQ[k]);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) Store<S>::st(m + (1 + a) * kBrick, Pd[k][a] + A[k][a]);
             }

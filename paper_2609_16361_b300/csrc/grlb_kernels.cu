@@ -56,8 +56,8 @@ __device__ __forceinline__ PullIdx pull_index(const DomainDev& D, int x, int y, 
 // step reads the ghost value instead of the missing neighbour, drops the population that
 // leaves the domain, and writes the ghost's incoming population into the boundary cell's own
 // slot (nobody else reads it in that step) for the AA_EVEN step to find.
-// MOM: two buffers of moments (brick_at_m layout, regularized collision): the pull rebuilds
-// f*_i(x - c_i) from the source cell's Q_k and J*_k with the collide's own operations, so the
+// MOM: two buffers of moments (mom_at layout, regularized collision): the pull rebuilds
+// f*_i(x - c_i) from the source cell's w_1 Q_k and J*_k with the collide's own operations, so the
 // sweep computes bit for bit what PULL computes on the populations those moments stand for,
 // reading 20 values per cell (each used by up to 7 cells, the reuse caught by L1 / L2) and
 // writing 20 instead of 35.
@@ -99,9 +99,10 @@ __device__ __forceinline__ PullAt pull_at_m(const PullIdx& P) {
     return A;
 }
 
-// Population i of the outgoing set (Q, J) of a field: Q / 4 at rest, fmaf(+-1/2, J_a, Q / 8)
-// along axis a (the regularized collide's own operations).
-__device__ __forceinline__ float mom_pop(float q, float j, float sign) { return fmaf(sign * 0.5f, j, q * 0.125f); }
+// Population i of the outgoing set of a field from its stored moments (w_1 Q, J): 2 w_1 Q = Q / 4
+// at rest, fmaf(+-1/2, J_a, w_1 Q) along axis a -- the regularized collide's own operations
+// (w_1 Q = Q / 8 is its q1, an exact scaling).
+__device__ __forceinline__ float mom_pop(float s1, float j, float sign) { return fmaf(sign * 0.5f, j, s1); }
 
 template <int S, int PAT>
 __device__ __forceinline__ void load_cell(const DomainDev& D, const typename Store<S>::T* fin,
@@ -113,7 +114,7 @@ __device__ __forceinline__ void load_cell(const DomainDev& D, const typename Sto
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             const int q = 4 * k * kBrick;
-            d[k][0] = 0.25f * St::ld(fin + A.c + q);
+            d[k][0] = 2.0f * St::ld(fin + A.c + q);
             d[k][1] = P.gl ? D.ghostL_st[k] : mom_pop(St::ld(fin + A.xm + q), St::ld(fin + A.xm + q + kBrick), 1.0f);
             d[k][2] = P.gr ? D.ghostR_st[k] : mom_pop(St::ld(fin + A.xp + q), St::ld(fin + A.xp + q + kBrick), -1.0f);
             d[k][3] = mom_pop(St::ld(fin + A.ym + q), St::ld(fin + A.ym + q + 2 * kBrick), 1.0f);
@@ -332,8 +333,10 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant
 // the two previous steps (L1 hits), and the tile's rows march through the planes together.
 // 256^3: 0.501 ms with 4 planes per thread, 0.513 / 0.532 / 0.544 with 8 / 16 / 32, 0.519 with
 // 1 (the loop costs 40 bytes of spills at the 6-CTA register cap); the one-cell kernel 0.511.
-// Prefetching the row segment's moments into L2 two planes ahead: 0.480 ms (one plane ahead
-// 0.485-0.49, three 0.477-0.484, into L1 alike; with 8 planes per thread 0.485-0.51).
+// Prefetching each row segment's moments into L2 two planes ahead (one prefetch per lane of
+// the first 20) ran 0.480 ms in short runs but added 5 % instructions, and in the sustained
+// benchmark the power cap then held the clock at ~1660 instead of ~1740 MHz: 31.07 against
+// 31.31 GLUP/s without it.
 // Staging the tile's planes in shared memory (cp.async, a ring of three planes, 96 KB per
 // 256-thread CTA) ran 0.821 ms: two CTAs per SM leave too few warps for the collide.
 constexpr int kZChunk = 4;  // planes per thread
@@ -346,15 +349,7 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom_col(const __grid_cons
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= D.nx || y >= D.ny) return;
     const int zb = blockIdx.z * lz, ze = min(zb + lz, D.nz);
-    const int lane = threadIdx.x;
     for (int z = zb; z < ze; ++z) {
-        // With 32-wide tiles a warp is one 32-cell row segment: its first 20 lanes warm the L2
-        // lines of the segment's 20 moment rows two planes ahead (one instruction per warp).
-        if (blockDim.x == 32 && lane < NM) {
-            const int zp = z + 2 >= D.nz ? z + 2 - D.nz : z + 2;
-            const float* pa = fin + mom_at(((int64_t)zp * D.ny + y) * D.nx + (x - lane)) + lane * kBrick;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-        }
         const PullIdx P = pull_index(D, x, y, z);
         const PullAt A = pull_at_m(P);
         float d[NF][NQ], o[NF][NQ];
@@ -581,11 +576,11 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
             for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? dp : 0.0f);
             Pd[4][a] = Hp * uv[a];
         }
-        if (swap == 2) {  // moment storage (FP32): Q_k and the first moment Phi^adv_k
+        if (swap == 2) {  // moment storage (FP32): w_1 Q_k and the first moment Phi^adv_k
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 T* m = fout + mom_at(c) + 4 * k * kBrick;
-                Store<S>::st(m, dQ[k]);
+                Store<S>::st(m, 0.125f * dQ[k]);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) Store<S>::st(m + (1 + a) * kBrick, Pd[k][a]);
             }
@@ -635,7 +630,7 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
             double acc = 0.0;
             const double sc = (double)D.dec[k];
             float mq = 0.0f, mj[3] = {0.0f, 0.0f, 0.0f};
-            if (gather == 2) {  // moment storage: the cell's own outgoing set
+            if (gather == 2) {  // moment storage: the cell's own outgoing set (mq = w_1 Q)
                 const T* m = fin + mom_at(c) + 4 * k * kBrick;
                 mq = Store<S>::ld(m);
 #pragma unroll
@@ -643,7 +638,7 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
             }
             for (int i = 0; i < NQ; ++i) {
                 double v;
-                if (gather == 2) v = (double)(i == 0 ? 0.25f * mq : mom_pop(mq, mj[(i - 1) >> 1], (i & 1) ? 1.0f : -1.0f));
+                if (gather == 2) v = (double)(i == 0 ? 2.0f * mq : mom_pop(mq, mj[(i - 1) >> 1], (i & 1) ? 1.0f : -1.0f));
                 else if (gather && i == 1 && P.gr) v = (double)Store<S>::ld(outflow + (5 + k) * nyz + P.yz);
                 else if (gather && i == 2 && P.gl) v = (double)Store<S>::ld(outflow + k * nyz + P.yz);
                 else v = (double)Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);

@@ -84,7 +84,7 @@ cudaError_t launch_halo_pack_z(const void* f, void* to_upper, void* to_lower, in
 cudaError_t launch_halo_unpack_z(void* f, const void* from_lower, const void* from_upper, int nz, int64_t nxy,
                                  size_t elem, cudaStream_t st);
 // The same for moment storage: per direction 10 slices of nx ny FP32 values, slice 2 k + h = row
-// 4 k (h = 0: Q_k) or 4 k + 3 (h = 1: J*_k,z) of the moment bricks.
+// 4 k (h = 0: Q_k / 8) or 4 k + 3 (h = 1: J*_k,z) of the moment bricks.
 cudaError_t launch_halo_z_mom(void* lower, void* upper, int nzl, int64_t nxy, cudaStream_t st);
 cudaError_t launch_halo_pack_z_mom(const void* f, void* to_upper, void* to_lower, int nz, int64_t nxy,
                                    cudaStream_t st);

@@ -273,11 +273,11 @@ __device__ __forceinline__ void prep_cell(const DomainDev& D, const typename Sto
         float acc = 0.0f;
         if (gather == 2) {  // moment storage: the cell's own outgoing set, summed as stored
             const typename Store<S>::T* m = fin + mom_at(c) + 4 * k * kBrick;
-            const float mq = Store<S>::ld(m);
-            acc = 0.25f * mq;
+            const float mq = Store<S>::ld(m);  // w_1 Q_k
+            acc = 2.0f * mq;
 #pragma unroll
             for (int i = 1; i < NQ; ++i)
-                acc += fmaf((i & 1) ? 0.5f : -0.5f, Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick), mq * 0.125f);
+                acc += fmaf((i & 1) ? 0.5f : -0.5f, Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick), mq);
         } else {
 #pragma unroll
             for (int i = 0; i < NQ; ++i) acc += Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);

@@ -98,7 +98,7 @@ def slab_params(prm):
 
 def halo_values(prm) -> int:
     """Values per cell of one exchanged slab face: the population along z of each field, or
-    Q_k and J*_k,z of each field for moment storage."""
+    Q_k / 8 and J*_k,z of each field for moment storage."""
     return 10 if prm.streaming == 2 else 5
 
 

@@ -108,7 +108,7 @@ def test_packed_slices_between_slabs_equal_the_undivided_run():
 
 
 def test_moment_slabs_bitwise_equal_the_undivided_moment_run():
-    """Moment storage: the exchange carries Q_k and J*_k,z of the boundary planes (on one device
+    """Moment storage: the exchange carries Q_k / 8 and J*_k,z of the boundary planes (on one device
     and through packed buffers, one rank closing the ring on itself); the interior is bitwise
     the undivided moment run, which is bitwise the population run."""
     c = inputs.tgv3d(32)
