@@ -83,6 +83,13 @@ def test_parameter_validation_without_device():
            good.replace(ref_p=0.0), good.replace(nx=2048, ny=2048, nz=1024)]
     for b in bad:
         assert capi.grlb_bytes_for(b) == 0
+    # moment storage: FP32 and the regularized collision only, 20 values per cell and buffer
+    mom = good.replace(streaming=2)
+    assert capi.grlb_bytes_for(good) - capi.grlb_bytes_for(mom) == 2 * (35 - 20) * 4 * 32 ** 3
+    for b in (mom.replace(collision=inputs.COLL_BGK), mom.replace(collision=inputs.COLL_RLB_GATED),
+              mom.replace(storage=inputs.STORE_F16), mom.replace(storage=inputs.STORE_BF16),
+              good.replace(streaming=3), good.replace(streaming=-1)):
+        assert capi.grlb_bytes_for(b) == 0
     h = C.c_void_p()
     st = capi.lib().grlb_create(C.byref(capi.to_params(good.replace(nx=0))), None, C.byref(h))
     assert st == -1 and b"nx" in capi.lib().grlb_last_error()
