@@ -1510,7 +1510,7 @@ extern "C" grlb_status grlb_halo_exchange_z(grlb_domain* lower, grlb_domain* upp
     return GRLB_OK;
 }
 
-// values per cell of one exchanged slab face: the population along z of each field, or Q_k and
+// values per cell of one exchanged slab face: the population along z of each field, or Q_k / 8 and
 // J*_k,z of each field (moment storage)
 static int halo_slices(const grlb_params& p) { return moment_storage(p) ? 10 : 5; }
 
