@@ -423,6 +423,14 @@ grlb_status grlb_spectral_diag(grlb_domain* d, int32_t nbins, double* spectrum, 
  * Errors: GRLB_EINVAL for ctas or iters < 1 or NULL pointers; GRLB_ECUDA on launch failure. */
 grlb_status grlb_ffma_probe(int32_t ctas, int32_t iters, float* sink, void* stream, double* warp_instructions);
 
+/* ---- cached device memory ----------------------------------------------------------------
+ * Domains and batches take device memory from the device's stream-ordered pool, which keeps what
+ * they release for reuse by this process (no device synchronisation on release).  grlb_trim_pool
+ * synchronises the current device and returns the pool's unused memory to the system, e.g.
+ * before creating a domain larger than any released before, or to leave the memory to another
+ * process.  Errors: GRLB_ECUDA. */
+grlb_status grlb_trim_pool(void);
+
 /* ---- bounds-checked build ------------------------------------------------------------------
  * A debugging aid with no counterpart in the paper, standing in for a memory checker.
  * libgrlb_checked.so is this library compiled with GRLB_CHECKED.  In it every load and store of

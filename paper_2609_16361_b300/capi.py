@@ -123,6 +123,7 @@ def lib():
             "grlb_halo_exchange_z": ([vp, vp], i32),
             "grlb_halo_pack_z": ([vp, vp, vp], i32),
             "grlb_halo_unpack_z": ([vp, vp, vp], i32),
+            "grlb_trim_pool": ([], i32),
             "grlb_checked_build": ([], C.c_int32),
             "grlb_check_read": ([C.POINTER(grlb_check_counts), C.c_int32], i32),
             "grlb_check_probe": ([vp, C.c_uint64, C.c_int64, C.c_uint64, vp], i32),
@@ -147,7 +148,7 @@ def exported_symbols():
             "grlb_batch_step", "grlb_batch_set_tile_x", "grlb_step_diag_noalloc",
             "grlb_spectrum_shells", "grlb_spectral_diag", "grlb_ffma_probe",
             "grlb_set_init_mode", "grlb_halo_exchange_z", "grlb_halo_pack_z", "grlb_halo_unpack_z",
-            "grlb_checked_build", "grlb_check_read", "grlb_check_probe"]
+            "grlb_trim_pool", "grlb_checked_build", "grlb_check_read", "grlb_check_probe"]
 
 
 def check(status):
@@ -430,6 +431,11 @@ class Domain:
     @property
     def steps(self):
         return grlb_steps_done(self.h)
+
+
+def grlb_trim_pool():
+    """Return the device memory the library's pool keeps for reuse to the system (synchronises)."""
+    check(lib().grlb_trim_pool())
 
 
 # ---- bounds-checked build (libgrlb_checked.so, selected with GRLB_LIB) -----------------------

@@ -1607,3 +1607,14 @@ extern "C" grlb_status grlb_check_probe(const void* base, uint64_t bytes, int64_
     return fail(GRLB_ESTATE, "grlb_check_probe: not a bounds-checked build (GRLB_CHECKED)");
 #endif
 }
+
+// ---- device memory cached by the pool ---------------------------------------------------------
+extern "C" grlb_status grlb_trim_pool(void) {
+    int dev = 0;
+    GRLB_CU(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    GRLB_CU(cudaDeviceGetDefaultMemPool(&pool, dev));
+    GRLB_CU(cudaDeviceSynchronize());  // releases still in flight on any stream complete first
+    GRLB_CU(cudaMemPoolTrimTo(pool, 0));
+    return GRLB_OK;
+}

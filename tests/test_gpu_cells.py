@@ -7,8 +7,9 @@ decoded independently (two buffers, every storage type); one-buffer domains afte
 against the two-buffer run of the same steps, with a check that a wrong slot would show; and
 the sum over links against grlb_read_conserved.  Then the capacity configurations -- 1024^3 with
 FP16 populations and 768^3 with FP32, one population buffer each, the workload `bench.py
---workload capacity` times -- one sweep of sampled cells against the oracle's update of the
-same cells from the probed pre-step populations of their pull sources."""
+--workload capacity` times, and 1024^3 FP32 with the state as moments -- one sweep of sampled
+cells against the oracle's update of the same cells from the probed pre-step populations of their
+pull sources."""
 import numpy as np
 import pytest
 
@@ -112,6 +113,8 @@ def test_capacity_sizes_sampled_cells(n, storage):
     to one FP16 spacing plus 16 units of 2^-24 of the field's largest stored value (the bound
     of the one-sweep storage pin)."""
     torch = pytest.importorskip("torch")
+    torch.cuda.empty_cache()
+    capi.grlb_trim_pool()
     prm, rho, u, p = inputs.tgv3d_device(n, storage=storage)
     prm = prm.replace(streaming=1)
     d = capi.Domain(prm)
@@ -144,3 +147,38 @@ def test_capacity_sizes_sampled_cells(n, storage):
         assert np.all(np.abs(g[blk] - w16[blk]) <= bound), (k, float(np.max(np.abs(g[blk] - w16[blk]) / bound)))
     share = float((g != w16).mean())
     assert share < 2e-3, share
+
+
+def test_capacity_moment_storage_sampled_cells():
+    """1024^3 in FP32 as moments (two buffers of 20 values per cell: 172 GB, where FP32
+    populations fit only at 768^3 with one buffer): after 5 sweeps, one more sweep of 2000
+    sampled cells against the oracle's update of the probed pre-step populations, within 2e-6
+    of each field's largest population.  Skipped if the device cannot hold it."""
+    torch = pytest.importorskip("torch")
+    n = 1024
+    prm = inputs.tgv3d(n, nxyz=(1, 1, 1)).params.replace(nx=n, ny=n, nz=n, streaming=2)
+    torch.cuda.empty_cache()
+    capi.grlb_trim_pool()  # earlier tests' domains went back to the library's pool
+    free, _ = torch.cuda.mem_get_info()
+    if capi.grlb_bytes_for(prm) + 5 * 8 * n ** 3 + (2 << 30) > free:
+        pytest.skip("device memory")
+    d = capi.Domain(prm)
+    _, rho, u, p = inputs.tgv3d_device(n)
+    capi.grlb_init_primitive_device(d.h, rho.data_ptr(), u.data_ptr(), p.data_ptr())
+    torch.cuda.synchronize()
+    del rho, u, p
+    torch.cuda.empty_cache()
+    d.step(5)
+    N = prm.ncells
+    rng = np.random.default_rng(12)
+    edges = [0, 1, n - 1, n, n * n - 1, n * n, N - n, N - 128, N - 1]
+    cells = np.unique(np.concatenate([rng.integers(0, N, 2000), edges])).astype(np.int64)
+    want, _ = oracle_update_cells(prm, lambda cs: capi.grlb_read_cells(d.h, cs), cells)
+    d.step(1)
+    got = capi.grlb_read_cells(d.h, cells)
+    d.close()
+    torch.cuda.empty_cache()
+    for k in range(5):
+        blk = slice(7 * k, 7 * k + 7)
+        scale = max(np.abs(want[blk]).max(), 1e-12)
+        assert np.abs(got[blk] - want[blk]).max() / scale < 2e-6, k
