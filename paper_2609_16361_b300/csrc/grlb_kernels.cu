@@ -339,6 +339,11 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant
 // 31.31 GLUP/s without it.
 // Staging the tile's planes in shared memory (cp.async, a ring of three planes, 96 KB per
 // 256-thread CTA) ran 0.821 ms: two CTAs per SM leave too few warps for the collide.
+// Carrying the column's z-window in registers (per field the arriving +z population and the
+// cell's own w_1 Q, J*_z, so a plane reads 2 values per field along z instead of 5: 55 loads
+// per cell instead of 65) spills 120 bytes at 6 CTAs per SM and ran 28.2 against 32.0 GLUP/s;
+// at 5 CTAs (96 registers) 32.1, within run-to-run spread, and that cap changed the collide's
+// multiply-add fusion (no longer bitwise the population sweep).  The loads are not the limit.
 constexpr int kZChunk = 4;  // planes per thread
 
 __global__ void __launch_bounds__(128, 6) sweep_kernel_mom_col(const __grid_constant__ DomainDev D, const void* fin_v,
