@@ -71,10 +71,26 @@ def job_mlups(ws, cells_per_rank, sweeps, seconds):
     return ws * cells_per_rank * sweeps / seconds / 1e6
 
 
-def kernel_source_sha(sources=None):
+def code_lines(text):
+    """The code of a CUDA source: `//` comments, trailing blanks and empty lines dropped (the
+    kernel sources hold no block comments and no `//` inside string literals)."""
+    out = []
+    for line in text.splitlines():
+        line = line.split("//", 1)[0].rstrip()
+        if line:
+            out.append(line)
+    return "\n".join(out)
+
+
+def kernel_source_sha(sources=None, read=None):
+    """Key of the counter records: a hash of the kernel sources' code, so a record stays valid
+    across comment edits and is dropped by any change to the code.  `read(path)` returns a
+    file's text (default: the working tree)."""
     h = hashlib.sha256()
     for p in KERNEL_SOURCES if sources is None else sources:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        text = read(p) if read else open(os.path.join(ROOT, p), encoding="utf-8").read()
+        h.update(code_lines(text).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

@@ -185,3 +185,22 @@ def test_per_cell_oracle_update_equals_the_oracle_sweep():
         cells = np.arange(c.params.ncells)
         want, _ = oracle_update_cells(c.params, lambda cs: pre[:, cs], cells)
         assert np.array_equal(want, o.f[:, cells]), c.params.name
+
+
+def test_counter_records_are_keyed_to_code_not_comments():
+    """bench.py attaches an ncu counter record to its line only while the kernel sources' code
+    is the code the counters were taken on: comment and blank-line edits keep the key, any code
+    change (an operand, a launch bound) drops it."""
+    import bench
+    base = "// header\n__global__ void k(float* a) {  // one thread per element\n    a[0] = 1.0f;\n}\n"
+    src = {"a.cu": base}
+    key = bench.kernel_source_sha(["a.cu"], read=src.get)
+    src["a.cu"] = "// header, reworded\n\n__global__ void k(float* a) {\n    a[0] = 1.0f;   // store\n}\n"
+    assert bench.kernel_source_sha(["a.cu"], read=src.get) == key
+    for edit in ("a[0] = 2.0f;", "a[1] = 1.0f;"):
+        src["a.cu"] = base.replace("a[0] = 1.0f;", edit)
+        assert bench.kernel_source_sha(["a.cu"], read=src.get) != key
+    # a file boundary is part of the key: the same lines split differently between files differ
+    two = {"a.cu": "int x;\nint y;", "b.cu": "int z;"}
+    moved = {"a.cu": "int x;", "b.cu": "int y;\nint z;"}
+    assert bench.kernel_source_sha(["a.cu", "b.cu"], read=two.get) != bench.kernel_source_sha(["a.cu", "b.cu"], read=moved.get)
