@@ -24,6 +24,12 @@ SOURCES = ["grlb_kernels.cu", "grlb_spectral.cu", "grlb_init_ce.cu", "grlb_halo.
            "grlb_api.cu"]
 HEADERS = ["grlb_device.cuh", "grlb_kernels.h", "grlb_check.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The sweep kernels' arithmetic is fixed by the source: no multiply-add contraction by the
+# compiler (every fused multiply-add is an explicit fmaf), so the rounding of each operation is
+# the same in every kernel the collide is instantiated in, whatever its launch bounds, register
+# budget or surrounding code -- the condition for moment and population storage, the checked
+# build, the batched and the diagnostic sweeps to agree bit for bit.
+FILE_FLAGS = {"grlb_kernels.cu": ["-fmad=false"]}
 
 
 def _nvcc():
@@ -54,7 +60,8 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
         flags += ["-Xptxas", "-v"]
     with tempfile.TemporaryDirectory(prefix="grlb_build_") as tmpdir:
         objs = [os.path.join(tmpdir, f[:-3] + ".o") for f in SOURCES]
-        jobs = [[_nvcc(), *flags, "-c", os.path.join(CSRC, f), "-o", o] for f, o in zip(SOURCES, objs)]
+        jobs = [[_nvcc(), *flags, *FILE_FLAGS.get(f, []), "-c", os.path.join(CSRC, f), "-o", o]
+                for f, o in zip(SOURCES, objs)]
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 1)) as ex:
             for rc, cmd in zip(ex.map(subprocess.call, jobs), jobs):
                 if rc != 0:

@@ -145,15 +145,17 @@ template <> struct Store<S_BF16> {
     }
 };
 
-// Division in the collide.  FP32 storage: IEEE division.  16-bit storage: the approximate
-// reciprocal-and-multiply (__fdividef, within 2 ulp for the O(1) divisors here, far below the
-// storage rounding of 2^-9 .. 2^-12): without the IEEE division's slow path the 16-bit sweeps,
-// which are limited by instruction issue and latency, need 64 registers instead of 89 and run
-// 8-10 % faster; the HBM-bound FP32 sweep gains nothing from the extra warps (0.8 % slower).
+// Division in the collide: the approximate reciprocal-and-multiply (__fdividef, within 2 ulp
+// for the divisors here: rho >= rho_min, t + T_S, 1 + beta >= 1 and 1 + 4 omega_E (g-1) kappa /
+// rho >= 1, all far inside its range), for every storage.  Without the IEEE division's slow
+// path the sweeps need 64 registers instead of 89: the 16-bit sweeps (limited by instruction
+// issue and latency) run 8-10 % faster, the moment-storage sweep 4 % (33.2 against 31.8
+// GLUP/s, and at a higher clock under the power cap); the FP32 population sweep, HBM-bound,
+// 0.8 % slower (0.678 against 0.673 ms).  Moment and population storage share the one
+// division, so they stay bit for bit the same.
 template <int S>
 __device__ __forceinline__ float coll_div(float a, float b) {
-    if constexpr (S == S_F32) return a / b;
-    else return __fdividef(a, b);
+    return __fdividef(a, b);
 }
 
 // Per-cell diagnostic values (FP32, reduced later in FP64).
@@ -172,9 +174,9 @@ __device__ __forceinline__ void add_source(const DomainDev& D, int32_t c, float 
         const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
         float sk = GRLB_LDG(D.src + (int64_t)k * D.plane + c) * D.src_scale[r];
         if (Store<S>::scaled) sk *= D.enc[k];
-        o[k][0] += 0.25f * sk;
+        o[k][0] = fmaf(0.25f, sk, o[k][0]);
 #pragma unroll
-        for (int i = 1; i < NQ; ++i) o[k][i] += 0.125f * sk;
+        for (int i = 1; i < NQ; ++i) o[k][i] = fmaf(0.125f, sk, o[k][i]);
     }
 }
 
@@ -219,6 +221,8 @@ __device__ __forceinline__ void collide(const DomainDev& D, const float (&d)[NF]
 
 // Everything after the moments: primitives and floors, reconstruction, sensor, closures,
 // equilibrium and collision.  The regularized collision needs only (dQ, dJ); BGK also reads d.
+// Each multiply-add that is to be fused is written as fmaf and the files that instantiate the
+// collide are compiled without contraction, so its rounding is the same in every kernel.
 template <int S, int COLL, bool DIAG, bool MOM>
 __device__ __forceinline__ void collide_moments(const DomainDev& D, const float (&dQ)[NF],
                                                 const float (&dJ)[NF][3], const float (&d)[NF][NQ],
@@ -232,8 +236,8 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
     const float irho = coll_div<S>(1.0f, rho);
     const float m0 = dQ[1], m1 = dQ[2], m2 = dQ[3];
     const float u0 = m0 * irho, u1 = m1 * irho, u2 = m2 * irho;
-    const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-    const float ke = 0.5f * (m0 * u0 + m1 * u1 + m2 * u2);
+    const float uu = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+    const float ke = 0.5f * fmaf(m0, u0, fmaf(m1, u1, m2 * u2));
     // p - p_ref = (gamma-1)(dE - ke): the pressure fluctuation without cancellation
     float dp = gm1 * (dQ[4] - ke);
     const float p_raw = D.p_ref + dp;
@@ -261,9 +265,12 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) nA[1 + j][c] = dJ[1 + j][c] - mm[j] * uv[c] - (j == c ? dp : 0.0f);
+        for (int c = 0; c < 3; ++c) {
+            const float v = fmaf(-mm[j], uv[c], dJ[1 + j][c]);
+            nA[1 + j][c] = j == c ? v - dp : v;
+        }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) nA[4][c] = dJ[4][c] - Hp * uv[c];
+    for (int c = 0; c < 3; ++c) nA[4][c] = fmaf(-Hp, uv[c], dJ[4][c]);
 
     // direct reconstruction grad Q~ = -omega Pi / cs^2 (cs^-2 = 4)
     const float w4r = -4.0f * D.omega[0], w4m = -4.0f * D.omega[1], w4e = -4.0f * D.omega[2];
@@ -278,26 +285,28 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
     // trace pass through, the symmetric-deviatoric part is divided by 1 + beta, beta = 2b.
     const float a_mu = mu * irho;
     const float b = 4.0f * D.omega[1] * a_mu;
-    const float ugr = u0 * gr[0] + u1 * gr[1] + u2 * gr[2];
+    const float ugr = fmaf(u0, gr[0], fmaf(u1, gr[1], u2 * gr[2]));
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            G[j][c] = w4m * nA[1 + j][c] +
-                      b * (uv[j] * gr[c] + uv[c] * gr[j] - (j == c ? (2.0f / 3.0f) * ugr : 0.0f));
+        for (int c = 0; c < 3; ++c) {
+            float sg = fmaf(uv[j], gr[c], uv[c] * gr[j]);
+            if (j == c) sg = fmaf(-(2.0f / 3.0f), ugr, sg);
+            G[j][c] = fmaf(b, sg, w4m * nA[1 + j][c]);
+        }
     {
         const float trG3 = (G[0][0] + G[1][1] + G[2][2]) * (1.0f / 3.0f);
-        const float kdamp = coll_div<S>(2.0f * b, 1.0f + 2.0f * b);  // beta / (1 + beta)
+        const float kdamp = coll_div<S>(2.0f * b, fmaf(2.0f, b, 1.0f));  // beta / (1 + beta)
         float Dv[3][3];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                Dv[j][c] = 0.5f * (G[j][c] + G[c][j]) - (j == c ? trG3 : 0.0f);
+                Dv[j][c] = j == c ? fmaf(0.5f, G[j][c] + G[c][j], -trG3) : 0.5f * (G[j][c] + G[c][j]);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) G[j][c] -= kdamp * Dv[j][c];  // G := grad m
+            for (int c = 0; c < 3; ++c) G[j][c] = fmaf(-kdamp, Dv[j][c], G[j][c]);  // G := grad m
     }
     // energy row (Eq. cnsfE): scalar division with the corrected upstream gradients
     const float kr = kap * irho;
@@ -306,22 +315,23 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
         const float trm23 = (2.0f / 3.0f) * (G[0][0] + G[1][1] + G[2][2]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            gmTu[c] = G[0][c] * u0 + G[1][c] * u1 + G[2][c] * u2;  // ((grad m)^T u)_c
+            gmTu[c] = fmaf(G[0][c], u0, fmaf(G[1][c], u1, G[2][c] * u2));  // ((grad m)^T u)_c
             // (S(grad m) u)_c = sum_j (G_cj + G_jc) u_j - 2/3 tr(G) u_c
-            Su[c] = (G[c][0] + G[0][c]) * u0 + (G[c][1] + G[1][c]) * u1 +
-                    (G[c][2] + G[2][c]) * u2 - trm23 * uv[c];
+            Su[c] = fmaf(-trm23, uv[c],
+                         fmaf(G[c][0] + G[0][c], u0, fmaf(G[c][1] + G[1][c], u1, (G[c][2] + G[2][c]) * u2)));
         }
     }
     {
-        const float cT = kr * (T - 0.5f * gm1 * uu);
+        const float cT = kr * fmaf(-0.5f * gm1, uu, T);
         const float w4 = 4.0f * D.omega[2];
-        const float inv = coll_div<S>(1.0f, 1.0f + w4 * gm1 * kr);
+        const float gkr = gm1 * kr;
+        const float inv = coll_div<S>(1.0f, fmaf(w4, gkr, 1.0f));
         const float ugr3 = (1.0f / 3.0f) * ugr;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float MEr = a_mu * (uu * gr[c] + ugr3 * uv[c]) + cT * gr[c];
-            const float MEm = -a_mu * Su[c] + gm1 * kr * gmTu[c];
-            ge[c] = (ge[c] + w4 * (MEr + MEm)) * inv;
+            const float MEr = fmaf(a_mu, fmaf(uu, gr[c], ugr3 * uv[c]), cT * gr[c]);
+            const float MEm = fmaf(-a_mu, Su[c], gkr * gmTu[c]);
+            ge[c] = fmaf(w4, MEr + MEm, ge[c]) * inv;
         }
     }
     // chain rule (Sec. 2.4): grad u and grad T
@@ -329,12 +339,12 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gu[j][c] = (G[j][c] - uv[j] * gr[c]) * irho;
+        for (int c = 0; c < 3; ++c) gu[j][c] = fmaf(-uv[j], gr[c], G[j][c]) * irho;
     {
-        const float cr = (0.5f * gm1 * uu - T) * irho;
+        const float cr = fmaf(0.5f * gm1, uu, -T) * irho;
         const float cg = gm1 * irho;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gT[c] = cg * (ge[c] - gmTu[c]) + cr * gr[c];
+        for (int c = 0; c < 3; ++c) gT[c] = fmaf(cg, ge[c] - gmTu[c], cr * gr[c]);
     }
     const float theta = gu[0][0] + gu[1][1] + gu[2][2];
     // compression sensor (Listing 2): s = -div u / cs, cs = 1/2
@@ -360,11 +370,11 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             Fd[1 + j][c] = -tau[j][c];
-            Pd[1 + j][c] = mm[j] * uv[c] + (j == c ? dp : 0.0f) - tau[j][c];
+            Pd[1 + j][c] = j == c ? fmaf(mm[j], uv[c], dp) - tau[j][c] : fmaf(mm[j], uv[c], -tau[j][c]);
         }
-        const float tu = tau[c][0] * u0 + tau[c][1] * u1 + tau[c][2] * u2;
-        Fd[4][c] = -tu - kap * gT[c];
-        Pd[4][c] = Hp * uv[c] + Fd[4][c];
+        const float tu = fmaf(tau[c][0], u0, fmaf(tau[c][1], u1, tau[c][2] * u2));
+        Fd[4][c] = fmaf(-kap, gT[c], -tu);
+        Pd[4][c] = fmaf(Hp, uv[c], Fd[4][c]);
     }
 
     // C_GATED takes one of the two per cell (chi is uniform over the cell's five fields)
@@ -376,7 +386,7 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             const int r = (k == 0) ? 0 : (k == 4 ? 2 : 1);
-            const float omh = D.omega[r] - chi * D.omega_red[r];
+            const float omh = fmaf(-chi, D.omega_red[r], D.omega[r]);
             const float onem = 1.0f - omh;
             // storage scale (a power of two) folded into w_i and 1/2: every product is exact,
             // so the stored values equal those of scaling the outgoing set afterwards
@@ -385,7 +395,7 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
             const float cj = SC ? D.enc_j[k] : 0.5f;
             float js[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) js[c] = Pd[k][c] + onem * (nA[k][c] - Fd[k][c]);
+            for (int c = 0; c < 3; ++c) js[c] = fmaf(onem, nA[k][c] - Fd[k][c], Pd[k][c]);
             if (MOM) {
                 o[k][0] = dQ[k] * cq1;  // w_1 Q_k: the rest of the set is rebuilt from it
                 o[k][1] = js[0];
@@ -429,7 +439,7 @@ __device__ __forceinline__ void collide_moments(const DomainDev& D, const float 
         for (int k = 0; k < NF; ++k) cd->dQ[k] = dQ[k];
         cd->ke = ke;
         const float wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
-        cd->eps_s = mu * (wx * wx + wy * wy + wz * wz);
+        cd->eps_s = mu * fmaf(wx, wx, fmaf(wy, wy, wz * wz));
         cd->eps_d = (4.0f / 3.0f) * mu * theta * theta;
         cd->rho_raw = rho_raw;
         cd->p_raw = p_raw;

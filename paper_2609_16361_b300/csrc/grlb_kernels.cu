@@ -1,5 +1,9 @@
 // grlb_kernels.cu -- sweep, initialisation, readback and diagnostic-reduction kernels.
 //
+// Compiled without multiply-add contraction (-fmad=false): each fused multiply-add is an
+// explicit fmaf, so every kernel the collide is instantiated in rounds each operation the same
+// way, whatever its launch bounds or register budget.
+//
 // Layout in HBM (per domain, per buffer): cell bricks (grlb_device.cuh) -- 128 consecutive
 // cells in storage order (x fastest) keep their 35 population rows q = 7k + i (field k, link i)
 // together, 128 elements each.  One CTA covers a tile of blockDim.x consecutive cells of
@@ -305,9 +309,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const __grid_constant__ Doma
 }
 
 // The gated FP32 collision keeps both updates live in a warp that straddles the gate (114
-// registers, 4 CTAs per SM); capped at 5 CTAs per SM (96 registers, 52 bytes of spills) it runs
-// 2.6 % faster (0.701 against 0.719 ms at 256^3).  A separate kernel carries the cap: a minimum
-// block count in the other instantiations' bounds, even 1, changes their register allocation.
+// registers, 4 CTAs per SM, with IEEE divisions in the collide); capped at 5 CTAs per SM it
+// needs 96 registers, without spills since the collide divides approximately, and takes 0.670
+// ms at 256^3 (0.701 with the IEEE divisions' 52 bytes of spills, 0.719 uncapped).  A separate
+// kernel carries the cap, so the other instantiations keep their own register allocation.
 template <bool DIAG, bool SRC, int PAT, bool LIN>
 __global__ void __launch_bounds__(128, 5) sweep_kernel_gated_f32(const __grid_constant__ DomainDev D,
                                                                  const void* fin_v, void* fout_v,
@@ -316,11 +321,12 @@ __global__ void __launch_bounds__(128, 5) sweep_kernel_gated_f32(const __grid_co
 }
 
 // The plain moment-storage sweep waits mostly on its 65 loads per cell (L1 / L2 hits of the
-// sources' moments) with 5 CTAs per SM at 92 registers; capped at 6 CTAs (80 registers, 28
-// bytes of spills) it runs 1.7 % faster.  Its own kernel carries the cap, as for the gated
-// sweep.  The diagnostic variant keeps the plain bound: capped, the compiler fused other
-// multiply-adds than in the population sweep's diagnostic variant, and the two storages would no
-// longer agree bit for bit.
+// sources' moments).  With IEEE divisions in the collide it held 92 registers (5 CTAs per SM)
+// and ran 1.7 % faster capped at 6 CTAs; with the approximate divisions it fits the 6-CTA cap
+// (80 registers) without spills, and 6 or 8 CTAs per SM run alike (33.2 GLUP/s).  The
+// diagnostic variant (72 registers) keeps the plain bound.  The rounding of every operation
+// is fixed by the source (no compiler contraction in this file), so the cap does not change
+// results.
 template <bool LIN>
 __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant__ DomainDev D, const void* fin_v,
                                                            void* fout_v, double* __restrict__ partials) {
@@ -342,8 +348,8 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant
 // Carrying the column's z-window in registers (per field the arriving +z population and the
 // cell's own w_1 Q, J*_z, so a plane reads 2 values per field along z instead of 5: 55 loads
 // per cell instead of 65) spills 120 bytes at 6 CTAs per SM and ran 28.2 against 32.0 GLUP/s;
-// at 5 CTAs (96 registers) 32.1, within run-to-run spread, and that cap changed the collide's
-// multiply-add fusion (no longer bitwise the population sweep).  The loads are not the limit.
+// at 5 CTAs (96 registers) 32.1, within run-to-run spread (both with IEEE divisions in the
+// collide).  The loads are not the limit.
 constexpr int kZChunk = 4;  // planes per thread
 
 __global__ void __launch_bounds__(128, 6) sweep_kernel_mom_col(const __grid_constant__ DomainDev D, const void* fin_v,
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
         const float uv[3] = {(float)(GRLB_LD(u + c) * s), (float)(GRLB_LD(u + N + c) * s),
                              (float)(GRLB_LD(u + 2 * N + c) * s)};
         const float m[3] = {rf * uv[0], rf * uv[1], rf * uv[2]};
-        const float ke = 0.5f * (m[0] * uv[0] + m[1] * uv[1] + m[2] * uv[2]);
+        const float ke = 0.5f * fmaf(m[0], uv[0], fmaf(m[1], uv[1], m[2] * uv[2]));
         const float dE = dp / g1 + ke;
         const float Hp = Hp_ref + dE + dp;  // E + p
         const float dQ[5] = {drho, m[0], m[1], m[2], dE};
@@ -578,7 +584,7 @@ __global__ void __launch_bounds__(256) init_kernel(const DomainDev D, void* __re
         for (int a = 0; a < 3; ++a) {
             Pd[0][a] = m[a];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? dp : 0.0f);
+            for (int j = 0; j < 3; ++j) Pd[1 + j][a] = j == a ? fmaf(m[j], uv[a], dp) : m[j] * uv[a];
             Pd[4][a] = Hp * uv[a];
         }
         if (swap == 2) {  // moment storage (FP32): w_1 Q_k and the first moment Phi^adv_k
@@ -647,7 +653,7 @@ __global__ void conserved_kernel(const DomainDev D, const void* __restrict__ fin
                 else if (gather && i == 1 && P.gr) v = (double)Store<S>::ld(outflow + (5 + k) * nyz + P.yz);
                 else if (gather && i == 2 && P.gl) v = (double)Store<S>::ld(outflow + k * nyz + P.yz);
                 else v = (double)Store<S>::ld(fin + brick_at(at[i]) + (7 * k + i) * kBrick);
-                acc += v * sc;
+                acc = fma(v, sc, acc);
             }
             double q = acc;
             if (k == 0) q += rho_ref;
@@ -686,9 +692,7 @@ static cudaError_t launch_sweep_p(const DomainDev& D, const void* fin, void* fou
 
 // column-marching moment sweep (plain sweeps of tiled domains): the grid's z extent split into
 // chunks of kZChunk planes
-// (The diagnostic sweep stays one cell per thread: a column-marching diagnostic variant ran
-// 0.858 against ~0.88 ms per 256^3 sweep, but compiled other multiply-add fusions than the
-// population sweep's diagnostic variant, so the two storages no longer agreed bit for bit.)
+// (The diagnostic sweep stays one cell per thread: 0.689 ms per 256^3 sweep, 1 in 50.)
 static cudaError_t launch_sweep_mom_col(const DomainDev& D, const void* fin, void* fout, dim3 grid, dim3 block,
                                         cudaStream_t st) {
     const int lz = D.nz < kZChunk ? D.nz : kZChunk;
