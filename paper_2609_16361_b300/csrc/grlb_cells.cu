@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) read_cells_kernel(const __grid_constant__
             const float mq = Store<S>::ld(m);
             const float v = i == 0 ? 2.0f * mq  // mq = w_1 Q_k
                                    : fmaf(((i & 1) ? 0.5f : -0.5f), Store<S>::ld(m + (1 + ((i - 1) >> 1)) * kBrick), mq);
-            GRLB_ST(out + t, (double)v * dec.dec[k] + dec.shift[q]);
+            GRLB_ST(out + t, fma((double)v, dec.dec[k], dec.shift[q]));
             continue;
         }
         if (layout == 0) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) read_cells_kernel(const __grid_constant__
             else src = buf + brick_at(xs + nx * (ys + ny * zs)) + (int64_t)q * kBrick;
         }
         const float v = Store<S>::ld(src);
-        GRLB_ST(out + t, (double)v * dec.dec[k] + dec.shift[q]);
+        GRLB_ST(out + t, fma((double)v, dec.dec[k], dec.shift[q]));
     }
 }
 

@@ -100,17 +100,17 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
                 const float uP = (float)P.u[j] * sl, uM = (float)M.u[j] * sl;
                 du[j] = (float)(P.u[j] - M.u[j]) * sl;
                 ub[j] = 0.5f * (uP + uM);
-                du2 += 2.0f * ub[j] * du[j];                                   // d |u|^2
-                u2b += 0.5f * (uP * uP + uM * uM);
+                du2 = fmaf(2.0f * ub[j], du[j], du2);                         // d |u|^2
+                u2b = fmaf(0.5f, fmaf(uP, uP, uM * uM), u2b);
             }
             gQ[0][a] = h * dr;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                gQ[1 + j][a] = h * (rb * du[j] + ub[j] * dr);                  // d (r u_j)
+                gQ[1 + j][a] = h * fmaf(rb, du[j], ub[j] * dr);                // d (r u_j)
                 gu[j][a] = h * du[j];
             }
-            gQ[4][a] = h * (dp / g1 + 0.5f * (rb * du2 + u2b * dr));           // d (p/(g-1) + r|u|^2/2)
-            gT[a] = h * (rb * dp - pb * dr) / (rP * rM);                       // d (p / r)
+            gQ[4][a] = h * fmaf(0.5f, fmaf(rb, du2, u2b * dr), dp / g1);      // d (p/(g-1) + r|u|^2/2)
+            gT[a] = h * fmaf(rb, dp, -(pb * dr)) / (rP * rM);                 // d (p / r)
         }
         const float T0 = (float)q0.p * sl2 / (float)q0.r;
         float fac = 1.0f;
@@ -131,11 +131,11 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float qa = -kap * gT[a];
-            const float dE = -(tv[a][0] * u0[0] + tv[a][1] * u0[1] + tv[a][2] * u0[2]) + qa;
+            const float dE = qa - fmaf(tv[a][0], u0[0], fmaf(tv[a][1], u0[1], tv[a][2] * u0[2]));
             A[0][a] = -((float)C.tau[0] - 1.0f) * 0.25f * gQ[0][a];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) A[1 + j][a] = -tv[j][a] - ((float)C.tau[1 + j] - 1.0f) * 0.25f * gQ[1 + j][a];
-            A[4][a] = dE - ((float)C.tau[4] - 1.0f) * 0.25f * gQ[4][a];
+            for (int j = 0; j < 3; ++j) A[1 + j][a] = fmaf(-((float)C.tau[1 + j] - 1.0f) * 0.25f, gQ[1 + j][a], -tv[j][a]);
+            A[4][a] = fmaf(-((float)C.tau[4] - 1.0f) * 0.25f, gQ[4][a], dE);
         }
 
         // equilibrium part: the plain initialisation's deviation arithmetic
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
         const float uv[3] = {(float)(GRLB_LD(u + c) * C.s), (float)(GRLB_LD(u + N + c) * C.s),
                              (float)(GRLB_LD(u + 2 * N + c) * C.s)};
         const float m[3] = {rf * uv[0], rf * uv[1], rf * uv[2]};
-        const float ke = 0.5f * (m[0] * uv[0] + m[1] * uv[1] + m[2] * uv[2]);
+        const float ke = 0.5f * fmaf(m[0], uv[0], fmaf(m[1], uv[1], m[2] * uv[2]));
         const float dEd = dp / g1 + ke;
         const float Hp = Hp_ref + dEd + dp;
         const float dQ[5] = {drho, m[0], m[1], m[2], dEd};
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) init_ce_kernel(const DomainDev D, void* _
         for (int a = 0; a < 3; ++a) {
             Pd[0][a] = m[a];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) Pd[1 + j][a] = m[j] * uv[a] + (j == a ? dp : 0.0f);
+            for (int j = 0; j < 3; ++j) Pd[1 + j][a] = j == a ? fmaf(m[j], uv[a], dp) : m[j] * uv[a];
             Pd[4][a] = Hp * uv[a];
         }
         if (swap == 2) {  // moment storage (FP32): w_1 Q_k and the first moment Phi^adv_k + A_k

@@ -6,7 +6,7 @@ with them bit for bit.
     GRLB_LIB=<library> python tests/checked_battery.py <out.json>
 
 Writes <out.json> = {"checked": bool, "scenarios": {name: {"parts": {label: {"digest": sha,
-"tol": t, "narrays": n}}, "violations": n, "first": addr}}, "probe": [...], "final": counts} and
+"narrays": n}}, "violations": n, "first": addr}}, "probe": [...], "final": counts} and
 <out.npz> with each part's floating-point arrays under "scenario|label|i".  Run as a child process (the library a process loads is fixed
 at its first call) by tests/test_gpu_checked.py.
 """
@@ -33,25 +33,22 @@ def with_params(case, **kw):
 
 
 class Digest:
-    """Per part of a scenario (one part per run): the sha256 of its arrays, the floating-point
-    arrays themselves (FP64 copies, for sizing a difference when two digests differ) and the
-    tolerance that applies to them (relative to each array's largest magnitude: 2e-6 where every
-    domain stores FP32 populations, 2e-3 where one stores 16-bit ones -- a one-ulp FP32
-    difference can flip a 16-bit rounding)."""
+    """Per part of a scenario (one part per run): the sha256 of its arrays and the floating-point
+    arrays themselves (FP64 copies, for sizing a difference when two digests differ)."""
 
     def __init__(self):
         self.parts = {}
         self.cur = None
 
-    def part(self, label, fp32=True):
-        self.cur = self.parts.setdefault(label, {"h": hashlib.sha256(), "arrays": [],
-                                                 "tol": 2e-6 if fp32 else 2e-3})
+    def part(self, label):
+        self.cur = self.parts.setdefault(label, {"h": hashlib.sha256(), "arrays": []})
 
     def add(self, *arrays):
         if self.cur is None:
-            self.part("all", fp32=False)
+            self.part("all")
         for a in arrays:
             a = np.ascontiguousarray(a)
+            assert a.dtype.kind in "biuf", a.dtype  # numbers only: an object array digests addresses
             self.cur["h"].update(a.tobytes())
             if a.dtype.kind == "f":
                 self.cur["arrays"].append(a.astype(np.float64).ravel())
@@ -62,7 +59,7 @@ class Digest:
                            g["n_floor"], g["n_nan"], g["n_sensor"], g["step"]], dtype=np.float64))
 
     def result(self):
-        return {k: {"digest": v["h"].hexdigest(), "tol": v["tol"], "narrays": len(v["arrays"])}
+        return {k: {"digest": v["h"].hexdigest(), "narrays": len(v["arrays"])}
                 for k, v in self.parts.items()}
 
     def arrays(self, scenario):
@@ -72,7 +69,7 @@ class Digest:
 def run_domain(dg, case, steps, ce=None, stream=None):
     prm = case.params
     dg.part(f"{prm.name} {prm.nx}x{prm.ny}x{prm.nz} s{prm.storage} c{prm.collision} "
-            f"aa{prm.streaming} n{steps} ce{int(bool(ce))}", fp32=prm.storage == inputs.STORE_F32)
+            f"aa{prm.streaming} n{steps} ce{int(bool(ce))}")
     d = capi.Domain(case.params, stream=stream)
     d.init(case.rho, case.u, case.p, ce_init=ce)
     d.step(steps)
@@ -177,7 +174,7 @@ def sc_batches(dg):
         for tile in (0, 1, 32, 128):
             if sched == capi.SCHED_CONCURRENT and tile:
                 continue
-            dg.part(f"schedule {sched} tile {tile}", fp32=False)
+            dg.part(f"schedule {sched} tile {tile}")
             cases = batch_cases()
             doms = [capi.Domain(c.params) for c in cases]
             for d, c in zip(doms, cases):
@@ -197,7 +194,7 @@ def sc_batches(dg):
 
 def sc_serve(dg):
     trace = inputs.serving_trace(seed=5, n_requests=6, rate=500.0, tgv_range=(12, 16), steps_range=(10, 40))
-    dg.part("served", fp32=False)
+    dg.part("served")
     for r in serve.Server(chunk=8, keep_fields=True).run(trace, realtime=False):
         dg.add(np.frombuffer(r.digest.encode(), dtype=np.uint8), r.fields)
 
@@ -258,17 +255,21 @@ def sc_noalloc(dg):
         d.close()
 
 
+def spectral_sums(sums):
+    """The three sums of a spectral call as numbers (a dict itself would digest as an object)."""
+    return np.array([sums["eps_s"], sums["eps_d"], sums["ke_u"]])
+
+
 def sc_spectral(dg):
     cases = [inputs.tgv3d(16), with_params(inputs.tgv3d(32, storage=inputs.STORE_F16), streaming=1),
              inputs.tgv2d(32), inputs.tgv2d(64), inputs.tgv2d(512)]
     for i, c in enumerate(cases):
-        dg.part(f"spectral {c.params.nx}x{c.params.ny}x{c.params.nz} s{c.params.storage} aa{c.params.streaming}",
-                fp32=c.params.storage == inputs.STORE_F32)
+        dg.part(f"spectral {c.params.nx}x{c.params.ny}x{c.params.nz} s{c.params.storage} aa{c.params.streaming}")
         d = capi.Domain(c.params)
         d.init(c.rho, c.u, c.p)
         d.step(3 if c.params.streaming else 1 + i % 2)  # odd: the one-buffer readback gathers
         E, sums = d.spectral()
-        dg.add(np.asarray(E), np.asarray(sums))
+        dg.add(np.asarray(E), spectral_sums(sums))
         d.close()
 
 
@@ -298,7 +299,7 @@ def sc_moments(dg):
         dg.add(capi.grlb_read_cells(d.h, np.arange(case.params.ncells)))
         if case.params.name.startswith("tgv"):
             E, sums = d.spectral()
-            dg.add(np.asarray(E), np.asarray(sums))
+            dg.add(np.asarray(E), spectral_sums(sums))
         d.close()
 
 
