@@ -64,6 +64,16 @@ float storage_scale(int storage, double Mk) {
     return std::ldexp(1.0f, 8 - e);
 }
 
+// A value in stored units as the storage type holds it (round to nearest even for FP16 / BF16):
+// the Dirichlet ghost populations are kept so, because the one-buffer pattern writes them to a
+// slot of the boundary cell and reads them back, and the two-buffer sweep must pull the same
+// number.
+float as_stored(int storage, float v) {
+    if (storage == GRLB_STORE_F16) return __half2float(__float2half_rn(v));
+    if (storage == GRLB_STORE_BF16) return __bfloat162float(__float2bfloat16_rn(v));
+    return v;
+}
+
 // Device memory of domains and batches comes from the device's stream-ordered pool
 // (cudaMallocAsync / cudaFreeAsync): freeing does not synchronise the device, so a serving loop
 // can release a finished request while the others keep running.  The pool keeps released
@@ -214,8 +224,8 @@ static void fill_domain_dev(grlb_domain* d) {
         D.enc_q0[k] = 0.25f * D.enc[k];
         D.enc_q1[k] = 0.125f * D.enc[k];
         D.enc_j[k] = 0.5f * D.enc[k];
-        D.ghostL_st[k] = D.ghostL[k] * D.enc[k];
-        D.ghostR_st[k] = D.ghostR[k] * D.enc[k];
+        D.ghostL_st[k] = as_stored(p.storage, D.ghostL[k] * D.enc[k]);
+        D.ghostR_st[k] = as_stored(p.storage, D.ghostR[k] * D.enc[k]);
     }
     D.src = nullptr;
     D.outflow = nullptr;

@@ -99,8 +99,8 @@ struct DomainDev {
     float enc[5];          // stored = value * enc[k] (a power of two)
     float enc_q0[5], enc_q1[5], enc_j[5];  // w_0 enc[k], w_1 enc[k], enc[k] / 2: the scale
                                            // folded into the constants of the outgoing set
-    float ghostL_st[5];    // ghostL[k] enc[k], ghostR[k] enc[k]: the ghost values in stored units
-    float ghostR_st[5];
+    float ghostL_st[5];    // ghostL[k] enc[k], ghostR[k] enc[k]: the ghost values in stored units,
+    float ghostR_st[5];    // rounded to the storage type (as a one-buffer slot holds them)
     void* outflow;         // one-buffer X_DIRICHLET_EQ: populations leaving through x = -1 / nx in
                            // an odd step, [side][k][y + ny z] (side 0: -x at x = 0, 1: +x at nx-1)
     const float* src;      // optional source S_k (5 planes, physical rates), or null

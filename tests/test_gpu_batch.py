@@ -5,10 +5,9 @@ in the constant table or in device memory (tile table).
 
 * A domain's batched result is bitwise independent of the other domains in the batch (alone
   in a batch == in the mix), under every schedule.
-* Under the concurrent schedule it is bitwise the solo run; under the table schedules it equals
-  the solo single-domain sweep within FP32 rounding (the kernels read the domain constants from
-  different memory spaces, so the compiler may contract different products; relative
-  L-infinity <= 1e-6 after 30 steps).
+* It is bitwise the solo run under every schedule: the table kernels read the domain constants
+  from other memory spaces than the single-domain sweep, but the collide's rounding is fixed by
+  its source (no compiler contraction in the sweep file).
 * Every domain of the mix matches the FP64 oracle after 100 batched steps: relative L-inf
   <= 1e-5 for smooth fields and relative L1 <= 1e-4 for the shock tubes (FP32 storage; the
   FP16 / BF16 domains within the loose bounds of their other oracle comparisons).
@@ -82,15 +81,8 @@ def test_batch_equals_solo_runs(use_graph, nsteps, block_x, schedule):
         # alone in a batch == in the mix, bitwise
         assert np.array_equal(raw, batched_alone(c, nsteps, block_x, use_graph, schedule)), c.params.name
         Q_ref, raw_ref = solo(c, nsteps)
-        if schedule == capi.SCHED_CONCURRENT:   # the single-domain sweep itself
-            assert np.array_equal(raw, raw_ref), c.params.name
-            continue
-        # == the solo sweep within FP32 rounding; with 16-bit storage an FP32 rounding difference
-        # between the two kernels can round a stored value to the neighbouring 16-bit number
-        # (the tolerance of the other 16-bit path comparisons)
-        err = rel_linf(d.conserved(), Q_ref)
-        tol = 1e-6 if c.params.storage == inputs.STORE_F32 else 1e-2
-        assert np.all(err <= tol), (c.params.name, err)
+        assert np.array_equal(raw, raw_ref), (c.params.name, schedule)
+        assert np.array_equal(d.conserved(), Q_ref), (c.params.name, schedule)
     capi.grlb_batch_destroy(b)
 
 
@@ -194,8 +186,8 @@ def test_batched_domains_match_the_oracle(schedule):
 def test_batches_beyond_the_constant_record_slots_fall_back_to_the_tile_table():
     """The small domains' records go to a constant table of 160 slots shared by all batches;
     a batch that finds too few free slots runs the tile-table sweep (records in device memory)
-    instead, and gives the same results within FP32 rounding (the two kernels read the
-    constants from different memory spaces).  Slots come back when a batch is destroyed."""
+    instead, and gives the same results bit for bit.  Slots come back when a batch is
+    destroyed."""
     cases = [inputs.random_smooth(8, 4, 2, seed=s) for s in range(170)]
     doms = []
     for c in cases:
@@ -208,9 +200,7 @@ def test_batches_beyond_the_constant_record_slots_fall_back_to_the_tile_table():
     capi.grlb_batch_destroy(big)
     for c, d in zip(cases[:12], doms[:12]):
         ref = batched_alone(c, 9)                                    # constant-table records
-        got = np.frombuffer(capi.grlb_save(d.h)[32:].tobytes(), np.float32)
-        want = np.frombuffer(ref.tobytes(), np.float32)
-        assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), c.params.name
+        assert np.array_equal(capi.grlb_save(d.h)[32:], ref), c.params.name
     # many batches in turn reuse the slots (each must find its own records)
     for rnd in range(3):
         part = doms[rnd * 50:(rnd + 1) * 50]
@@ -223,9 +213,8 @@ def test_batches_beyond_the_constant_record_slots_fall_back_to_the_tile_table():
 
 
 def test_table_schedules_agree():
-    """Records in the constant table or in device memory: the same updates, within FP32
-    rounding (the kernels read the constants from different memory spaces); each schedule
-    bitwise reproducible."""
+    """Records in the constant table or in device memory: the same updates bit for bit; each
+    schedule bitwise reproducible."""
     cases = mixed_cases()
     res = {}
     for mode in (capi.SCHED_TABLE_CONST, capi.SCHED_TABLE, capi.SCHED_TABLE_CONST):
@@ -244,8 +233,7 @@ def test_table_schedules_agree():
         for d in doms:
             d.close()
     for c, x, y in zip(cases, res[capi.SCHED_TABLE_CONST], res[capi.SCHED_TABLE]):
-        tol = 1e-6 if c.params.storage == inputs.STORE_F32 else 1e-2
-        assert np.all(rel_linf(x, y) <= tol), c.params.name
+        assert np.array_equal(x, y), c.params.name
     with pytest.raises(capi.GrlbError):
         capi.grlb_batch_create([capi.Domain(cases[0].params).h], schedule=3)
 
