@@ -256,6 +256,8 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
     }
 }
 
+constexpr int kPrefetchPlanes = 2;  // L2 prefetch distance of the sweeps (planes)
+
 // ---- single-domain sweep -----------------------------------------------------------------
 // One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
 // parameter, so its constants are read as constant-bank operands of the arithmetic (a record
@@ -286,6 +288,21 @@ __device__ __forceinline__ void sweep_body(const DomainDev& D, const void* fin_v
         active = (x < D.nx) && (y < D.ny);
     }
     CellDiag cd;
+#ifndef GRLB_CHECKED
+    // 16-bit plain two-buffer sweeps of tiled domains whose rows are whole bricks: lane 0 of each
+    // row of a tile that starts a brick prefetches that brick (35 rows, 8.75 KB) two planes
+    // ahead into L2 with one bulk prefetch (the plane's CTAs run about a plane later).  256^3:
+    // FP16 0.426 -> 0.417 ms, BF16 0.422 -> 0.406 ms.  Not for FP32, HBM-bound at the copy
+    // bandwidth: 0.678 -> 0.803 ms with it.
+    if constexpr (S != S_F32 && !LIN && PAT == PULL && !DIAG) {
+        if (threadIdx.x == 0 && (D.nx & (kBrick - 1)) == 0 && (x & (kBrick - 1)) == 0 && y < D.ny &&
+            z + kPrefetchPlanes < D.nz) {
+            const T* brick = fin + brick_at_u32((uint32_t)((y + D.ny * (z + kPrefetchPlanes)) * D.nx + x));
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(brick), "r"((int)(NP * kBrick * sizeof(T)))
+                         : "memory");
+        }
+    }
+#endif
     if (active) {
         const PullIdx P = pull_index(D, x, y, z);
         const PullAt A = PAT == MOM ? pull_at_m(P) : pull_at(P);
@@ -339,10 +356,14 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant
 // the two previous steps (L1 hits), and the tile's rows march through the planes together.
 // 256^3: 0.501 ms with 4 planes per thread, 0.513 / 0.532 / 0.544 with 8 / 16 / 32, 0.519 with
 // 1 (the loop costs 40 bytes of spills at the 6-CTA register cap); the one-cell kernel 0.511.
-// Prefetching each row segment's moments into L2 two planes ahead (one prefetch per lane of
-// the first 20) ran 0.480 ms in short runs but added 5 % instructions, and in the sustained
-// benchmark the power cap then held the clock at ~1660 instead of ~1740 MHz: 31.07 against
-// 31.31 GLUP/s without it.
+// L2 prefetch two planes ahead: when the domain's rows are whole bricks (nx a multiple of 128),
+// lane 0 of each row of the CTAs whose tile starts a brick issues one bulk prefetch of that
+// brick at plane z + 2 (its 20 moment rows, 10 KB; at the first plane also z + 1), so the
+// rows a tile reaches next are on their way from DRAM while it collides.  256^3: 35.2 against
+// 33.1 GLUP/s in the benchmark (0.461 against 0.493 ms per sweep, at a lower clock under the
+// power cap); three planes ahead the same.  One instruction per row and plane: an earlier
+// prefetch of one 128-byte line per lane cost 5 % more instructions and lost under the power cap.
+// Not in the checked build (a prefetch reads nothing the kernel uses).
 // Staging the tile's planes in shared memory (cp.async, a ring of three planes, 96 KB per
 // 256-thread CTA) ran 0.821 ms: two CTAs per SM leave too few warps for the collide.
 // Carrying the column's z-window in registers (per field the arriving +z population and the
@@ -360,7 +381,20 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom_col(const __grid_cons
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= D.nx || y >= D.ny) return;
     const int zb = blockIdx.z * lz, ze = min(zb + lz, D.nz);
+#ifndef GRLB_CHECKED
+    // x is a multiple of kBrick and so is every row start: cell (x, y, zz) begins a brick, which
+    // lies whole inside the buffer for zz < nz
+    const bool pf = threadIdx.x == 0 && (D.nx & (kBrick - 1)) == 0 && (x & (kBrick - 1)) == 0;
+#endif
     for (int z = zb; z < ze; ++z) {
+#ifndef GRLB_CHECKED
+        if (pf) {
+            for (int zz = z == zb ? z + 1 : z + kPrefetchPlanes; zz <= z + kPrefetchPlanes && zz < D.nz; ++zz) {
+                const float* brick = fin + mom_at_u32((uint32_t)((y + D.ny * zz) * D.nx + x));
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(brick), "r"(NM * kBrick * 4) : "memory");
+            }
+        }
+#endif
         const PullIdx P = pull_index(D, x, y, z);
         const PullAt A = pull_at_m(P);
         float d[NF][NQ], o[NF][NQ];
