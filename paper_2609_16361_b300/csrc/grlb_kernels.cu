@@ -256,7 +256,8 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
     }
 }
 
-constexpr int kPrefetchPlanes = 2;  // L2 prefetch distance of the sweeps (planes)
+constexpr int kPrefetchPlanes = 2;           // L2 prefetch distance of the sweeps (planes)
+constexpr int kPrefetchMaxPlane = 256 * 256;  // largest plane (cells) the prefetch is issued for
 
 // ---- single-domain sweep -----------------------------------------------------------------
 // One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
@@ -293,10 +294,11 @@ __device__ __forceinline__ void sweep_body(const DomainDev& D, const void* fin_v
     // row of a tile that starts a brick prefetches that brick (35 rows, 8.75 KB) two planes
     // ahead into L2 with one bulk prefetch (the plane's CTAs run about a plane later).  256^3:
     // FP16 0.426 -> 0.417 ms, BF16 0.422 -> 0.406 ms.  Not for FP32, HBM-bound at the copy
-    // bandwidth: 0.678 -> 0.803 ms with it.
+    // bandwidth: 0.678 -> 0.803 ms with it; nor for the one-buffer patterns (1024^3 FP16: 29.0 ->
+    // 33.3 ms); planes of up to 256^2 cells only, as for the moment sweep.
     if constexpr (S != S_F32 && !LIN && PAT == PULL && !DIAG) {
         if (threadIdx.x == 0 && (D.nx & (kBrick - 1)) == 0 && (x & (kBrick - 1)) == 0 && y < D.ny &&
-            z + kPrefetchPlanes < D.nz) {
+            z + kPrefetchPlanes < D.nz && D.nx * D.ny <= kPrefetchMaxPlane) {
             const T* brick = fin + brick_at_u32((uint32_t)((y + D.ny * (z + kPrefetchPlanes)) * D.nx + x));
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(brick), "r"((int)(NP * kBrick * sizeof(T)))
                          : "memory");
@@ -363,7 +365,10 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant
 // 33.1 GLUP/s in the benchmark (0.461 against 0.493 ms per sweep, at a lower clock under the
 // power cap); three planes ahead the same.  One instruction per row and plane: an earlier
 // prefetch of one 128-byte line per lane cost 5 % more instructions and lost under the power cap.
-// Not in the checked build (a prefetch reads nothing the kernel uses).
+// Only for planes of up to 256^2 cells: at 512^3 and 1024^3 the cap held a lower clock with it
+// (1680 against 1845 MHz) and the sweep lost 3 % / 2.4 % (4.42 against 4.28 ms, 34.7 against
+// 33.9 ms); at 128^3 it changes nothing.  Not in the checked build (a prefetch reads nothing the
+// kernel uses).
 // Staging the tile's planes in shared memory (cp.async, a ring of three planes, 96 KB per
 // 256-thread CTA) ran 0.821 ms: two CTAs per SM leave too few warps for the collide.
 // Carrying the column's z-window in registers (per field the arriving +z population and the
@@ -384,7 +389,8 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom_col(const __grid_cons
 #ifndef GRLB_CHECKED
     // x is a multiple of kBrick and so is every row start: cell (x, y, zz) begins a brick, which
     // lies whole inside the buffer for zz < nz
-    const bool pf = threadIdx.x == 0 && (D.nx & (kBrick - 1)) == 0 && (x & (kBrick - 1)) == 0;
+    const bool pf = threadIdx.x == 0 && (D.nx & (kBrick - 1)) == 0 && (x & (kBrick - 1)) == 0 &&
+                    D.nx * D.ny <= kPrefetchMaxPlane;
 #endif
     for (int z = zb; z < ze; ++z) {
 #ifndef GRLB_CHECKED
