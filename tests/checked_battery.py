@@ -83,11 +83,14 @@ def run_domain(dg, case, steps, ce=None, stream=None):
 
 def sc_sweeps(dg):
     """Every storage x collision on a tiled grid (32^3: 32 x 4 CTA tiles) and on the linear
-    mapping (40 x 21 x 7, ragged last brick); 9 sweeps (one graph replay of 8) + 1 diagnostic."""
+    mapping (40 x 21 x 7, ragged last brick); 9 sweeps (one graph replay of 8) + 1 diagnostic.
+    And rows of whole bricks (128 x 4 x 6), where the plain library's 16-bit sweeps prefetch the
+    bricks two planes ahead into L2 and the checked build does not: the results must not move."""
     for s in STORAGES:
         for c in COLLISIONS:
             run_domain(dg, with_params(inputs.tgv3d(32, storage=s), collision=c), 9)
             run_domain(dg, inputs.random_smooth(40, 21, 7, seed=3, storage=s, collision=c), 9)
+        run_domain(dg, inputs.random_smooth(128, 4, 6, seed=7, storage=s), 9)
 
 
 def sc_one_buffer(dg):
@@ -291,6 +294,7 @@ def sc_moments(dg):
     sweep, the Chapman-Enskog start, readback, probes and spectra."""
     for case, ce in ((inputs.tgv3d(16), False), (inputs.tgv3d(16, mach=0.5, re=100.0), True),
                      (inputs.tgv3d(32), False),   # tiled: the column-marching sweep
+                     (inputs.random_smooth(128, 8, 6, seed=8), False),   # whole-brick rows: L2 prefetch
                      (inputs.random_smooth(40, 21, 7, seed=3), False), (inputs.sod(64), False)):
         run_domain(dg, with_params(case, streaming=2), 9, ce=ce)
         d = capi.Domain(case.params.replace(streaming=2))

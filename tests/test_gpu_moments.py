@@ -33,6 +33,7 @@ def run(case, steps, streaming, ce=None, diag=False):
 
 CASES = {
     "tgv32 (tiled, 32 x 4)": lambda: inputs.tgv3d(32),
+    "128x8x6 (whole-brick rows: L2 prefetch)": lambda: inputs.random_smooth(128, 8, 6, seed=8),
     "ragged 40x21x7 (linear)": lambda: inputs.random_smooth(40, 21, 7, seed=3),
     "sod 400 (Dirichlet ghosts)": lambda: inputs.sod(400),
     "becker 128x4x4": lambda: inputs.becker(128, ny=4, nz=4),
