@@ -256,8 +256,9 @@ __device__ __forceinline__ void block_reduce_diag(const CellDiag& cd, bool activ
     }
 }
 
-constexpr int kPrefetchPlanes = 2;           // L2 prefetch distance of the sweeps (planes)
-constexpr int kPrefetchMaxPlane = 256 * 256;  // largest plane (cells) the prefetch is issued for
+// (unused in the checked build, which issues no prefetch)
+[[maybe_unused]] constexpr int kPrefetchPlanes = 2;           // L2 prefetch distance (planes)
+[[maybe_unused]] constexpr int kPrefetchMaxPlane = 256 * 256;  // largest plane (cells) prefetched for
 
 // ---- single-domain sweep -----------------------------------------------------------------
 // One CTA per tile of blockDim.x x blockDim.y cells at one z.  The domain record is a kernel
@@ -342,7 +343,8 @@ __global__ void __launch_bounds__(128, 5) sweep_kernel_gated_f32(const __grid_co
 // The plain moment-storage sweep waits mostly on its 65 loads per cell (L1 / L2 hits of the
 // sources' moments).  With IEEE divisions in the collide it held 92 registers (5 CTAs per SM)
 // and ran 1.7 % faster capped at 6 CTAs; with the approximate divisions it fits the 6-CTA cap
-// (80 registers) without spills, and 6 or 8 CTAs per SM run alike (33.2 GLUP/s).  The
+// (80 registers) without spills; 6 or 8 CTAs per SM ran alike (33.2 GLUP/s) before the column
+// kernel's L2 prefetch, with it 6 CTAs 35.0 against 34.4 GLUP/s at 8 (64 registers).  The
 // diagnostic variant (72 registers) keeps the plain bound.  The rounding of every operation
 // is fixed by the source (no compiler contraction in this file), so the cap does not change
 // results.
