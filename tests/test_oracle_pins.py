@@ -210,6 +210,37 @@ def test_gated_collision_is_bgk_off_the_sensor_and_regularized_on_it():
             np.testing.assert_allclose(Jout, J[k] + om_r * (Phi[k] - J[k]), atol=1e-14)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_regularized_outgoing_set_lies_in_the_span_of_four_moments(seed):
+    """Sec. 2.5: the regularized collision keeps only the equilibrium and the first-moment
+    non-equilibrium part, so each field's outgoing populations are w_i (Q*_k + c_i . J*_k / cs^2)
+    with Q*_k, J*_k their own zeroth and first moments -- four numbers per field, whatever
+    second-moment non-equilibrium the incoming set carries (the fact that lets the state be
+    stored as 20 moments per cell).  BGK keeps (1 - omega) of that part, so its outgoing set
+    leaves the span: the check can fail."""
+    rng = np.random.default_rng(40 + seed)
+    rho, p = rng.uniform(0.7, 1.5), rng.uniform(0.1, 0.5)
+    u = rng.uniform(-0.1, 0.1, 3)
+    gu = rng.uniform(-2e-3, 2e-3, (3, 3))
+    gr, gT = rng.uniform(-1e-3, 1e-3, 3), rng.uniform(-1e-3, 1e-3, 3)
+    out = {}
+    for coll in (inputs.COLL_RLB_SENSOR, inputs.COLL_BGK):
+        P = lattice_P(mu_ref=0.05, collision=coll)
+        Q, J, _ = build_first_moments(rho, u, p, gr, gu, gT, 0.05, 0.07, np.full(5, P.omega[0]), 1.4)
+        f = pops_with_moments(Q, J)
+        f += 1e-3 * rng.standard_normal(35) * np.repeat([1, 1, 1, 1, 2], 7)  # every moment perturbed
+        fstar, _ = oracle.cell(P, f)
+        worst = 0.0
+        for k in range(5):
+            fk = fstar[7 * k:7 * k + 7]
+            Qs, Js = fk.sum(), CI.T @ fk
+            span = WI * (Qs + CI @ Js / CS2)
+            worst = max(worst, np.abs(fk - span).max())
+        out[coll] = worst
+    assert out[inputs.COLL_RLB_SENSOR] <= 1e-15
+    assert out[inputs.COLL_BGK] > 1e-6
+
+
 def test_gated_collision_without_sensor_gain_is_bgk():
     """With gain 0 the sensor never fires, so the gated collision is BGK on every cell."""
     c = inputs.random_smooth(10, 7, 5, seed=4)
