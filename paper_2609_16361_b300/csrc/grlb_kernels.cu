@@ -366,7 +366,9 @@ __global__ void __launch_bounds__(128, 6) sweep_kernel_mom(const __grid_constant
 // rows a tile reaches next are on their way from DRAM while it collides.  256^3: 35.2 against
 // 33.1 GLUP/s in the benchmark (0.461 against 0.493 ms per sweep, at a lower clock under the
 // power cap); three planes ahead the same.  One instruction per row and plane: an earlier
-// prefetch of one 128-byte line per lane cost 5 % more instructions and lost under the power cap.
+// prefetch of one 128-byte line per lane cost 5 % more instructions and lost under the power cap,
+// and one thread per band of rows prefetching the band's bricks (fewer warps take the branch)
+// ran 34.8 against 35.8 GLUP/s.
 // Only for planes of up to 256^2 cells: at 512^3 and 1024^3 the cap held a lower clock with it
 // (1680 against 1845 MHz) and the sweep lost 3 % / 2.4 % (4.42 against 4.28 ms, 34.7 against
 // 33.9 ms); at 128^3 it changes nothing.  Not in the checked build (a prefetch reads nothing the
