@@ -204,3 +204,47 @@ def test_counter_records_are_keyed_to_code_not_comments():
     two = {"a.cu": "int x;\nint y;", "b.cu": "int z;"}
     moved = {"a.cu": "int x;", "b.cu": "int y;\nint z;"}
     assert bench.kernel_source_sha(["a.cu", "b.cu"], read=two.get) != bench.kernel_source_sha(["a.cu", "b.cu"], read=moved.get)
+
+
+def test_l2_prefetch_addresses_stay_inside_the_state_buffer():
+    """The sweeps' bulk L2 prefetches (not seen by the bounds-checked build, which issues none)
+    replayed on the host with the kernels' index arithmetic for every CTA of many launches:
+    each prefetched range is one whole brick (20 moment rows x 128 FP32 values, or 35
+    population rows x 128 16-bit values), starts on a 16-byte boundary and lies inside the
+    buffer.  Moment sweep: lane 0 of each tile row whose x starts a brick, planes z + 1 (first
+    plane of a chunk) and z + 2 below nz; 16-bit sweep: the same lane, plane z + 2 below nz;
+    both only when nx is a multiple of 128 and nx ny <= 256^2."""
+    BR, NM, NP = 128, 20, 35
+    for nx in (128, 256, 384, 512):
+        for ny in (1, 3, 4, 8, 37):
+            for nz in (1, 2, 3, 5, 8):
+                N = nx * ny * nz
+                if nx % BR or nx * ny > 256 * 256:
+                    continue
+                nbricks = -(-N // BR)
+                for bx, by in ((32, 4), (64, 2), (128, 1)):
+                    lz = min(nz, 4)
+                    for gx in range(-(-nx // bx)):
+                        x = gx * bx                      # lane threadIdx.x == 0
+                        if x % BR:
+                            continue
+                        for gy in range(-(-ny // by)):
+                            for ty in range(by):
+                                y = gy * by + ty
+                                if y >= ny:
+                                    continue
+                                for gz in range(-(-nz // lz)):       # moment column kernel
+                                    zb, ze = gz * lz, min(gz * lz + lz, nz)
+                                    for z in range(zb, ze):
+                                        for zz in range(z + 1 if z == zb else z + 2, min(z + 2, nz - 1) + 1):
+                                            c = (y + ny * zz) * nx + x
+                                            assert c % BR == 0 and c < N
+                                            start = (c // BR) * NM * BR * 4          # bytes
+                                            assert start % 16 == 0 and (NM * BR * 4) % 16 == 0
+                                            assert start + NM * BR * 4 <= nbricks * NM * BR * 4
+                                for z in range(nz):                  # 16-bit population sweep
+                                    if z + 2 < nz:
+                                        c = (y + ny * (z + 2)) * nx + x
+                                        start = (c // BR) * NP * BR * 2
+                                        assert c % BR == 0 and start % 16 == 0 and (NP * BR * 2) % 16 == 0
+                                        assert start + NP * BR * 2 <= nbricks * NP * BR * 2
